@@ -1,0 +1,207 @@
+"""Pins of the oracle's CG, Algorithm I and Algorithm II (CPU only).
+
+Each pin comes from outside the oracle: a dense factorisation, a closed-form
+spectrum, the convergence bound of Eq. (9), an exactly representable case.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+import synth
+
+
+def random_spd(n, kappa, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.geomspace(1.0, kappa, n)
+    M = (Q * ev) @ Q.T
+    M = 0.5 * (M + M.T)
+    rows, cols = np.nonzero(np.ones((n, n)))
+    return synth.CSR(np.arange(0, n * n + 1, n, dtype=np.int32), cols.astype(np.int32),
+                     M[rows, cols].copy(), f"dense_spd_{n}"), M
+
+
+def star_laplacian(n, sigma):
+    """L = D - Adj of the star K_{1,n-1} plus sigma I: eigenvalues sigma, 1+sigma, n+sigma."""
+    i = np.zeros(n - 1, dtype=np.int64)
+    j = np.arange(1, n, dtype=np.int64)
+    deg = np.ones(n)
+    deg[0] = n - 1
+    return synth.from_edges(n, i, j, -np.ones(n - 1), deg + sigma, "starlap")
+
+
+def test_spmv_matches_dense_product():
+    A, M = random_spd(40, 100.0, 0)
+    x = np.random.default_rng(1).standard_normal(40)
+    np.testing.assert_allclose(oracle.spmv64(A, x), M @ x, rtol=1e-13, atol=1e-13)
+    y32 = oracle.spmv32(A, x)
+    M32 = M.astype(np.float32).astype(np.float64)
+    ref = M32 @ x.astype(np.float32).astype(np.float64)
+    assert np.all(np.abs(y32 - ref) <= 40 * 6e-8 * (np.abs(M32) @ np.abs(x)))
+
+
+def test_fp32_dot_accumulates_in_double():
+    """Remark 3 (Sec. 9): norms of the FP32 stage in double.  A float32
+    accumulator would return exactly 1.0 here."""
+    a = np.concatenate([[1.0], np.full(1000, 1e-4)]).astype(np.float32)
+    exact = math.fsum(float(v) * float(v) for v in a)
+    assert oracle.dot32(a, a) == pytest.approx(exact, rel=1e-14)
+    assert oracle.dot32(a, a) > 1.0 + 9e-6
+
+
+@pytest.mark.parametrize("n,kappa,seed", [(8, 10.0, 0), (32, 1e3, 1), (64, 1e4, 2)])
+def test_cg64_matches_cholesky(n, kappa, seed):
+    A, M = random_spd(n, kappa, seed)
+    b = np.random.default_rng(seed + 10).standard_normal(n)
+    xc = scipy.linalg.cho_solve(scipy.linalg.cho_factor(M), b)
+    x, it, st = oracle.cg64(A, b, 1e-14, max_it=20 * n)
+    assert st == oracle.OK
+    assert np.linalg.norm(x - xc) / np.linalg.norm(xc) <= kappa * 1e-13
+
+
+@pytest.mark.parametrize("n,seed", [(6, 0), (12, 1), (16, 2), (20, 3)])
+def test_cg64_terminates_within_n_steps(n, seed):
+    """n distinct eigenvalues in [1, 10]: the rate of Eq. (9) alone would need
+    about 37 iterations for 1e-10, so stopping by n is finite termination."""
+    A, M = random_spd(n, 10.0, seed)
+    b = np.random.default_rng(seed).standard_normal(n)
+    _, it, st = oracle.cg64(A, b, 1e-10, max_it=4 * n)
+    assert st == oracle.OK and it <= n
+
+
+@pytest.mark.parametrize("n,sigma", [(50, 0.5), (1001, 1e-2), (400, 1.0)])
+def test_cg64_three_distinct_eigenvalues(n, sigma):
+    A = star_laplacian(n, sigma)
+    ev = np.unique(np.round(np.linalg.eigvalsh(A.to_dense()), 9))
+    np.testing.assert_allclose(ev, [sigma, 1 + sigma, n + sigma], rtol=1e-9)
+    b = np.random.default_rng(0).uniform(-1, 1, n)
+    kappa = (n + sigma) / sigma
+    x, it, st, h = oracle.cg64(A, b, 0.0, max_it=3, history=True)
+    # the Krylov space is exhausted at step 3: the residual falls from O(1e-2)
+    # to the rounding floor (a multiple of u * kappa)
+    assert h.size == 4 and h[2] > 1e-3
+    assert h[3] <= 1000 * kappa * 1.1e-16
+
+
+def test_scaled_identity_one_iteration_and_v_zero():
+    """A = 4I: alpha = 1/4 exactly, r1 = 0 exactly, so v over one ratio is 0."""
+    n = 300
+    A = synth.from_edges(n, np.zeros(0), np.zeros(0), np.zeros(0), np.full(n, 4.0))
+    b = np.random.default_rng(2).uniform(1, 2, n)
+    x, it, st = oracle.cg64(A, b, 1e-12)
+    assert it == 1 and np.array_equal(x, b / 4)
+    feat, k0d, st = oracle.features(A, b, k0=10)
+    assert k0d == 1 and feat[3] == 0.0 and feat[2] == 0.0
+    # Algorithm I: the FP32 stage ends at float32(b)/4; the FP64 restart sees
+    # r0 = b - float32(b) != 0 and needs exactly one step, which lands on b/4.
+    x, r = oracle.solve(A, b, eps1=1e-4, eps2=1e-10)
+    assert (r["n1"], r["n2"]) == (1, 1) and np.array_equal(x, b / 4)
+
+
+def test_residual_bound_eq9():
+    """Eq. (9) in the residual norm: ||r_k|| / ||r_0|| <= 2 sqrt(kappa) rho^k."""
+    nx, ny = 24, 17
+    A = synth.laplacian_2d(nx, ny)
+    ev = np.linalg.eigvalsh(A.to_dense())
+    kappa = ev[-1] / ev[0]
+    rho = (math.sqrt(kappa) - 1) / (math.sqrt(kappa) + 1)
+    _, b = synth.rhs(A, 4)
+    x, it, st, hist = oracle.cg64(A, b, 1e-12, history=True)
+    assert st == oracle.OK
+    rel = hist / hist[0]
+    bound = 2 * math.sqrt(kappa) * rho ** np.arange(rel.size)
+    assert np.all(rel <= bound * (1 + 1e-9))
+    # and Eq. (9) bounds the iteration count through the A-norm error
+    assert it <= oracle.metrics.cg_iter_bound(kappa, 1e-12 / math.sqrt(kappa)) + 1
+
+
+def test_fp32_cg_follows_fp64_cg_on_the_rounded_matrix():
+    """Before rounding errors dominate, the FP32 iterates track FP64 CG run on
+    float32(A), float32(b)."""
+    A = synth.laplacian_2d(30, 30)
+    _, b = synth.rhs(A, 7)
+    A32 = synth.CSR(A.row_ptr, A.col, A.val.astype(np.float32).astype(np.float64))
+    b32 = b.astype(np.float32).astype(np.float64)
+    _, _, _, h32 = oracle.cg32(A, b, 1e-5, history=True)
+    _, _, _, h64 = oracle.cg64(A32, b32, 1e-5, history=True)
+    k = min(h32.size, h64.size, 20)
+    np.testing.assert_allclose(h32[:k], h64[:k], rtol=1e-4)
+    assert abs(h32.size - h64.size) <= 2
+
+
+def test_algorithm_i_stages_are_plain_cg_runs():
+    """Algorithm I = FP32 CG to eps1, promote, FP64 CG to eps2 (Sec. 1)."""
+    A, xs, b = synth.poisson64()
+    x32, it32, _ = oracle.cg32(A, b, 1e-4)
+    x64, it64, _ = oracle.cg64(A, b, 1e-10, x0=x32.astype(np.float64))
+    x, r = oracle.solve(A, b, eps1=1e-4, eps2=1e-10)
+    assert r["status"] == oracle.OK
+    assert (r["n1"], r["n2"]) == (it32, it64)
+    assert np.array_equal(x, x64)
+    assert r["true_rel_resid"] <= 1e-10
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1711.7 * 1e-10 * 10
+    assert r["true_rel_resid"] == pytest.approx(oracle.true_rel_resid(A, b, x), rel=1e-12)
+
+
+def test_algorithm_ii_with_one_class_sample():
+    """A sample whose every label is t = 5 must give eps1 = 1e-5; the k0
+    iterations count toward N1 and the stage continues from iterate k0."""
+    A, xs, b = synth.poisson64()
+    feat, cls = synth.random_sample(30, seed=1)
+    cls[:] = 5
+    x, r = oracle.solve(A, b, S=(feat, cls), k0=10)
+    assert r["cls"] == 5 and r["eps1"] == 1e-5 and r["k0_done"] == 10
+    _, it32, _ = oracle.cg32(A, b, 1e-5)
+    assert r["n1"] == it32          # continuing from k0 is the same FP32 trajectory
+    assert r["pdiam"] == 126 and r["feat"][:3] == [4096.0, 20224.0, 126.0]
+    _, _, _, h = oracle.cg32(A, b, 1e-5, history=True)
+    v = np.mean(h[1:11] / h[0:10])
+    assert r["v"] == pytest.approx(v, rel=1e-12)
+
+
+def test_zero_rhs_and_nan_and_indefinite():
+    A = synth.laplacian_2d(8, 8)
+    x, r = oracle.solve(A, np.zeros(A.n), eps1=1e-4)
+    assert r["status"] == oracle.OK and not x.any() and r["n1"] == r["n2"] == 0
+    b = np.ones(A.n)
+    b[3] = np.nan
+    _, r = oracle.solve(A, b, eps1=1e-4)
+    assert r["status"] == oracle.ERR_NAN
+    neg = synth.CSR(A.row_ptr, A.col, -A.val)
+    _, r = oracle.solve(neg, np.ones(A.n), eps1=1e-4)
+    assert r["status"] == oracle.ERR_BREAKDOWN
+
+
+def test_fp64_cap_reports_not_converged():
+    A, xs, b = synth.poisson64()
+    _, r = oracle.solve(A, b, eps1=1e-4, max_it_fp64=5)
+    assert r["status"] == oracle.ERR_NOT_CONVERGED and r["n2"] == 5
+
+
+def test_eps1_cap_warns_and_switches():
+    A, xs, b = synth.poisson64()
+    x, r = oracle.solve(A, b, eps1=1e-4, max_it_fp32=7)
+    assert r["status"] == oracle.WARN_EPS1_NOT_REACHED and r["n1"] == 7
+    assert r["true_rel_resid"] <= 1e-10
+
+
+def test_decay_rate_v_closed_form_two_eigenvalues():
+    """Eq. (13) with k0 = 1 on A = diag(l1 I, l2 I): the first CG step is a
+    steepest-descent step, so ||r1||^2 = (1 - a l1)^2 |u|^2 + (1 - a l2)^2 |w|^2
+    with a = (|u|^2 + |w|^2) / (l1 |u|^2 + l2 |w|^2), b = (u, w).  With k0 = 2
+    the second ratio is ~0 (two eigenvalues: CG ends at step 2)."""
+    n, l1, l2 = 64, 1.0, 16.0
+    diag = np.where(np.arange(n) < n // 2, l1, l2)
+    A = synth.from_edges(n, np.zeros(0), np.zeros(0), np.zeros(0), diag)
+    b = np.random.default_rng(5).uniform(1, 2, n).astype(np.float32).astype(np.float64)
+    u2 = float(np.sum(b[: n // 2] ** 2))
+    w2 = float(np.sum(b[n // 2:] ** 2))
+    a = (u2 + w2) / (l1 * u2 + l2 * w2)
+    ratio1 = math.sqrt((1 - a * l1) ** 2 * u2 + (1 - a * l2) ** 2 * w2) / math.sqrt(u2 + w2)
+    feat, k0d, _ = oracle.features(A, b, k0=1)
+    assert k0d == 1 and feat[3] == pytest.approx(ratio1, rel=2e-6)
+    feat, k0d, _ = oracle.features(A, b, k0=2, eps2=0.0)
+    assert k0d == 2 and feat[3] == pytest.approx(ratio1 / 2, rel=1e-5)
