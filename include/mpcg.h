@@ -1,0 +1,201 @@
+/*
+ * mpcg.h -- C ABI of libmpcg: restarted mixed-precision conjugate gradient
+ * for sparse SPD systems on NVIDIA GB300 (sm_103a).
+ *
+ * Method: Prolubnikov, "Parameter Optimization for Restarted Mixed-Precision
+ * Iterative Sparse Solver" (arXiv 2412.08059).
+ *   - Algorithm I (Sec. 1): CG (Sec. 3) on float32(A), float32(b) from x = 0
+ *     until the residual reaches eps1; x0 = float64(x~); CG in double from
+ *     x0, with r0 = b - A x0 recomputed in double, until eps2.
+ *   - Algorithm II (Sec. 9): the first k0 single-precision iterations give
+ *     the mean residual-decay ratio v (Eq. 13); with n, m and the 2BFS
+ *     pseudo-diameter (Sec. 6) it forms chi = (n, m, l~, v); a
+ *     distance-weighted kNN vote over a labelled sample (Sec. 11, Eq. 23)
+ *     picks eps1 = 10^-t; the single-precision stage continues from
+ *     iterate k0.
+ *
+ * Conventions (all entry points):
+ *   - Every array argument is DEVICE memory owned by the caller unless the
+ *     parameter says otherwise.  The library never allocates device memory:
+ *     it carves the caller's workspace `ws` (size from mpcg_workspace_bytes).
+ *   - Calls are stream-ordered on `stream` and never synchronise the host.
+ *     The workspace, the outputs and the inputs must stay valid until the
+ *     stream reaches the end of the call's work.  Two calls that share a
+ *     workspace must not overlap on the GPU.
+ *   - The return value reports argument and launch errors found on the host
+ *     (MPCG_ERR_INVALID_ARG, MPCG_ERR_WORKSPACE, MPCG_ERR_CUDA).  Numerical
+ *     outcomes (convergence, breakdown, NaN, timeouts of device-side waits)
+ *     are written to the device-side result record and are valid after the
+ *     stream has synchronised.  Negative = error, positive = warning.
+ *   - CSR input: row_ptr int32[n+1] (row_ptr[0] = 0, non-decreasing,
+ *     row_ptr[n] = nnz), col int32[nnz] (0 <= col < n, sorted within each
+ *     row, diagonal stored), val float64[nnz].  The matrix is assumed
+ *     symmetric positive definite; the sparsity graph of Sec. 4 uses the
+ *     stored off-diagonal entries.  A CSR that violates the index rules is
+ *     reported as MPCG_ERR_INVALID_ARG in the result record (the device
+ *     check skips the work, it never faults).
+ *
+ * Numerics of the single-precision stage (readings of the paper): SpMV sums
+ * each row in stored order with single-precision fused multiply-adds; dot
+ * products and norms are accumulated with at least double accuracy (Remark 3
+ * of Sec. 9); alpha and beta are rounded once to float.  The stop test uses
+ * the recursively updated residual, relative to ||b|| by default.
+ */
+#ifndef MPCG_H
+#define MPCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; 0 is the legacy default stream. */
+struct CUstream_st;
+typedef struct CUstream_st* mpcg_stream_t;
+
+typedef enum {
+  MPCG_OK = 0,
+  MPCG_WARN_EPS1_NOT_REACHED = 1,     /* stage 1 stopped by its cap or a breakdown; switched anyway */
+  MPCG_WARN_TRUE_RESID_RESTARTED = 2, /* recursive residual met eps2, true one did not: FP64 restarted */
+  MPCG_ERR_INVALID_ARG = -1,
+  MPCG_ERR_WORKSPACE = -2,            /* ws NULL, misaligned (256 B) or smaller than required */
+  MPCG_ERR_BREAKDOWN = -3,            /* d^T A d <= 0 in the FP64 stage: A is not SPD */
+  MPCG_ERR_NAN = -4,                  /* non-finite value in b, A or an iterate */
+  MPCG_ERR_NOT_CONVERGED = -5,        /* FP64 stage reached max_it_fp64 */
+  MPCG_ERR_TIMEOUT = -6,              /* a device-side wait exceeded timeout_ms */
+  MPCG_ERR_CUDA = -7,                 /* a CUDA launch or runtime call failed */
+  MPCG_ERR_CANCELLED = -8,
+  MPCG_ERR_UNIMPLEMENTED = -9
+} mpcg_status_t;
+
+/* Sparse SPD matrix, CSR, device pointers, caller-owned (see conventions). */
+typedef struct {
+  int32_t n;
+  int32_t nnz;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+} mpcg_csr_t;
+
+/* Feature vector chi = (n, m, l~, v) of Sec. 4; m = stored nnz. */
+typedef struct {
+  double n, m, pdiam, v;
+  int32_t k0_done; /* single-precision iterations that entered v */
+  int32_t status;
+} mpcg_features_t;
+
+/* Labelled kNN sample S of Sec. 11: feat = raw features [count][4]
+ * (device, float64, row-major), cls = class t per row (device, int8,
+ * eps1 = 10^-t, 0 <= t <= 15), fmin/fmax = per-component min-max scaling
+ * (host values, copied at call time).  count <= MPCG_KNN_MAX_SAMPLE. */
+#define MPCG_KNN_MAX_SAMPLE 65536
+#define MPCG_KNN_MAX_K 64
+typedef struct {
+  const double* feat;
+  const int8_t* cls;
+  int32_t count;
+  double fmin[4], fmax[4];
+} mpcg_sample_t;
+
+typedef struct {
+  double eps1;               /* > 0: Algorithm I with this eps1; <= 0: Algorithm II */
+  double eps2;               /* final tolerance (default 1e-10) */
+  int32_t k0;                /* iterations that define v (default 10) */
+  int32_t knn_k;             /* neighbours (default 5, <= MPCG_KNN_MAX_K) */
+  int32_t weighted;          /* 1: Eq. (23) vote (default); 0: Eq. (22) */
+  int32_t tol_relative;      /* 1: ||r||/||b|| <= eps (default); 0: ||r|| <= eps */
+  int32_t max_it_fp32;       /* cap on N1 including k0 (<= 0: n) */
+  int32_t max_it_fp64;       /* cap on N2 (<= 0: 10 n) */
+  int32_t max_true_restarts; /* extra FP64 restarts if the true residual misses eps2 (default 2) */
+  uint32_t feat_mask;        /* bit c: feature c enters the distance (default 0xF) */
+  int32_t fp64_only;         /* 1: pure FP64 CG from x0 = 0 (the baseline); no stage 1 */
+  int32_t grid_blocks;       /* persistent grid size; 0 = one full wave of the device */
+  int32_t timeout_ms;        /* limit of every device-side wait (default 20000) */
+  int32_t reserved[5];
+} mpcg_options_t;
+
+/* Result record, written by the device at the end of the call's work into
+ * memory the device can write (device memory or mapped pinned host memory). */
+typedef struct {
+  int32_t status;
+  int32_t n1;                /* single-precision iterations, k0 included */
+  int32_t n2;                /* double-precision iterations, restarts included */
+  int32_t cls;               /* kNN class t (-1 under Algorithm I) */
+  int32_t k0_done;
+  int32_t restarts;          /* extra FP64 restarts taken */
+  double eps1;
+  double true_rel_resid;     /* ||b - A x||_2 / ||b||_2 in FP64 */
+  double pdiam;              /* 2BFS pseudo-diameter (Algorithm II) */
+  double v;                  /* Eq. (13) */
+  double res_fp32;           /* stop measure at the end of stage 1 */
+  double res_fp64;           /* stop measure at the end of stage 2 */
+  uint64_t t_start_ns, t_features_ns, t_fp32_ns, t_fp64_ns, t_end_ns; /* device clock marks */
+} mpcg_result_t;
+
+mpcg_options_t mpcg_options_default(void);
+const char* mpcg_status_string(int32_t status);
+
+/* Device workspace bytes for an n x n matrix with nnz stored entries.  The
+ * bound holds for every sparsity pattern with those counts.  0 on invalid
+ * sizes.  Base pointers must be 256-byte aligned. */
+size_t mpcg_workspace_bytes(int32_t n, int32_t nnz, const mpcg_options_t* opts);
+
+/* Features of Algorithm II (Sec. 9 steps 1-3; Sec. 6 for l~): converts A and
+ * b to float32, runs k0 single-precision CG iterations from x = 0 for v
+ * (Eq. 13) and the 2BFS pseudo-diameter.  out: device mpcg_features_t. */
+int32_t mpcg_features(const mpcg_csr_t* A, const double* b, const mpcg_options_t* opts,
+                      void* ws, size_t ws_bytes, mpcg_features_t* out, mpcg_stream_t stream);
+
+/* kNN choice of eps1 (Sec. 11): min-max scales f with the sample's
+ * fmin/fmax, selects the k nearest by (squared distance, index), votes by
+ * Eq. (23) or Eq. (22); a zero distance votes by count among the
+ * zero-distance neighbours; vote ties go to the smallest t.  f: device
+ * features; eps1_out (double) and cls_out (int32): device, nullable. */
+int32_t mpcg_choose_eps1(const mpcg_features_t* f, const mpcg_sample_t* sample,
+                         const mpcg_options_t* opts, double* eps1_out, int32_t* cls_out,
+                         mpcg_stream_t stream);
+
+/* The method (Algorithm II, or Algorithm I when opts->eps1 > 0, or pure FP64
+ * CG when opts->fp64_only): x (device, float64[n]) receives the solution;
+ * its input value is ignored (x0 = 0).  sample: required by Algorithm II,
+ * ignored otherwise.  res: device-writable result record. */
+int32_t mpcg_solve(const mpcg_csr_t* A, const double* b, double* x, const mpcg_sample_t* sample,
+                   const mpcg_options_t* opts, void* ws, size_t ws_bytes, mpcg_result_t* res,
+                   mpcg_stream_t stream);
+
+/* Independent systems solved together (spec batching pattern, not in
+ * the paper).  A: host array of nsys CSR descriptors (device pointers);
+ * b, x: host arrays of nsys device pointers; res: device array of nsys
+ * records.  Workspace: mpcg_batch_workspace_bytes.  Every system gets its own
+ * eps1 and features; systems run concurrently on disjoint parts of the GPU. */
+size_t mpcg_batch_workspace_bytes(int32_t nsys, const int32_t* n, const int32_t* nnz,
+                                  const mpcg_options_t* opts);
+int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const double* const* b,
+                         double* const* x, const mpcg_sample_t* sample,
+                         const mpcg_options_t* opts, void* ws, size_t ws_bytes,
+                         mpcg_result_t* res, mpcg_stream_t stream);
+
+/* ---- building blocks exposed for verification (same kernels as above) ---- */
+
+/* y = A x through the library's SpMV (single or double precision, chosen by
+ * `fp32`); x, y device float32[n] or float64[n].  Uses ws for the sliced
+ * layout built from A (same layout as the solver). */
+int32_t mpcg_spmv(const mpcg_csr_t* A, int32_t fp32, const void* x, void* y, void* ws,
+                  size_t ws_bytes, mpcg_stream_t stream);
+
+/* Breadth-first distances from src over the sparsity graph (Sec. 6):
+ * dist device int32[n], -1 for unreached vertices. */
+int32_t mpcg_bfs(const mpcg_csr_t* A, int32_t src, int32_t* dist, void* ws, size_t ws_bytes,
+                 mpcg_stream_t stream);
+
+/* 2BFS pseudo-diameter with the per-component rule (Sec. 6); out: device
+ * int32[2] = {l~, t} where t is the farthest vertex found from vertex 0. */
+int32_t mpcg_pseudo_diameter(const mpcg_csr_t* A, int32_t* out, void* ws, size_t ws_bytes,
+                             mpcg_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPCG_H */

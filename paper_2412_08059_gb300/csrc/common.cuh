@@ -1,0 +1,216 @@
+// common.cuh -- device-side building blocks shared by the libmpcg kernels:
+// the per-solve control block, the workspace map, bounded grid barriers,
+// deterministic reductions and float-float accumulation.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mpcg.h"
+
+namespace mpcg {
+
+constexpr int kSlice = 32;          // rows per slice of the sliced layout (one warp)
+constexpr int kCgThreads = 512;     // threads per block of the persistent kernels
+constexpr int kMaxGrid = 2048;      // upper bound on persistent grid blocks
+constexpr int kBarSlots = 32;       // barrier counters per control block
+constexpr uint32_t kOverflowBit = 0x80000000u;
+
+// ---------------------------------------------------------------------------------------
+// Control block: all state of one solve that lives on the device.  Zeroed by
+// the host (cudaMemsetAsync) at the start of every call, then initialised.
+// ---------------------------------------------------------------------------------------
+struct Ctl {
+  unsigned long long bar[kBarSlots];  // monotone grid-barrier arrival counters
+  int status;                         // first error wins (atomicCAS from 0)
+  int trivial;                        // b == 0: x = 0 and nothing else runs
+  int warn_eps1;
+  int warn_restart;
+  // problem and options
+  int n, nnz, nslices, wcap;
+  int k0, max1, max2, max_restarts, tol_relative;
+  double eps1, eps2;
+  long long timeout_ns;
+  // norms
+  double bnorm32, bnorm64;
+  // CG state carried between launches
+  double rr;          // r^T r of the current residual
+  float beta32;       // pending beta of the single-precision stage
+  int first;          // next iteration starts with d = r
+  int parity;         // current d buffer of the single-precision stage
+  int broke32;        // stage 1 ended by d^T A d <= 0
+  int n1, n2, k0_done, restarts;
+  double vsum, v;
+  double res32, res64, true_rel;
+  // features and kNN
+  int pdiam, far_t, reached, ncomp, connected;
+  unsigned long long key;
+  int qsize[3];
+  int ccflag[2];
+  int cls;
+  // device clock marks (ns)
+  unsigned long long t_start, t_features, t_fp32, t_fp64, t_end;
+};
+
+// ---------------------------------------------------------------------------------------
+// Workspace map (device pointers carved from the caller's buffer).
+// ---------------------------------------------------------------------------------------
+struct Ws {
+  Ctl* ctl;
+  double* partials;      // [4][kMaxGrid]
+  uint32_t* slice_w;     // width | overflow flag
+  int32_t* slice_ptr;    // [nslices + 1] element offsets
+  int32_t* scol;         // sliced column indices
+  float* sv32;           // sliced values, single
+  double* sv64;          // sliced values, double
+  float *b32, *x32, *r32, *d32a, *d32b, *q32;
+  double *r64, *d64, *q64;
+  int32_t *dist, *dist2, *fq0, *fq1, *label;
+  unsigned long long* ckey;  // per-component farthest-vertex keys
+  size_t bytes;
+};
+
+// ---------------------------------------------------------------------------------------
+// Small device helpers
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void set_status(Ctl* c, int s) { atomicCAS(&c->status, 0, s); }
+
+__device__ __forceinline__ int volatile_status(const Ctl* c) {
+  return *reinterpret_cast<const volatile int*>(&c->status);
+}
+
+// Streaming (read-once-per-sweep) loads for the matrix: evict-first in L1/L2.
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+
+// Grid barrier for a cooperative (co-resident) launch.  `slot` selects a
+// counter that the host zeroed before the launch; `round` counts the
+// barriers this launch has passed on that slot.  Every wait is bounded by
+// ctl->timeout_ns of device time; on timeout the status becomes
+// MPCG_ERR_TIMEOUT and the function returns false in every thread.
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, int slot, unsigned long long& round) {
+  __shared__ int s_ok;
+  __syncthreads();
+  round += 1;
+  if (threadIdx.x == 0) {
+    unsigned long long target = round * (unsigned long long)gridDim.x;
+    __threadfence();
+    red_release_add(&ctl->bar[slot], 1ull);
+    unsigned long long t0 = globaltimer();
+    int ok = 1;
+    unsigned spins = 0;
+    while (ld_acquire(&ctl->bar[slot]) < target) {
+      if ((++spins & 255u) == 0) {
+        if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
+          set_status(ctl, MPCG_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// Float-float accumulation (error-free transformations in single precision).
+// A product of two floats is split exactly into p + e; sums are carried as
+// (hi, lo).  The result is converted to double once per warp.
+// ---------------------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void ff_add_prod(FF& s, float a, float b) {
+  float p = a * b;
+  float e = __fmaf_rn(a, b, -p);             // a*b = p + e exactly
+  float t = s.hi + p;                         // two-sum(s.hi, p)
+  float bp = t - s.hi;
+  float err = (s.hi - (t - bp)) + (p - bp);
+  s.hi = t;
+  s.lo += err + e;
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  float t = a.hi + b.hi;
+  float bp = t - a.hi;
+  float err = (a.hi - (t - bp)) + (b.hi - bp);
+  float lo = a.lo + b.lo + err;
+  float hi = t + lo;                          // fast two-sum renormalisation
+  lo = lo - (hi - t);
+  return {hi, lo};
+}
+
+__device__ __forceinline__ FF ff_warp_sum(FF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    FF w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = ff_add(v, w);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum of one double per warp (`w` valid in lane 0 of
+// each warp).  Returns the total in every thread.  Uses `sm` (>= 32 doubles).
+__device__ __forceinline__ double block_sum_warp_values(double w, double* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) sm[warp] = w;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < nw ? sm[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) sm[32] = t;
+  }
+  __syncthreads();
+  return sm[32];
+}
+
+// Sum of `count` doubles in global memory, identical in every block that
+// calls it (fixed assignment and tree order).  Plain loads: the caller has
+// passed a grid barrier after the values were written.
+__device__ __forceinline__ double block_sum_global(const double* v, int count, double* sm) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) s += v[i];
+  s = warp_sum(s);
+  return block_sum_warp_values(s, sm);
+}
+
+// Key for the farthest-vertex choice of 2BFS: larger distance first, then
+// smaller vertex index.
+__device__ __forceinline__ unsigned long long far_key(int dist, int v) {
+  return ((unsigned long long)(unsigned)dist << 32) | (unsigned long long)(0xffffffffu - (unsigned)v);
+}
+__device__ __forceinline__ int far_key_vertex(unsigned long long k) {
+  return (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
+}
+
+}  // namespace mpcg

@@ -1,0 +1,54 @@
+// internal.h -- host-side interfaces between the translation units of libmpcg.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mpcg {
+
+// Layout parameters that depend only on (n, nnz): rows per slice is fixed at
+// 32; a slice stores at most `wcap` entries per row in the sliced arrays,
+// and the rest of a longer row is read from the caller's CSR.
+struct Dims {
+  int n, nnz, nslices, wcap;
+  long long pcap;  // capacity of the sliced arrays (elements)
+};
+
+bool dims_for(int n, int nnz, Dims* d);
+size_t carve(const Dims& d, char* base, Ws* ws);  // base == nullptr: size only
+
+struct Launch {
+  Dims d;
+  Ws ws;
+  const mpcg_csr_t* A;
+  cudaStream_t st;
+  int grid;  // persistent grid blocks
+};
+
+int persistent_grid(const void* kernel, int threads, int requested);
+
+// prep.cu
+cudaError_t launch_init(const Launch& L, const mpcg_options_t& o, int fp64_only);
+cudaError_t launch_prep(const Launch& L, const double* b);
+cudaError_t launch_finalize(const Launch& L, mpcg_result_t* res, mpcg_features_t* feat);
+
+// cg.cu
+enum Cg32Mode { kCgK0 = 0, kCgToEps1 = 1, kCgContinue = 2 };
+cudaError_t launch_cg32(const Launch& L, int mode, int slot);
+cudaError_t launch_cg64(const Launch& L, const double* b, double* x, int from_zero, int slot);
+cudaError_t launch_spmv(const Launch& L, int fp32, const void* x, void* y);
+const void* cg32_kernel();
+const void* cg64_kernel();
+
+// bfs.cu
+cudaError_t launch_pseudo_diameter(const Launch& L, int first_slot);
+cudaError_t launch_bfs_only(const Launch& L, int src, int32_t* dist, int slot);
+cudaError_t launch_copy_pdiam(const Launch& L, int32_t* out);
+const void* bfs_kernel();
+const void* cc_kernel();
+
+// knn.cu
+cudaError_t launch_knn(cudaStream_t st, const double* feat4, const mpcg_sample_t& S,
+                       const mpcg_options_t& o, Ctl* ctl, double* eps1_out, int32_t* cls_out);
+
+}  // namespace mpcg

@@ -1,0 +1,288 @@
+"""Python binding of libmpcg (include/mpcg.h): ctypes argument marshalling only.
+
+Device arrays are torch CUDA tensors; their raw pointers and the current CUDA
+stream are handed to the C ABI.  Every step of the solver runs in the CUDA
+kernels of libmpcg.so; this module holds no numerical code and no fallback:
+if the library is missing it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpcg.so")
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+WARN_EPS1_NOT_REACHED = 1
+WARN_TRUE_RESID_RESTARTED = 2
+ERR_INVALID_ARG = -1
+ERR_WORKSPACE = -2
+ERR_BREAKDOWN = -3
+ERR_NAN = -4
+ERR_NOT_CONVERGED = -5
+ERR_TIMEOUT = -6
+ERR_CUDA = -7
+KNN_MAX_SAMPLE = 65536
+KNN_MAX_K = 64
+
+
+class CsrDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("row_ptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class Features(C.Structure):
+    _fields_ = [("n", C.c_double), ("m", C.c_double), ("pdiam", C.c_double), ("v", C.c_double),
+                ("k0_done", C.c_int32), ("status", C.c_int32)]
+
+
+class SampleDesc(C.Structure):
+    _fields_ = [("feat", C.c_void_p), ("cls", C.c_void_p), ("count", C.c_int32),
+                ("fmin", C.c_double * 4), ("fmax", C.c_double * 4)]
+
+
+class Options(C.Structure):
+    _fields_ = [("eps1", C.c_double), ("eps2", C.c_double), ("k0", C.c_int32),
+                ("knn_k", C.c_int32), ("weighted", C.c_int32), ("tol_relative", C.c_int32),
+                ("max_it_fp32", C.c_int32), ("max_it_fp64", C.c_int32),
+                ("max_true_restarts", C.c_int32), ("feat_mask", C.c_uint32),
+                ("fp64_only", C.c_int32), ("grid_blocks", C.c_int32), ("timeout_ms", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n1", C.c_int32), ("n2", C.c_int32), ("cls", C.c_int32),
+                ("k0_done", C.c_int32), ("restarts", C.c_int32), ("eps1", C.c_double),
+                ("true_rel_resid", C.c_double), ("pdiam", C.c_double), ("v", C.c_double),
+                ("res_fp32", C.c_double), ("res_fp64", C.c_double),
+                ("t_start_ns", C.c_uint64), ("t_features_ns", C.c_uint64),
+                ("t_fp32_ns", C.c_uint64), ("t_fp64_ns", C.c_uint64), ("t_end_ns", C.c_uint64)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["ms_features"] = (self.t_features_ns - self.t_start_ns) / 1e6
+        d["ms_fp32"] = (self.t_fp32_ns - self.t_features_ns) / 1e6
+        d["ms_fp64"] = (self.t_fp64_ns - self.t_fp32_ns) / 1e6
+        d["ms_total"] = (self.t_end_ns - self.t_start_ns) / 1e6
+        return d
+
+
+SYMBOLS = ("mpcg_options_default", "mpcg_status_string", "mpcg_workspace_bytes", "mpcg_features",
+           "mpcg_choose_eps1", "mpcg_solve", "mpcg_batch_workspace_bytes", "mpcg_solve_batch",
+           "mpcg_spmv", "mpcg_bfs", "mpcg_pseudo_diameter")
+
+
+def load(path: str = LIB_PATH):
+    """Load libmpcg.so and declare the C signatures.  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmpcg.so is not built ({path}); run "
+                               "paper_2412_08059_gb300.build.build() first")
+        L = C.CDLL(path)
+        P, I32, SZ = C.c_void_p, C.c_int32, C.c_size_t
+        L.mpcg_options_default.restype = Options
+        L.mpcg_options_default.argtypes = []
+        L.mpcg_status_string.restype = C.c_char_p
+        L.mpcg_status_string.argtypes = [I32]
+        L.mpcg_workspace_bytes.restype = SZ
+        L.mpcg_workspace_bytes.argtypes = [I32, I32, C.POINTER(Options)]
+        L.mpcg_features.restype = I32
+        L.mpcg_features.argtypes = [C.POINTER(CsrDesc), P, C.POINTER(Options), P, SZ, P, P]
+        L.mpcg_choose_eps1.restype = I32
+        L.mpcg_choose_eps1.argtypes = [P, C.POINTER(SampleDesc), C.POINTER(Options), P, P, P]
+        L.mpcg_solve.restype = I32
+        L.mpcg_solve.argtypes = [C.POINTER(CsrDesc), P, P, C.POINTER(SampleDesc),
+                                 C.POINTER(Options), P, SZ, P, P]
+        L.mpcg_batch_workspace_bytes.restype = SZ
+        L.mpcg_batch_workspace_bytes.argtypes = [I32, P, P, C.POINTER(Options)]
+        L.mpcg_solve_batch.restype = I32
+        L.mpcg_solve_batch.argtypes = [I32, P, P, P, C.POINTER(SampleDesc), C.POINTER(Options),
+                                       P, SZ, P, P]
+        L.mpcg_spmv.restype = I32
+        L.mpcg_spmv.argtypes = [C.POINTER(CsrDesc), I32, P, P, P, SZ, P]
+        L.mpcg_bfs.restype = I32
+        L.mpcg_bfs.argtypes = [C.POINTER(CsrDesc), I32, P, P, SZ, P]
+        L.mpcg_pseudo_diameter.restype = I32
+        L.mpcg_pseudo_diameter.argtypes = [C.POINTER(CsrDesc), P, P, SZ, P]
+        _lib = L
+        return L
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def status_string(st: int) -> str:
+    return load().mpcg_status_string(st).decode()
+
+
+def options(**kw) -> Options:
+    o = load().mpcg_options_default()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _check(st: int, what: str):
+    if st != OK:
+        raise RuntimeError(f"{what}: {status_string(st)} ({st})")
+
+
+class DeviceCSR:
+    """A CSR matrix held in torch CUDA tensors (int32 row_ptr/col, float64 val)."""
+
+    def __init__(self, row_ptr, col, val, device="cuda"):
+        self.row_ptr = torch.as_tensor(row_ptr, dtype=torch.int32, device=device).contiguous()
+        self.col = torch.as_tensor(col, dtype=torch.int32, device=device).contiguous()
+        self.val = torch.as_tensor(val, dtype=torch.float64, device=device).contiguous()
+        self.n = self.row_ptr.numel() - 1
+        self.nnz = self.col.numel()
+        self.desc = CsrDesc(self.n, self.nnz, self.row_ptr.data_ptr(), self.col.data_ptr(),
+                            self.val.data_ptr())
+
+    @classmethod
+    def from_host(cls, A, device="cuda"):
+        return cls(torch.from_numpy(A.row_ptr), torch.from_numpy(A.col), torch.from_numpy(A.val),
+                   device)
+
+
+class DeviceSample:
+    """A labelled kNN sample in device memory (raw features [count, 4], int8 classes)."""
+
+    def __init__(self, feat, cls, fmin=None, fmax=None, device="cuda"):
+        f = torch.as_tensor(feat, dtype=torch.float64).reshape(-1, 4)
+        self.feat = f.to(device).contiguous()
+        self.cls = torch.as_tensor(cls, dtype=torch.int8).to(device).contiguous()
+        fmin = f.min(dim=0).values.tolist() if fmin is None else list(map(float, fmin))
+        fmax = f.max(dim=0).values.tolist() if fmax is None else list(map(float, fmax))
+        self.desc = SampleDesc(self.feat.data_ptr(), self.cls.data_ptr(), f.shape[0],
+                               (C.c_double * 4)(*fmin), (C.c_double * 4)(*fmax))
+
+
+def workspace_bytes(n: int, nnz: int) -> int:
+    return int(load().mpcg_workspace_bytes(n, nnz, None))
+
+
+def workspace(n: int, nnz: int, device="cuda") -> torch.Tensor:
+    """A device byte buffer large enough for (n, nnz), base 256-byte aligned."""
+    nb = workspace_bytes(n, nnz)
+    if nb == 0:
+        raise ValueError("invalid sizes")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def _ws_for(A: DeviceCSR, ws):
+    return workspace(A.n, A.nnz, A.val.device) if ws is None else ws
+
+
+def result_buffer(count: int = 1, device="cuda") -> torch.Tensor:
+    return torch.zeros(count * C.sizeof(Result), dtype=torch.uint8, device=device)
+
+
+def read_results(buf: torch.Tensor, count: int = 1) -> list[dict]:
+    raw = bytes(buf.cpu().numpy())
+    sz = C.sizeof(Result)
+    return [Result.from_buffer_copy(raw[i * sz:(i + 1) * sz]).as_dict() for i in range(count)]
+
+
+def solve_async(A: DeviceCSR, b: torch.Tensor, x: torch.Tensor, opts: Options, ws: torch.Tensor,
+                res: torch.Tensor, sample: DeviceSample | None = None, stream=None) -> None:
+    """Enqueue mpcg_solve on the stream; no host synchronisation."""
+    st = load().mpcg_solve(C.byref(A.desc), _ptr(b), _ptr(x),
+                           C.byref(sample.desc) if sample is not None else None, C.byref(opts),
+                           _ptr(ws), ws.numel(), _ptr(res), _stream(stream))
+    _check(st, "mpcg_solve")
+
+
+def solve(A: DeviceCSR, b: torch.Tensor, sample: DeviceSample | None = None, ws=None, **kw):
+    """mpcg_solve; returns (x, result dict) after synchronising."""
+    x = torch.empty(A.n, dtype=torch.float64, device=b.device)
+    res = result_buffer(1, b.device)
+    solve_async(A, b, x, options(**kw), _ws_for(A, ws), res, sample)
+    torch.cuda.synchronize(b.device)
+    return x, read_results(res)[0]
+
+
+def features(A: DeviceCSR, b: torch.Tensor, ws=None, **kw) -> dict:
+    out = torch.zeros(C.sizeof(Features), dtype=torch.uint8, device=b.device)
+    w = _ws_for(A, ws)
+    st = load().mpcg_features(C.byref(A.desc), _ptr(b), C.byref(options(**kw)), _ptr(w),
+                              w.numel(), _ptr(out), _stream())
+    _check(st, "mpcg_features")
+    f = Features.from_buffer_copy(bytes(out.cpu().numpy()))
+    return {k: getattr(f, k) for k, _ in f._fields_}
+
+
+def choose_eps1(feat4, sample: DeviceSample, **kw):
+    """kNN on a feature vector (n, m, l~, v) given as 4 numbers; returns (eps1, t)."""
+    f = Features(*[float(v) for v in feat4], 0, 0)
+    fdev = torch.frombuffer(bytearray(bytes(f)), dtype=torch.uint8).to("cuda")
+    eps = torch.zeros(1, dtype=torch.float64, device="cuda")
+    cls = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = load().mpcg_choose_eps1(_ptr(fdev), C.byref(sample.desc), C.byref(options(**kw)),
+                                 _ptr(eps), _ptr(cls), _stream())
+    _check(st, "mpcg_choose_eps1")
+    return float(eps.item()), int(cls.item())
+
+
+def spmv(A: DeviceCSR, x: torch.Tensor, ws=None) -> torch.Tensor:
+    fp32 = x.dtype == torch.float32
+    y = torch.empty_like(x)
+    w = _ws_for(A, ws)
+    st = load().mpcg_spmv(C.byref(A.desc), int(fp32), _ptr(x), _ptr(y), _ptr(w), w.numel(),
+                          _stream())
+    _check(st, "mpcg_spmv")
+    return y
+
+
+def bfs(A: DeviceCSR, src: int, ws=None) -> torch.Tensor:
+    dist = torch.empty(A.n, dtype=torch.int32, device=A.val.device)
+    w = _ws_for(A, ws)
+    st = load().mpcg_bfs(C.byref(A.desc), int(src), _ptr(dist), _ptr(w), w.numel(), _stream())
+    _check(st, "mpcg_bfs")
+    return dist
+
+
+def pseudo_diameter(A: DeviceCSR, ws=None) -> tuple[int, int]:
+    out = torch.zeros(2, dtype=torch.int32, device=A.val.device)
+    w = _ws_for(A, ws)
+    st = load().mpcg_pseudo_diameter(C.byref(A.desc), _ptr(out), _ptr(w), w.numel(), _stream())
+    _check(st, "mpcg_pseudo_diameter")
+    o = out.cpu().tolist()
+    return o[0], o[1]
+
+
+def solve_batch_async(mats: list[DeviceCSR], bs: list, xs: list, opts: Options,
+                      ws: torch.Tensor, res: torch.Tensor, sample: DeviceSample | None = None,
+                      stream=None) -> None:
+    n = len(mats)
+    descs = (CsrDesc * n)(*[m.desc for m in mats])
+    bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    st = load().mpcg_solve_batch(n, descs, bp, xp,
+                                 C.byref(sample.desc) if sample is not None else None,
+                                 C.byref(opts), _ptr(ws), ws.numel(), _ptr(res), _stream(stream))
+    _check(st, "mpcg_solve_batch")
+
+
+def batch_workspace_bytes(mats: list[DeviceCSR]) -> int:
+    n = len(mats)
+    ns = (C.c_int32 * n)(*[m.n for m in mats])
+    nz = (C.c_int32 * n)(*[m.nnz for m in mats])
+    return int(load().mpcg_batch_workspace_bytes(n, ns, nz, None))

@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every entry point of include/mpcg.h (CPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mpcg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpcg_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2412_08059_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mpcg_features", "mpcg_choose_eps1", "mpcg_solve", "mpcg_solve_batch",
+                     "mpcg_workspace_bytes", "mpcg_options_default"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_declares_every_symbol():
+    from paper_2412_08059_gb300 import mpcg
+    assert sorted(mpcg.SYMBOLS) == declared_functions()
+
+
+def test_host_only_entry_points(lib_path):
+    """Calls that do no device work: defaults, status strings, workspace sizes."""
+    from paper_2412_08059_gb300 import mpcg
+    mpcg.load(lib_path)
+    o = mpcg.options()
+    assert (o.eps1, o.eps2, o.k0, o.knn_k, o.weighted, o.tol_relative) == (-1.0, 1e-10, 10, 5, 1, 1)
+    assert mpcg.status_string(0) == "ok"
+    assert "workspace" in mpcg.status_string(-2)
+    assert mpcg.workspace_bytes(0, 10) == 0
+    n, nnz = 2_097_152, 14_581_760
+    wb = mpcg.workspace_bytes(n, nnz)
+    # sliced arrays (<= 32 * wcap per slice, 16 B per entry) + vectors: < 1 GB at 128^3
+    assert 16 * nnz < wb < 1_000_000_000
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle and the CUDA sources do not include or import each other."""
+    csrc = os.path.join(ROOT, "paper_2412_08059_gb300", "csrc")
+    for f in os.listdir(csrc):
+        txt = open(os.path.join(csrc, f)).read()
+        assert "oracle" not in txt.lower(), f          # no include, no shared helper
+    for f in ("mpcg.py", "build.py", "__init__.py"):
+        txt = open(os.path.join(ROOT, "paper_2412_08059_gb300", f)).read()
+        assert "import oracle" not in txt and "from oracle" not in txt
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".c", ".h", ".py")):
+            txt = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "import paper_2412_08059_gb300" not in txt
+            assert "from paper_2412_08059_gb300" not in txt
+            assert "mpcg.h" not in txt and "libmpcg.so" not in txt
