@@ -1,0 +1,489 @@
+#!/usr/bin/env python
+"""Benchmark: auto-eps1 mixed-precision CG vs pure FP64 CG on one GB300.
+
+Workload (one step): the six 128^3 7-point Laplacian systems of the 3-D family
+(shifts sigma = 0, 1e-4, 1e-2, 1; anisotropy (1, 1, eps), eps = 1e-2, 1e-3),
+x* ~ U[-1, 1] (seed 1), b = A x*, eps2 = 1e-10.  Each system is solved by
+mpcg_solve with Algorithm II: demotion and sliced layout, 2BFS, k0 = 10 FP32
+iterations and v, kNN (k = 5) over a labelled sample built beforehand on other
+grid sizes and coefficients, FP32 CG to eps1, FP64 restart to eps2, true
+residual.  value = solves per second over all ranks (inputs resident in HBM).
+
+Also reported: the same systems by pure FP64 CG (the baseline), a fixed-eps1
+sweep 1e-2..1e-7, the end-to-end rate with host buffers, the HBM roofline of
+the dominant kernel, and the CPU oracle timed on the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("time-to-solution & equiv-FP64-iters/s, mixed vs pure-FP64 CG on 1 GB300 at "
+          "eps2=1e-10; HBM %")
+UNIT = "solves/s"
+KERNELS_PER_SOLVE_AUTO = 18   # kernels one Algorithm II solve launches
+KERNELS_PER_SOLVE_FP64 = 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--size", type=int, default=128)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sample", default=None, help="load a kNN sample (json) instead of building")
+    ap.add_argument("--save-sample", default=None)
+    return ap.parse_args()
+
+
+def workload_config(size):
+    n = size ** 3
+    nnz = 7 * n - 6 * size * size
+    return {"workload": f"lap3d-{size}^3 x6 (sigma 0/1e-4/1e-2/1; aniso eps 1e-2/1e-3)",
+            "n": n, "nnz_per_system": nnz, "systems": 6, "eps2": 1e-10, "k0": 10, "knn_k": 5,
+            "rhs": "x* ~ U[-1,1] seed 1, b = A x*", "parallelism": "replicas",
+            "l2": "inputs larger than L2 (each system: %.0f MB of CSR in HBM)" % (
+                (12 * nnz + 4 * (n + 1)) / 1e6)}
+
+
+def algorithmic_bytes(n, nnz, p):
+    """Per CG iteration: the matrix once, row offsets, x, r, d read and written once."""
+    return nnz * (p + 4) + 4 * (n + 1) + 6 * p * n
+
+
+# ------------------------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ------------------------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (bounded sample, one core)
+# ------------------------------------------------------------------------------------------
+def oracle_costs(size, iters=10):
+    """Live per-iteration costs of the oracle on the sigma = 0 system."""
+    import oracle
+    import synth
+    oracle.build()
+    A = synth.laplacian_3d(size)
+    _, b = synth.rhs(A, 1)
+    t0 = time.perf_counter()
+    oracle.pseudo_diameter(A)
+    t_2bfs = time.perf_counter() - t0
+
+    def timed(fn, k):
+        t = time.perf_counter()
+        fn(A, b, 0.0, max_it=k)
+        return time.perf_counter() - t
+    base32 = timed(oracle.cg32, 0)
+    t32 = (timed(oracle.cg32, iters) - base32) / iters
+    base64 = timed(oracle.cg64, 0)
+    t64 = (timed(oracle.cg64, iters) - base64) / iters
+    return {"t_2bfs": t_2bfs, "t_setup32": base32, "t_setup64": base64, "t_it32": t32,
+            "t_it64": t64, "sample_s": t_2bfs + base32 + base64 + (t32 + t64) * iters + base32
+            + base64}
+
+
+def oracle_rate(costs, size):
+    """Solves/s of the oracle's mixed method at its best eps1 per system (scaled from
+    the bounded sample by the oracle's own iteration counts)."""
+    path = os.path.join(ROOT, "oracle", "data", f"lap3d{size}_counts.json")
+    with open(path) as f:
+        counts = json.load(f)
+    total = 0.0
+    for s in counts["systems"]:
+        best = min(costs["t_setup32"] + costs["t_setup64"] + v["n1"] * costs["t_it32"]
+                   + v["n2"] * costs["t_it64"] for v in s["sweep"].values())
+        total += costs["t_2bfs"] + best
+    nsys = len(counts["systems"])
+    return nsys / total, total / nsys
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    cfg = workload_config(args.size)
+    vals, walls = [], []
+    for step in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        costs = oracle_costs(args.size, iters=5)
+        rate, per_solve = oracle_rate(costs, args.size)
+        if step >= args.warmup:
+            vals.append(rate)
+            walls.append(time.perf_counter() - t)
+    value = statistics.mean(vals)
+    sample = ("per step: 2BFS + 5 FP32 + 5 FP64 oracle iterations on the sigma=0 128^3 system "
+              "(%.1f s wall); scaled to whole solves by the oracle's own (N1, N2) at its best "
+              "eps1 per system (oracle/data/lap3d%d_counts.json)" % (statistics.mean(walls),
+                                                                    args.size))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * cfg["systems"] / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# Native arm
+# ------------------------------------------------------------------------------------------
+def native_arm(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2412_08059_gb300 import build as pkg_build
+    from paper_2412_08059_gb300 import mpcg, sample
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0:
+        pkg_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    mpcg.load()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- inputs in HBM ----
+    systems = []
+    for name, A, xs, b in synth.lap3d_workload(args.size):
+        systems.append({"name": name, "A": A, "dA": mpcg.DeviceCSR.from_host(A, dev),
+                        "db": torch.from_numpy(b).to(dev), "xs": xs, "b": b,
+                        "x": torch.empty(A.n, dtype=torch.float64, device=dev)})
+    n, nnz = systems[0]["A"].n, systems[0]["A"].nnz
+    nsys = len(systems)
+    ws = mpcg.workspace(n, nnz, dev)
+    res = mpcg.result_buffer(nsys, dev)
+    rsz = res.numel() // nsys
+    res_views = [res[i * rsz:(i + 1) * rsz] for i in range(nsys)]
+
+    # ---- labelled kNN sample (Sec. 11.1), built on other systems of the family ----
+    t = time.time()
+    if args.sample:
+        feat, cls, _ = sample.load(args.sample)
+        sample_desc = f"loaded {args.sample}"
+    else:
+        feat, cls, recs = sample.build(synth.lap3d_training(), device=dev)
+        sample_desc = (f"{len(cls)} training systems (sizes 72..152, other sigma/eps), labels = "
+                       "argmin omega*N1 + N2 with the measured per-matrix omega")
+        if args.save_sample and rank == 0:
+            sample.save(args.save_sample, feat, cls, recs, {"size": args.size})
+    t_sample = time.time() - t
+    S = mpcg.DeviceSample(feat, cls, device=dev)
+    o_auto = mpcg.options()
+    o_fp64 = mpcg.options(fp64_only=1)
+
+    def step(opts):
+        for i, s in enumerate(systems):
+            mpcg.solve_async(s["dA"], s["db"], s["x"], opts, ws, res_views[i], S)
+
+    visible = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    gpu_id = visible[local_rank] if local_rank < len(visible) else str(local_rank)
+
+    def timed(opts, steps, warmup, clocks=False):
+        for _ in range(warmup):
+            step(opts)
+        torch.cuda.synchronize()
+        barrier()
+        ck = Clocks(gpu_id) if clocks else None
+        if ck:
+            ck.start()
+            time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step(opts)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        clk = ck.stop() if ck else None
+        if world > 1:
+            tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms, mpcg.read_results(res, nsys), clk
+
+    ms_auto, r_auto, clocks = timed(o_auto, args.steps, args.warmup, clocks=True)
+    ms_fp64, r_fp64, _ = timed(o_fp64, args.steps, max(1, args.warmup // 2))
+    for r in r_auto + r_fp64:
+        if r["status"] < 0:
+            raise RuntimeError(f"solve failed: {r}")
+    value = world * args.steps * nsys / (ms_auto / 1000.0)
+    value_fp64 = world * args.steps * nsys / (ms_fp64 / 1000.0)
+
+    # ---- per system: time to solution, equivalent FP64 iterations, E (Eqs. 4, 12) ----
+    B32 = algorithmic_bytes(n, nnz, 4)
+    B64 = algorithmic_bytes(n, nnz, 8)
+    per = []
+    for s, ra, rd in zip(systems, r_auto, r_fp64):
+        n1c = ra["n1"] - ra["k0_done"]
+        t_sp = ra["ms_fp32"] / max(1, n1c)
+        t_dp = rd["ms_fp64"] / max(1, rd["n2"])
+        omega = t_sp / t_dp
+        I3 = ra["n1"] / 3.0 + ra["n2"]
+        Im = omega * ra["n1"] + ra["n2"]
+        err = float(np.linalg.norm(s["x"].cpu().numpy() - s["xs"]) / np.linalg.norm(s["xs"]))
+        per.append({"name": s["name"], "n1": ra["n1"], "n2": ra["n2"], "eps1": ra["eps1"],
+                    "cls": ra["cls"], "pdiam": ra["pdiam"], "v": round(ra["v"], 6),
+                    "n_dp": rd["n2"], "ms_mixed": round(ra["ms_total"], 3),
+                    "ms_fp64": round(rd["ms_total"], 3), "ms_features": round(ra["ms_features"], 3),
+                    "ms_stage1": round(ra["ms_fp32"], 3), "ms_stage2": round(ra["ms_fp64"], 3),
+                    "omega_measured": round(omega, 4),
+                    "E_omega_1_3_pct": round(100 * (1 - I3 / rd["n2"]), 2),
+                    "E_omega_measured_pct": round(100 * (1 - Im / rd["n2"]), 2),
+                    "stage1_GBps": round(B32 * n1c / (ra["ms_fp32"] * 1e-3) / 1e9, 1) if n1c else None,
+                    "stage2_GBps": round(B64 * (ra["n2"] + 2) / (ra["ms_fp64"] * 1e-3) / 1e9, 1),
+                    "true_rel_resid": ra["true_rel_resid"], "fp64_true_rel_resid": rd["true_rel_resid"],
+                    "err_vs_xstar": err, "status": ra["status"]})
+    tot = lambda k: sum(p[k] for p in per)
+    eq_iters_13 = sum(p["n1"] / 3.0 + p["n2"] for p in per) * args.steps * world
+    eq_iters_m = sum(p["omega_measured"] * p["n1"] + p["n2"] for p in per) * args.steps * world
+
+    # ---- fixed-eps1 sweep (config: eps1 1e-2 .. 1e-7 vs auto) ----
+    sweep = None
+    if not args.no_sweep:
+        sweep = {}
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        for i, s in enumerate(systems):
+            row = {}
+            for tcls in range(2, 8):
+                o = mpcg.options(eps1=float(f"1e-{tcls}"))
+                e0.record()
+                mpcg.solve_async(s["dA"], s["db"], s["x"], o, ws, res_views[i], S)
+                e1.record()
+                torch.cuda.synchronize()
+                r = mpcg.read_results(res_views[i])[0]
+                row[f"1e-{tcls}"] = {"ms": round(e0.elapsed_time(e1), 3), "n1": r["n1"], "n2": r["n2"]}
+            best = min(row, key=lambda k: row[k]["ms"])
+            sweep[s["name"]] = {"best_eps1": best, "best_ms": row[best]["ms"], "runs": row}
+
+    # ---- roofline of the dominant kernel ----
+    share = {"stage1 (k_cg32)": tot("ms_stage1"), "stage2 (k_cg64)": tot("ms_stage2"),
+             "features": tot("ms_features")}
+    dominant = max(share, key=share.get)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+        peak_src = "measured"
+    # CUDA-event durations of the two CG kernels: a stage-1-only solve (set-up + k_cg32
+    # + promote) and a pure-FP64 solve (set-up + k_cg64), each minus the set-up alone.
+    s0 = systems[0]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ytmp = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def ev_ms(fn, reps=3):
+        vals = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            vals.append(e0.elapsed_time(e1))
+        return statistics.median(vals)
+    setup_ms = ev_ms(lambda: mpcg.spmv(s0["dA"], s0["db"], ws))
+    o_s1 = mpcg.options(eps1=1e-7, stage1_only=1)
+    k32_ms = ev_ms(lambda: mpcg.solve_async(s0["dA"], s0["db"], ytmp, o_s1, ws, res_views[0])) - setup_ms
+    r_s1 = mpcg.read_results(res_views[0])[0]
+    k64_ms = ev_ms(lambda: mpcg.solve_async(s0["dA"], s0["db"], ytmp, o_fp64, ws, res_views[0])) - setup_ms
+    r_d = mpcg.read_results(res_views[0])[0]
+    k32 = {"kernel": "k_cg32", "bytes_per_launch": B32 * r_s1["n1"], "ms": k32_ms,
+           "iters": r_s1["n1"]}
+    k64 = {"kernel": "k_cg64", "bytes_per_launch": B64 * (r_d["n2"] + 2), "ms": k64_ms,
+           "iters": r_d["n2"]}
+    dk = k64 if "k_cg64" in dominant else k32
+    achieved = dk["bytes_per_launch"] / (dk["ms"] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": dk["kernel"], "peak_source": peak_src,
+                "time_share_in_step": {k: round(v / sum(share.values()), 3) for k, v in share.items()},
+                "per_kernel": {k["kernel"]: {"GBps": round(k["bytes_per_launch"] / (k["ms"] * 1e-3) / 1e9, 1),
+                                             "frac": round(k["bytes_per_launch"] / (k["ms"] * 1e-3) / 1e9 / peak, 4),
+                                             "ms": round(k["ms"], 3), "iters": k["iters"],
+                                             "algorithmic_bytes_per_iter": B32 if k is k32 else B64}
+                               for k in (k32, k64)}}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        pinned = []
+        for s in systems:
+            A = s["A"]
+            pinned.append({"rp": torch.from_numpy(A.row_ptr).pin_memory(),
+                           "col": torch.from_numpy(A.col).pin_memory(),
+                           "val": torch.from_numpy(A.val).pin_memory(),
+                           "b": torch.from_numpy(s["b"]).pin_memory(),
+                           "x": torch.empty(A.n, dtype=torch.float64).pin_memory(),
+                           "res": torch.empty(rsz, dtype=torch.uint8).pin_memory()})
+        dbufs = [mpcg.DeviceCSR(torch.empty_like(p["rp"], device=dev), torch.empty_like(p["col"], device=dev),
+                                torch.empty_like(p["val"], device=dev), dev) for p in pinned]
+        dbs = [torch.empty_like(p["b"], device=dev) for p in pinned]
+        h2d = sum(p["rp"].nbytes + p["col"].nbytes + p["val"].nbytes + p["b"].nbytes for p in pinned)
+        d2h = sum(p["x"].nbytes + p["res"].nbytes for p in pinned)
+
+        def e2e_step():
+            for i, (p, dA, db) in enumerate(zip(pinned, dbufs, dbs)):
+                dA.row_ptr.copy_(p["rp"], non_blocking=True)
+                dA.col.copy_(p["col"], non_blocking=True)
+                dA.val.copy_(p["val"], non_blocking=True)
+                db.copy_(p["b"], non_blocking=True)
+                mpcg.solve_async(dA, db, systems[i]["x"], o_auto, ws, res_views[i], S)
+                p["x"].copy_(systems[i]["x"], non_blocking=True)
+                p["res"].copy_(res_views[i], non_blocking=True)
+        for _ in range(max(1, args.warmup // 2)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t
+        if world > 1:
+            tt = torch.tensor([wall], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            wall = float(tt.item())
+        e2e = {"value": world * args.steps * nsys / wall, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "timing": "host wall clock around K steps incl. pinned H2D of CSR+b and D2H of x+result"}
+
+    # ---- CPU oracle baseline (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        costs = oracle_costs(args.size, iters=10)
+        rate, per_solve = oracle_rate(costs, args.size)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": ("2BFS + 10 FP32 + 10 FP64 oracle iterations on the sigma=0 128^3 system "
+                          "(%.1f s of CPU); scaled to whole solves by the oracle's own (N1, N2) at "
+                          "its best eps1 per system" % costs["sample_s"]),
+               "per_iteration_ms": {"fp32": round(costs["t_it32"] * 1e3, 2),
+                                    "fp64": round(costs["t_it64"] * 1e3, 2)},
+               "host_cores_available": os.cpu_count()}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_auto / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": workload_config(args.size),
+                "fp64_baseline": {"value": value_fp64, "unit": UNIT,
+                                  "ms_per_step": ms_fp64 / args.steps,
+                                  "speedup_mixed_over_fp64": value / value_fp64},
+                "time_to_solution_ms": {"mixed_auto": round(ms_auto / args.steps / nsys, 3),
+                                        "fp64": round(ms_fp64 / args.steps / nsys, 3)},
+                "equiv_fp64_iters_per_s": {"omega_1_3": eq_iters_13 / (ms_auto / 1000.0),
+                                           "omega_measured": eq_iters_m / (ms_auto / 1000.0),
+                                           "fp64": sum(p["n_dp"] for p in per) * args.steps * world
+                                           / (ms_fp64 / 1000.0)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": KERNELS_PER_SOLVE_AUTO * nsys * args.steps,
+                "clocks": clocks, "systems": per, "eps1_sweep": sweep,
+                "sample": {"desc": sample_desc, "seconds_to_build": round(t_sample, 1),
+                           "labels": np.bincount(cls, minlength=8)[2:].tolist()}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        native_arm(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

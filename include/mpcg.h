@@ -113,7 +113,8 @@ typedef struct {
   int32_t fp64_only;         /* 1: pure FP64 CG from x0 = 0 (the baseline); no stage 1 */
   int32_t grid_blocks;       /* persistent grid size; 0 = one full wave of the device */
   int32_t timeout_ms;        /* limit of every device-side wait (default 20000) */
-  int32_t reserved[5];
+  int32_t stage1_only;       /* 1: stop after the single-precision stage; x = float64(x~) */
+  int32_t reserved[4];
 } mpcg_options_t;
 
 /* Result record, written by the device at the end of the call's work into

@@ -155,7 +155,11 @@ int32_t mpcg_solve(const mpcg_csr_t* A, const double* b, double* x, const mpcg_s
       if ((e = launch_cg32(L, kCgToEps1, kSlotCg32)) != cudaSuccess) return cuda_status(e);
     }
   }
-  if ((e = launch_cg64(L, b, x, fp64_only, kSlotCg64)) != cudaSuccess) return cuda_status(e);
+  if (opts->stage1_only && !fp64_only) {
+    if ((e = launch_promote(L, x)) != cudaSuccess) return cuda_status(e);
+  } else {
+    if ((e = launch_cg64(L, b, x, fp64_only, kSlotCg64)) != cudaSuccess) return cuda_status(e);
+  }
   return cuda_status(launch_finalize(L, res, nullptr));
 }
 

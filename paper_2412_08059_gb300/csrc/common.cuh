@@ -48,7 +48,7 @@ struct Ctl {
   int ccflag[2];
   int cls;
   // device clock marks (ns)
-  unsigned long long t_start, t_features, t_fp32, t_fp64, t_end;
+  unsigned long long t_start, t_prep, t_features, t_fp32, t_fp64, t_end;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -104,27 +104,30 @@ __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p);
 // barriers this launch has passed on that slot.  Every wait is bounded by
 // ctl->timeout_ns of device time; on timeout the status becomes
 // MPCG_ERR_TIMEOUT and the function returns false in every thread.
+//
+// Ordering: the block's writes are ordered before thread 0's release-add by
+// the CTA barrier; thread 0's acquire load, followed by the second CTA
+// barrier, orders every thread's later loads after all blocks' writes.
 __device__ __forceinline__ bool grid_barrier(Ctl* ctl, int slot, unsigned long long& round) {
   __shared__ int s_ok;
   __syncthreads();
   round += 1;
   if (threadIdx.x == 0) {
-    unsigned long long target = round * (unsigned long long)gridDim.x;
-    __threadfence();
+    const unsigned long long target = round * (unsigned long long)gridDim.x;
     red_release_add(&ctl->bar[slot], 1ull);
-    unsigned long long t0 = globaltimer();
     int ok = 1;
-    unsigned spins = 0;
-    while (ld_acquire(&ctl->bar[slot]) < target) {
-      if ((++spins & 255u) == 0) {
-        if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
+    if (ld_acquire(&ctl->bar[slot]) < target) {
+      const unsigned long long t0 = globaltimer();
+      unsigned spins = 0;
+      while (ld_acquire(&ctl->bar[slot]) < target) {
+        if ((++spins & 1023u) == 0 &&
+            globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
           set_status(ctl, MPCG_ERR_TIMEOUT);
           ok = 0;
           break;
         }
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();

@@ -37,6 +37,7 @@ enum Cg32Mode { kCgK0 = 0, kCgToEps1 = 1, kCgContinue = 2 };
 cudaError_t launch_cg32(const Launch& L, int mode, int slot);
 cudaError_t launch_cg64(const Launch& L, const double* b, double* x, int from_zero, int slot);
 cudaError_t launch_spmv(const Launch& L, int fp32, const void* x, void* y);
+cudaError_t launch_promote(const Launch& L, double* x);
 const void* cg32_kernel();
 const void* cg64_kernel();
 

@@ -206,6 +206,7 @@ __global__ void k_bnorm_final(Ctl* c, const double* __restrict__ part, int nb) {
   double s = block_sum_global(part, nb, sm);
   if (threadIdx.x == 0) {
     double bn = sqrt(s);
+    c->t_prep = globaltimer();
     c->bnorm64 = bn;
     if (!isfinite(bn)) set_status(c, MPCG_ERR_NAN);
     else if (bn == 0.0) c->trivial = 1;
@@ -259,7 +260,8 @@ __global__ void k_finalize(const Ctl* c, mpcg_result_t* res, mpcg_features_t* fe
     res->res_fp32 = c->res32;
     res->res_fp64 = c->res64;
     res->t_start_ns = c->t_start;
-    res->t_features_ns = c->t_features ? c->t_features : c->t_start;
+    const unsigned long long t0 = c->t_prep ? c->t_prep : c->t_start;
+    res->t_features_ns = c->t_features ? c->t_features : t0;
     res->t_fp32_ns = c->t_fp32 ? c->t_fp32 : res->t_features_ns;
     res->t_fp64_ns = c->t_fp64 ? c->t_fp64 : res->t_fp32_ns;
     res->t_end_ns = now;

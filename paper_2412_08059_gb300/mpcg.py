@@ -53,7 +53,7 @@ class Options(C.Structure):
                 ("max_it_fp32", C.c_int32), ("max_it_fp64", C.c_int32),
                 ("max_true_restarts", C.c_int32), ("feat_mask", C.c_uint32),
                 ("fp64_only", C.c_int32), ("grid_blocks", C.c_int32), ("timeout_ms", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("stage1_only", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class Result(C.Structure):

@@ -323,6 +323,35 @@ def batch_family(nsys: int, seed: int = 0, n_lo: float = 1e3, n_hi: float = 2.6e
     return out
 
 
+# The 3-D 7-point family of the benchmark: (name, anisotropy eps, shift sigma).
+LAP3D_VARIANTS = (("sigma0", 1.0, 0.0), ("sigma1e-4", 1.0, 1e-4), ("sigma1e-2", 1.0, 1e-2),
+                  ("sigma1", 1.0, 1.0), ("aniso1e-2", 1e-2, 0.0), ("aniso1e-3", 1e-3, 0.0))
+
+
+def lap3d_workload(size: int = 128, seed: int = 1):
+    """The benchmark systems: every LAP3D_VARIANTS matrix on a size^3 grid with
+    x* ~ U[-1, 1] (seed) and b = A x*.  Yields (name, A, x*, b)."""
+    for name, eps, sigma in LAP3D_VARIANTS:
+        A = laplacian_3d(size, eps=eps, sigma=sigma)
+        xs, b = rhs(A, seed)
+        yield name, A, xs, b
+
+
+def lap3d_training(seed: int = 7):
+    """Training systems for a kNN sample of the 3-D family: other grid sizes and
+    other shift / anisotropy values than the benchmark systems.
+    Yields (name, A, b)."""
+    rng = np.random.default_rng(seed)
+    sizes = (72, 88, 104, 120, 136, 152)
+    kinds = (("sigma", 0.0), ("sigma", 3e-4), ("sigma", 5e-3), ("sigma", 0.3), ("aniso", 3e-2),
+             ("aniso", 3e-3))
+    for s in sizes:
+        for kind, p in kinds:
+            A = laplacian_3d(s, eps=p if kind == "aniso" else 1.0, sigma=p if kind == "sigma" else 0.0)
+            _, b = rhs(A, int(rng.integers(1, 1 << 30)))
+            yield A.name, A, b
+
+
 def build_desc(desc) -> CSR:
     fam, kw = desc
     if fam == "2d":
