@@ -27,11 +27,7 @@ bool sample_ok(const mpcg_sample_t* s) {
 }
 
 int grid_size(int requested) {
-  static const void* kernels[4] = {nullptr, nullptr, nullptr, nullptr};
-  kernels[0] = cg32_kernel();
-  kernels[1] = cg64_kernel();
-  kernels[2] = bfs_kernel();
-  kernels[3] = cc_kernel();
+  const void* kernels[2] = {bfs_kernel(), cc_kernel()};
   int g = kMaxGrid;
   for (const void* k : kernels) {
     int gk = persistent_grid(k, kCgThreads, requested);
@@ -52,8 +48,9 @@ int32_t prepare(const mpcg_csr_t* A, void* ws, size_t ws_bytes, mpcg_stream_t st
   L->d = d;
   L->A = A;
   L->st = (cudaStream_t)stream;
+  L->grid_req = grid_req;
   L->grid = grid_size(grid_req);
-  if (L->grid <= 0) return MPCG_ERR_CUDA;
+  if (L->grid <= 0 || cg_grid(grid_req) <= 0) return MPCG_ERR_CUDA;
   return MPCG_OK;
 }
 

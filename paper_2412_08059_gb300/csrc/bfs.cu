@@ -113,14 +113,37 @@ __global__ void __launch_bounds__(kCgThreads) k_bfs(BfsArgs a) {
         deg = a.rp[u + 1] - e0;
       }
       const int maxdeg = __reduce_max_sync(0xffffffffu, deg);
-      for (int k = 0; k < maxdeg; ++k) {
-        bool push = false;
-        int w = 0;
-        if (k < deg) {
-          w = a.col[e0 + k];
-          if (w != u && a.dist[w] == -1 && atomicCAS(&a.dist[w], -1, level + 1) == -1) push = true;
+      // Neighbours in groups of 8: all column loads of a group, then all
+      // claims (atomicCAS on dist), then the appends -- three dependent
+      // round trips per group instead of per neighbour.
+      for (int k0 = 0; k0 < maxdeg; k0 += 8) {
+        int w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = (k0 + j < deg) ? a.col[e0 + k0 + j] : -1;
+        bool push[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          push[j] = w[j] >= 0 && w[j] != u && atomicCAS(&a.dist[w[j]], -1, level + 1) == -1;
+        // One reservation per warp for all of its pushes of this group.
+        int mine = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mine += push[j] ? 1 : 0;
+        const int lane = threadIdx.x & 31;
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
         }
-        warp_append(push, w, out, cnt);
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total > 0) {
+          int base0 = 0;
+          if (lane == 0) base0 = atomicAdd(cnt, total);
+          int pos = __shfl_sync(0xffffffffu, base0, 0) + incl - mine;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (push[j]) out[pos++] = w[j];
+        }
       }
     }
     ++level;

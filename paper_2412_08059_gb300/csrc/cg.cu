@@ -1,21 +1,27 @@
 // cg.cu -- persistent conjugate-gradient kernels (CG procedure of Sec. 3) for
 // the two stages of Algorithm I / II.
 //
-// One cooperative launch runs a whole stage.  Every warp owns a fixed,
-// contiguous range of 32-row slices; in the SpMV each lane owns one row of a
-// slice, so a row is summed in its stored order by one thread (bit-identical
-// to a sequential fused-multiply-add chain).  The convergence test is taken
-// on the device after each grid-wide reduction, identically in every block.
-//
-// Memory-level parallelism: a warp first loads the widths and offsets of up
-// to 32 of its slices (one per lane), then streams two slices at a time with
-// fully unrolled loads of up to 8 entries per row held in registers: the
-// next slice's columns and values are in flight while the current slice's
-// gathers and FMAs run.  The per-row update phases use 16-byte vector loads.
+// One cooperative launch runs a whole stage, one block per SM.  A block
+// owns a contiguous range of 32-row slices and is warp-specialised:
+//   * a producer warp (one elected thread) streams the block's part of the
+//     sliced matrix -- columns and values, a contiguous element range --
+//     through a ring of shared-memory stages with 1-D bulk asynchronous
+//     copies (TMA engine, cp.async.bulk) completing on mbarriers.  The matrix
+//     does not change, so the producer streams it cyclically, pass after
+//     pass, and keeps prefetching the next pass while the consumers are in a
+//     grid barrier or in the per-row update phases;
+//   * consumer warps take the block's slices round-robin; in the SpMV each
+//     lane owns one row of a slice and sums it in stored order (the same
+//     chain of fused multiply-adds as a sequential loop, so the SpMV result is
+//     bit-identical), reading columns and values from shared memory and
+//     gathering the vector from L1/L2.  Consumers synchronise among
+//     themselves with a named barrier, never with the producer.
+// The convergence test is taken after each grid-wide reduction, identically
+// in every block.  Every wait is bounded in device time.
 //
 // Single-precision stage (float32(A), float32(b)), per iteration:
 //   P1  d_k = r_k + beta_k d_{k-1} formed on the fly for every gathered
-//       column and stored for the warp's own rows (double-buffered d);
+//       column and stored for the block's own rows (double-buffered d);
 //       q = A d_k; partial d_k^T q                        -> grid reduction
 //   P2  x += alpha d_k; r -= alpha q; partial r^T r          -> grid reduction
 // Dot products are accumulated as float-float sums (error-free products and
@@ -32,8 +38,30 @@
 
 namespace mpcg {
 
-constexpr int kFastW = 8;  // rows up to this width take the unrolled path
-constexpr unsigned kFull = 0xffffffffu;
+constexpr int kNC = 15;                       // consumer warps per block
+constexpr int kTmaThreads = (kNC + 1) * 32;   // + one producer warp
+constexpr int kLogCH = 12;
+constexpr int kCH = 1 << kLogCH;              // elements per streamed chunk
+constexpr int kFastW = 8;                     // rows up to this width take the unrolled path
+
+template <typename T>
+struct StageCfg;
+template <>
+struct StageCfg<float> {
+  static constexpr int kStages = 5;
+};
+template <>
+struct StageCfg<double> {
+  static constexpr int kStages = 4;
+};
+template <typename T>
+__host__ __device__ constexpr size_t stage_bytes() {
+  return (size_t)kCH * (sizeof(int32_t) + sizeof(T));
+}
+template <typename T>
+__host__ __device__ constexpr size_t ring_smem_bytes() {
+  return StageCfg<T>::kStages * stage_bytes<T>() + 2 * StageCfg<T>::kStages * 8 + 16;
+}
 
 struct CgArgs {
   Ctl* ctl;
@@ -53,50 +81,6 @@ struct CgArgs {
   double *x64, *r64, *d64, *q64;
 };
 
-// Slice range [lo, hi) of the calling warp: contiguous per warp, warps of a
-// block adjacent.
-__device__ __forceinline__ void warp_slices(int nslices, int& lo, int& hi) {
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  lo = (int)(nslices * gw / nw);
-  hi = (int)(nslices * (gw + 1) / nw);
-}
-
-// Grid-wide double sum of the block partials (the block partial is in every
-// thread).  Alternating halves of `partials`.
-__device__ __forceinline__ double grid_total(double block_part, double* partials, int& red,
-                                             Ctl* ctl, int slot, unsigned long long& round,
-                                             double* sm, bool& ok) {
-  double* buf = partials + (red & 1) * kMaxGrid;
-  ++red;
-  if (threadIdx.x == 0) buf[blockIdx.x] = block_part;
-  ok = grid_barrier(ctl, slot, round);
-  return block_sum_global(buf, gridDim.x, sm);
-}
-
-__device__ __forceinline__ double ff_block(FF v, double* sm) {
-  v = ff_warp_sum(v);
-  return block_sum_warp_values((double)v.hi + (double)v.lo, sm);
-}
-
-__device__ __forceinline__ double stop_measure(double rr, double bnorm, int rel) {
-  return rel ? sqrt(rr) / bnorm : sqrt(rr);
-}
-
-__device__ __forceinline__ bool fast_slice(uint32_t wf) {
-  return !(wf & kOverflowBit) && (int)wf <= kFastW;
-}
-
-// ---------------------------------------------------------------------------------------
-// Sliced SpMV rows, generic over the value type.  G(c) is the gathered vector
-// entry for column c (d, or r + beta d formed on the fly).
-// ---------------------------------------------------------------------------------------
-template <typename T>
-struct SliceBuf {
-  int c[kFastW];
-  T v[kFastW];
-};
-
 template <typename T>
 __device__ __forceinline__ const T* svals(const CgArgs& a);
 template <>
@@ -104,93 +88,381 @@ __device__ __forceinline__ const float* svals<float>(const CgArgs& a) { return a
 template <>
 __device__ __forceinline__ const double* svals<double>(const CgArgs& a) { return a.sv64; }
 
+__device__ __forceinline__ double stop_measure(double rr, double bnorm, int rel) {
+  return rel ? sqrt(rr) / bnorm : sqrt(rr);
+}
+
+// ---------------------------------------------------------------------------------------
+// Consumer-group synchronisation (named barrier 1, consumer warps only).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void cbar() {
+  asm volatile("bar.sync 1, %0;" ::"r"(kNC * 32) : "memory");
+}
+
+// Shared scratch of the consumer group: per-thread partials and the values
+// that thread 0 broadcasts after each reduction.  Scalars of the iteration
+// (alpha, beta, the stop test) are computed once per block by thread 0 (they
+// are the same in every block: same totals, same operations), which keeps
+// the slow FP64 units free of redundant work.
+struct CShared {
+  double part[kNC * 32];
+  float ffp[2 * kNC];
+  double rr, val;
+  float alpha, beta;
+  int dec;
+  int ok;
+};
+
+// Block partial of float-float sums, valid in thread 0 (float ops only until
+// the final conversion).
+__device__ __forceinline__ double block_ff(FF v, CShared& S) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = ff_warp_sum(v);
+  if (lane == 0) {
+    S.ffp[2 * warp] = v.hi;
+    S.ffp[2 * warp + 1] = v.lo;
+  }
+  cbar();
+  double r = 0.0;
+  if (warp == 0) {
+    FF t = lane < kNC ? FF{S.ffp[2 * lane], S.ffp[2 * lane + 1]} : FF{0.f, 0.f};
+    t = ff_warp_sum(t);
+    r = (double)t.hi + (double)t.lo;
+  }
+  return r;
+}
+
+// Block partial of per-thread doubles, valid in thread 0 (one warp adds them
+// in a fixed order).
+__device__ __forceinline__ double block_d(double p, CShared& S) {
+  const int lane = threadIdx.x & 31;
+  S.part[threadIdx.x] = p;
+  cbar();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < kNC; ++j) s += S.part[lane + 32 * j];
+    r = warp_sum(s);
+  }
+  return r;
+}
+
+// Grid barrier among the consumer groups of all blocks; bounded; also stops
+// when another block has recorded an error.
+__device__ __forceinline__ bool cgrid_barrier(Ctl* ctl, int slot, unsigned long long& round,
+                                              int* s_ok) {
+  cbar();
+  round += 1;
+  if (threadIdx.x == 0) {
+    const unsigned long long target = round * (unsigned long long)gridDim.x;
+    red_release_add(&ctl->bar[slot], 1ull);
+    int ok = 1;
+    if (ld_acquire(&ctl->bar[slot]) < target) {
+      const unsigned long long t0 = globaltimer();
+      unsigned spins = 0;
+      while (ld_acquire(&ctl->bar[slot]) < target) {
+        if ((++spins & 1023u) == 0) {
+          if (volatile_status(ctl) != 0) {
+            ok = 0;
+            break;
+          }
+          if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
+            set_status(ctl, MPCG_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    *s_ok = ok;
+  }
+  cbar();
+  return *s_ok != 0;
+}
+
+// Grid-wide sum of the block partials (block partial valid in thread 0;
+// alternating halves of `partials`).  The total is valid in thread 0; the
+// caller derives its scalars there and broadcasts them with cbar().
+__device__ __forceinline__ double cgrid_total(double block_part, double* partials, int& red,
+                                              Ctl* ctl, int slot, unsigned long long& round,
+                                              CShared& S, bool& ok) {
+  double* buf = partials + (red & 1) * kMaxGrid;
+  ++red;
+  if (threadIdx.x == 0) buf[blockIdx.x] = block_part;
+  ok = cgrid_barrier(ctl, slot, round, &S.ok);
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) s += buf[i];
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------------------
+// The streamed matrix ring.
+// ---------------------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void slice_load(const CgArgs& a, uint32_t wf, int p, SliceBuf<T>& b) {
-  if (!fast_slice(wf)) return;
-  const int w = (int)wf;
+struct Ring {
+  static constexpr int S = StageCfg<T>::kStages;
+  char* base;                   // stage s: columns at base + s*stage_bytes, values after them
+  unsigned long long* full;     // [S]
+  unsigned long long* empty;    // [S]
+  volatile int* stop;
+  int E0, E1;                   // element range of the block
+  unsigned nch;                 // chunks per pass
+  __device__ __forceinline__ const int32_t* cols(int s) const {
+    return reinterpret_cast<const int32_t*>(base + (size_t)s * stage_bytes<T>());
+  }
+  __device__ __forceinline__ const T* vals(int s) const {
+    return reinterpret_cast<const T*>(base + (size_t)s * stage_bytes<T>() + kCH * sizeof(int32_t));
+  }
+};
+
+// Producer: one thread.  Streams chunks g = 0, 1, 2, ... (chunk g % nch of the
+// block's elements) until the consumers raise `stop`; then waits for every
+// copy it issued before the block's shared memory can be released.
+template <typename T>
+__device__ void ring_producer(const CgArgs& a, Ring<T>& R) {
+  constexpr int S = Ring<T>::S;
+  if (R.nch == 0) return;
+  const unsigned long long pol = l2_policy_evict_first();
   const T* sv = svals<T>(a);
-#pragma unroll
-  for (int k = 0; k < kFastW; ++k) {
-    if (k < w) {
-      b.c[k] = ld_stream(a.scol + p + kSlice * k);
-      b.v[k] = ld_stream(sv + p + kSlice * k);
-    }
+  long long issued[S];
+  for (int s = 0; s < S; ++s) issued[s] = -1;
+  for (unsigned g = 0;; ++g) {
+    if (*R.stop) break;
+    const int st = (int)(g % S);
+    const unsigned use = g / S;
+    if (use >= 1 && !mbar_wait(&R.empty[st], (use - 1) & 1u, a.ctl, R.stop)) break;
+    const unsigned c = g % R.nch;
+    const int e = R.E0 + (int)(c << kLogCH);
+    const int cnt = min(kCH, R.E1 - e);
+    mbar_arrive_expect_tx(&R.full[st], (uint32_t)cnt * (uint32_t)(sizeof(int32_t) + sizeof(T)));
+    bulk_g2s(const_cast<int32_t*>(R.cols(st)), a.scol + e, (uint32_t)cnt * sizeof(int32_t),
+             &R.full[st], pol);
+    bulk_g2s(const_cast<T*>(R.vals(st)), sv + e, (uint32_t)cnt * sizeof(T), &R.full[st], pol);
+    issued[st] = g;
   }
+  for (int s = 0; s < S; ++s)
+    if (issued[s] >= 0) mbar_wait(&R.full[s], (unsigned)(issued[s] / S) & 1u, a.ctl, nullptr);
 }
 
-// Row i = 32 s + lane: returns sum_k v_k G(c_k) in stored order.
-template <typename T, class Gather>
-__device__ __forceinline__ T slice_row(const CgArgs& a, int i, uint32_t wf, int p,
-                                       const SliceBuf<T>& b, Gather G) {
-  T acc = (T)0;
-  if (fast_slice(wf)) {
-    const int w = (int)wf;
-#pragma unroll
-    for (int k = 0; k < kFastW; ++k)
-      if (k < w) acc = fma(b.v[k], G(b.c[k]), acc);
-  } else {
-    const int w = (int)(wf & ~kOverflowBit);
-    const T* sv = svals<T>(a);
-    for (int k = 0; k < w; ++k)
-      acc = fma(ld_stream(sv + p + kSlice * k), G(ld_stream(a.scol + p + kSlice * k)), acc);
-    if ((wf & kOverflowBit) && i < a.n) {
-      const int e1 = a.rp[i + 1];
-      for (int e = a.rp[i] + w; e < e1; ++e) acc = fma((T)a.val[e], G(a.col[e]), acc);
+// Consumer-side cursor: chunks below `waited_plus1` are known full; chunks
+// below `rel` have been released by this warp.
+struct Cursor {
+  unsigned pass_base, waited_plus1, rel;
+};
+
+// Release every chunk below g.  A chunk is released only after it has been
+// filled: the producer fills chunk h only once every warp released chunk
+// h - S, so an arrival for h always lands in the empty-barrier phase of h
+// (a warp that skips chunks would otherwise count its arrival for h towards
+// the phase of h - S while another warp still reads h - S).
+template <typename T>
+__device__ __forceinline__ bool ring_release_below(Ring<T>& R, Cursor& C, unsigned g, int lane,
+                                                   Ctl* ctl) {
+  while (C.rel < g) {
+    if (C.rel >= C.waited_plus1) {
+      if (!mbar_wait(&R.full[C.rel % Ring<T>::S], (C.rel / Ring<T>::S) & 1u, ctl, nullptr))
+        return false;
+      C.waited_plus1 = C.rel + 1;
     }
+    if (lane == 0) mbar_arrive(&R.empty[C.rel % Ring<T>::S]);
+    ++C.rel;
   }
-  return acc;
+  return true;
 }
 
-// Walk the warp's slices two at a time; Row(i, acc) consumes each row.  With
-// DB (double buffering) the next slice's loads are issued before the current
-// slice's gathers; without it only the slice metadata is preloaded.
-template <typename T, bool DB, class Gather, class Row>
-__device__ __forceinline__ void spmv_slices(const CgArgs& a, int s_lo, int s_hi, int lane,
-                                            Gather G, Row R) {
-  if (!DB) {
-    for (int cb = s_lo; cb < s_hi; cb += 32) {
-      const int cnt = min(32, s_hi - cb);
-      const uint32_t mw = lane < cnt ? a.slice_w[cb + lane] : 0u;
-      const int mp = lane < cnt ? a.slice_ptr[cb + lane] : 0;
-      for (int j = 0; j < cnt; ++j) {
-        const uint32_t wf = __shfl_sync(kFull, mw, j);
-        const int p = __shfl_sync(kFull, mp, j) + lane;
-        SliceBuf<T> A;
-        slice_load<T>(a, wf, p, A);
-        const int i = (cb + j) * kSlice + lane;
-        R(i, slice_row<T>(a, i, wf, p, A, G));
+template <typename T>
+__device__ __forceinline__ bool ring_acquire(Ring<T>& R, Cursor& C, unsigned g_lo, unsigned g_hi,
+                                             Ctl* ctl) {
+  unsigned g = C.waited_plus1 > g_lo ? C.waited_plus1 : g_lo;
+  for (; g <= g_hi; ++g)
+    if (!mbar_wait(&R.full[g % Ring<T>::S], (g / Ring<T>::S) & 1u, ctl, nullptr)) return false;
+  if (g_hi + 1 > C.waited_plus1) C.waited_plus1 = g_hi + 1;
+  return true;
+}
+
+// Chunk range [lo, hi] of a slice's k-rows (w > 0) relative to the pass.
+__device__ __forceinline__ void slice_chunks(int r0, int w, unsigned& lo, unsigned& hi) {
+  lo = (unsigned)r0 >> kLogCH;
+  hi = (unsigned)(r0 + kSlice * (w - 1)) >> kLogCH;
+}
+
+// Load the (column, value) pairs of one slice row from the ring.  A slice
+// spans at most two chunks: the stage of its first chunk and the next one.
+template <typename T>
+__device__ __forceinline__ void ring_load(const Ring<T>& R, const Cursor& C, int r0, int w,
+                                          int lane, int (&c)[kFastW], T (&v)[kFastW]) {
+  const unsigned g0 = C.pass_base + ((unsigned)r0 >> kLogCH);
+  const int st0 = (int)(g0 % Ring<T>::S);
+  const int st1 = st0 + 1 == Ring<T>::S ? 0 : st0 + 1;
+  const int off0 = (r0 & (kCH - 1)) + lane;
+  const int32_t* c0p = R.cols(st0);
+  const T* v0p = R.vals(st0);
+  if ((r0 & (kCH - 1)) + kSlice * kFastW <= kCH) {  // the slice lies in one chunk
+    const int32_t* cp = c0p + off0;
+    const T* vp = v0p + off0;
+#pragma unroll
+    for (int k = 0; k < kFastW; ++k) {
+      if (k < w) {
+        c[k] = cp[kSlice * k];
+        v[k] = vp[kSlice * k];
       }
     }
     return;
   }
-  for (int cb = s_lo; cb < s_hi; cb += 32) {
-    const int cnt = min(32, s_hi - cb);
-    const uint32_t mw = lane < cnt ? a.slice_w[cb + lane] : 0u;
-    const int mp = lane < cnt ? a.slice_ptr[cb + lane] : 0;
-    SliceBuf<T> A, B;
-    uint32_t wa = __shfl_sync(kFull, mw, 0);
-    int pa = __shfl_sync(kFull, mp, 0) + lane;
-    slice_load<T>(a, wa, pa, A);
-    for (int j = 0; j < cnt; j += 2) {
-      const bool hb = j + 1 < cnt;
-      const uint32_t wb = __shfl_sync(kFull, mw, (j + 1) & 31);
-      const int pb = __shfl_sync(kFull, mp, (j + 1) & 31) + lane;
-      if (hb) slice_load<T>(a, wb, pb, B);
-      {
-        const int i = (cb + j) * kSlice + lane;
-        R(i, slice_row<T>(a, i, wa, pa, A, G));
-      }
-      if (j + 2 < cnt) {
-        wa = __shfl_sync(kFull, mw, j + 2);
-        pa = __shfl_sync(kFull, mp, j + 2) + lane;
-        slice_load<T>(a, wa, pa, A);
-      }
-      if (hb) {
-        const int i = (cb + j + 1) * kSlice + lane;
-        R(i, slice_row<T>(a, i, wb, pb, B, G));
-      }
+  const int32_t* c1p = R.cols(st1);
+  const T* v1p = R.vals(st1);
+#pragma unroll
+  for (int k = 0; k < kFastW; ++k) {
+    if (k < w) {
+      const int off = off0 + kSlice * k;
+      const bool second = off >= kCH;
+      const int o = second ? off - kCH : off;
+      c[k] = second ? c1p[o] : c0p[o];
+      v[k] = second ? v1p[o] : v0p[o];
     }
   }
+}
+
+// Row sum of one slice row, generic width, from the ring (plus the tail of an
+// overflowing row from the caller's CSR).
+template <typename T, class Gather>
+__device__ __forceinline__ T ring_row_generic(const CgArgs& a, const Ring<T>& R, const Cursor& C,
+                                              int r0, uint32_t wf, int i, int lane, Gather G) {
+  const int w = (int)(wf & ~kOverflowBit);
+  T acc = (T)0;
+  for (int k = 0; k < w; ++k) {
+    const int rr = r0 + kSlice * k + lane;
+    const int st = (int)((C.pass_base + ((unsigned)rr >> kLogCH)) % Ring<T>::S);
+    const int off = rr & (kCH - 1);
+    acc = fma(R.vals(st)[off], G(R.cols(st)[off]), acc);
+  }
+  if ((wf & kOverflowBit) && i < a.n) {
+    const int e1 = a.rp[i + 1];
+    for (int e = a.rp[i] + w; e < e1; ++e) acc = fma((T)a.val[e], G(a.col[e]), acc);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ bool fast_w(uint32_t wf) {
+  return !(wf & kOverflowBit) && (int)wf <= kFastW;
+}
+
+// One SpMV pass over the block's slices by the consumer warps.  For every
+// row i of the block's slices (padding rows included), Rw(i, acc) receives
+// sum_k v_k G(c_k) in stored order.  A warp takes two slices (s, s + kNC) per
+// step when both fit in two chunks, so that the gathers of both rows are in
+// flight together; a step never needs more than two chunks at once (the ring
+// has at least four), which keeps the producer/consumer ring free of
+// deadlock.  Returns false if a wait failed.
+template <typename T, class Gather, class Row>
+__device__ __forceinline__ bool ring_spmv(const CgArgs& a, Ring<T>& R, Cursor& C, int S0, int S1,
+                                          Gather G, Row Rw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool ok = true;
+  for (int s0 = S0 + warp; s0 < S1; s0 += 2 * kNC) {
+    const int s1 = s0 + kNC;
+    const bool h1 = s1 < S1;
+    const uint32_t wf0 = a.slice_w[s0];
+    const uint32_t wf1 = h1 ? a.slice_w[s1] : 0u;
+    const int w0 = (int)(wf0 & ~kOverflowBit), w1 = (int)(wf1 & ~kOverflowBit);
+    const int r00 = a.slice_ptr[s0] - R.E0;
+    const int r01 = h1 ? a.slice_ptr[s1] - R.E0 : 0;
+    const int i0 = s0 * kSlice + lane, i1 = s1 * kSlice + lane;
+    unsigned lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+    if (w0 > 0) slice_chunks(r00, w0, lo0, hi0);
+    if (w1 > 0) slice_chunks(r01, w1, lo1, hi1);
+    const bool pair = h1 && w0 > 0 && w1 > 0 && fast_w(wf0) && fast_w(wf1) && hi1 <= lo0 + 1;
+    if (pair) {
+      if (ok) ok = ring_release_below(R, C, C.pass_base + lo0, lane, a.ctl);
+      if (ok) ok = ring_acquire(R, C, C.pass_base + lo0, C.pass_base + hi1, a.ctl);
+      T acc0 = (T)0, acc1 = (T)0;
+      if (ok) {
+        int c0[kFastW], c1[kFastW];
+        T v0[kFastW], v1[kFastW];
+        ring_load(R, C, r00, w0, lane, c0, v0);
+        ring_load(R, C, r01, w1, lane, c1, v1);
+#pragma unroll
+        for (int k = 0; k < kFastW; ++k) {
+          if (k < w0) acc0 = fma(v0[k], G(c0[k]), acc0);
+          if (k < w1) acc1 = fma(v1[k], G(c1[k]), acc1);
+        }
+      }
+      Rw(i0, acc0);
+      Rw(i1, acc1);
+      continue;
+    }
+    for (int j = 0; j < 2; ++j) {  // one slice at a time
+      const bool hj = j == 0 || h1;
+      if (!hj) break;
+      const uint32_t wf = j ? wf1 : wf0;
+      const int w = j ? w1 : w0;
+      const int r0 = j ? r01 : r00;
+      const int i = j ? i1 : i0;
+      T acc = (T)0;
+      if (w > 0) {
+        const unsigned lo = j ? lo1 : lo0, hi = j ? hi1 : hi0;
+        if (ok) ok = ring_release_below(R, C, C.pass_base + lo, lane, a.ctl);
+        if (ok) ok = ring_acquire(R, C, C.pass_base + lo, C.pass_base + hi, a.ctl);
+      }
+      if (ok) {
+        if (fast_w(wf)) {
+          int c[kFastW];
+          T v[kFastW];
+          ring_load(R, C, r0, w, lane, c, v);
+#pragma unroll
+          for (int k = 0; k < kFastW; ++k)
+            if (k < w) acc = fma(v[k], G(c[k]), acc);
+        } else {
+          acc = ring_row_generic(a, R, C, r0, wf, i, lane, G);
+        }
+      }
+      Rw(i, acc);
+    }
+  }
+  C.pass_base += R.nch;
+  if (ok) ok = ring_release_below(R, C, C.pass_base, lane, a.ctl);
+  return ok;
+}
+
+// Set-up common to both stages: the ring in dynamic shared memory, the
+// block's slice range and element range, barrier initialisation.
+template <typename T>
+__device__ __forceinline__ void ring_setup(const CgArgs& a, char* smem, Ring<T>& R, int& S0,
+                                           int& S1) {
+  constexpr int S = Ring<T>::S;
+  R.base = smem;
+  R.full = reinterpret_cast<unsigned long long*>(smem + S * stage_bytes<T>());
+  R.empty = R.full + S;
+  R.stop = reinterpret_cast<volatile int*>(R.empty + S);
+  S0 = (int)((long long)a.nslices * blockIdx.x / gridDim.x);
+  S1 = (int)((long long)a.nslices * (blockIdx.x + 1) / gridDim.x);
+  R.E0 = a.slice_ptr[S0];
+  R.E1 = a.slice_ptr[S1];
+  R.nch = (unsigned)((R.E1 - R.E0 + kCH - 1) >> kLogCH);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&R.full[s], 1);
+      mbar_init(&R.empty[s], kNC);
+    }
+    *R.stop = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+}
+
+// Rows [R0, R1) of consumer warp `warp` inside the block's row range.
+__device__ __forceinline__ void warp_rows(int S0, int S1, int n, int& R0, int& R1) {
+  const int warp = threadIdx.x >> 5;
+  const int B0 = S0 * kSlice, B1 = min(S1 * kSlice, n);
+  const int rows = max(0, B1 - B0);
+  // split in multiples of 4 rows so that 16-byte vectors stay aligned
+  const int q4 = (rows + 3) >> 2;
+  R0 = B0 + 4 * (int)((long long)q4 * warp / kNC);
+  R1 = min(B1, B0 + 4 * (int)((long long)q4 * (warp + 1) / kNC));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -200,64 +472,63 @@ __device__ __forceinline__ void spmv_slices(const CgArgs& a, int s_lo, int s_hi,
 //   mode kCgToEps1:  start from x = 0; iterate to eps1 (Algorithm I).
 //   mode kCgContinue continue the state left by kCgK0 to eps1 (Algorithm II).
 // ---------------------------------------------------------------------------------------
-template <bool FIRST>
-__device__ __forceinline__ void p1_32(const CgArgs& a, int s_lo, int s_hi, int lane,
-                                      const float* r, const float* dold, float* dnew, float beta,
-                                      FF& pdq) {
-  const int n = a.n;
-  float* q = a.q32;
-  auto G = [&](int c) -> float {
-    if (FIRST) return r[c];
-    return __fmaf_rn(beta, dold[c], r[c]);
-  };
-  auto R = [&](int i, float acc) {
-    if (i < n) {
-      const float di = G(i);
-      dnew[i] = di;
-      q[i] = acc;
-      ff_add_prod(pdq, di, acc);
-    }
-  };
-  spmv_slices<float, false>(a, s_lo, s_hi, lane, G, R);
+
+// x += alpha d, r -= alpha q, r^T r over rows [R0, R1): four rows per lane,
+// two groups of four in flight.
+__device__ __forceinline__ void upd32(const CgArgs& a, int i, float4 d4, float4 q4, float alpha,
+                                      FF& prr) {
+  float4 x4 = *reinterpret_cast<const float4*>(a.x32 + i);
+  float4 r4 = *reinterpret_cast<const float4*>(a.r32 + i);
+  x4.x = __fmaf_rn(alpha, d4.x, x4.x);
+  x4.y = __fmaf_rn(alpha, d4.y, x4.y);
+  x4.z = __fmaf_rn(alpha, d4.z, x4.z);
+  x4.w = __fmaf_rn(alpha, d4.w, x4.w);
+  r4.x = __fmaf_rn(-alpha, q4.x, r4.x);
+  r4.y = __fmaf_rn(-alpha, q4.y, r4.y);
+  r4.z = __fmaf_rn(-alpha, q4.z, r4.z);
+  r4.w = __fmaf_rn(-alpha, q4.w, r4.w);
+  *reinterpret_cast<float4*>(a.x32 + i) = x4;
+  *reinterpret_cast<float4*>(a.r32 + i) = r4;
+  ff_add_prod(prr, r4.x, r4.x);
+  ff_add_prod(prr, r4.y, r4.y);
+  ff_add_prod(prr, r4.z, r4.z);
+  ff_add_prod(prr, r4.w, r4.w);
 }
 
-// x += alpha d, r -= alpha q, r^T r over the warp's rows, four rows per lane.
-__device__ __forceinline__ void p2_32(const CgArgs& a, int s_lo, int s_hi, int lane,
-                                      const float* d, float alpha, FF& prr) {
-  const int R0 = s_lo * kSlice, R1 = min(s_hi * kSlice, a.n);
-  for (int base = R0 + 4 * lane; base < R1; base += 4 * kSlice) {
-    if (base + 4 <= R1) {
+__device__ __forceinline__ void p2_32(const CgArgs& a, int R0, int R1, int lane, const float* d,
+                                      float alpha, FF& prr) {
+  for (int base = R0 + 4 * lane; base < R1; base += 8 * kSlice) {
+    const int b2 = base + 4 * kSlice;
+    if (b2 + 4 <= R1) {
       const float4 d4 = *reinterpret_cast<const float4*>(d + base);
       const float4 q4 = *reinterpret_cast<const float4*>(a.q32 + base);
-      float4 x4 = *reinterpret_cast<const float4*>(a.x32 + base);
-      float4 r4 = *reinterpret_cast<const float4*>(a.r32 + base);
-      x4.x = __fmaf_rn(alpha, d4.x, x4.x);
-      x4.y = __fmaf_rn(alpha, d4.y, x4.y);
-      x4.z = __fmaf_rn(alpha, d4.z, x4.z);
-      x4.w = __fmaf_rn(alpha, d4.w, x4.w);
-      r4.x = __fmaf_rn(-alpha, q4.x, r4.x);
-      r4.y = __fmaf_rn(-alpha, q4.y, r4.y);
-      r4.z = __fmaf_rn(-alpha, q4.z, r4.z);
-      r4.w = __fmaf_rn(-alpha, q4.w, r4.w);
-      *reinterpret_cast<float4*>(a.x32 + base) = x4;
-      *reinterpret_cast<float4*>(a.r32 + base) = r4;
-      ff_add_prod(prr, r4.x, r4.x);
-      ff_add_prod(prr, r4.y, r4.y);
-      ff_add_prod(prr, r4.z, r4.z);
-      ff_add_prod(prr, r4.w, r4.w);
+      const float4 e4 = *reinterpret_cast<const float4*>(d + b2);
+      const float4 s4 = *reinterpret_cast<const float4*>(a.q32 + b2);
+      upd32(a, base, d4, q4, alpha, prr);
+      upd32(a, b2, e4, s4, alpha, prr);
     } else {
-      for (int i = base; i < R1; ++i) {
-        a.x32[i] = __fmaf_rn(alpha, d[i], a.x32[i]);
-        const float ri = __fmaf_rn(-alpha, a.q32[i], a.r32[i]);
-        a.r32[i] = ri;
-        ff_add_prod(prr, ri, ri);
+      for (int g = base; g < R1 && g <= b2; g += 4 * kSlice) {
+        if (g + 4 <= R1) {
+          upd32(a, g, *reinterpret_cast<const float4*>(d + g),
+                *reinterpret_cast<const float4*>(a.q32 + g), alpha, prr);
+        } else {
+          for (int i = g; i < R1; ++i) {
+            a.x32[i] = __fmaf_rn(alpha, d[i], a.x32[i]);
+            const float ri = __fmaf_rn(-alpha, a.q32[i], a.r32[i]);
+            a.r32[i] = ri;
+            ff_add_prod(prr, ri, ri);
+          }
+        }
       }
     }
   }
 }
 
-__global__ void __launch_bounds__(kCgThreads, 2) k_cg32(CgArgs a) {
-  __shared__ double sm[33];
+enum Dec { kGo = 0, kStop = 1, kNan = 2, kBroke = 3, kBreakdown = 4 };
+
+__global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
+  extern __shared__ __align__(128) char smem[];
+  __shared__ CShared S;
   Ctl* ctl = a.ctl;
   if (volatile_status(ctl) != 0 || ctl->trivial) return;
   if (a.mode == kCgContinue && ctl->broke32) {  // stage 1 already ended in the k0 phase
@@ -267,38 +538,54 @@ __global__ void __launch_bounds__(kCgThreads, 2) k_cg32(CgArgs a) {
     }
     return;
   }
-  const int lane = threadIdx.x & 31;
-  int s_lo, s_hi;
-  warp_slices(a.nslices, s_lo, s_hi);
+  Ring<float> R;
+  int S0, S1;
+  ring_setup(a, smem, R, S0, S1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == kNC) {
+    if (lane == 0) ring_producer(a, R);
+    return;
+  }
+  const bool lead = threadIdx.x == 0;           // computes the block's scalars
+  const bool lead0 = lead && blockIdx.x == 0;   // writes the control block
+  Cursor C{0u, 0u, 0u};
+  int R0, R1;
+  warp_rows(S0, S1, a.n, R0, R1);
   const int n = a.n;
   const int rel = ctl->tol_relative;
   unsigned long long round = 0;
   int red = 0;
   bool ok = true;
 
-  double rr, bnorm;
+  double rr, bnorm;  // identical in every thread after each broadcast
   float beta;
   int first, parity, it;
   if (a.mode != kCgContinue) {
     // CG line 1: x0 = 0, r0 = b - A x0 = b~, d0 = r0.
     FF acc{0.f, 0.f};
-    const int R0 = s_lo * kSlice, R1 = min(s_hi * kSlice, n);
     for (int i = R0 + lane; i < R1; i += kSlice) {
       const float bi = a.b32[i];
       a.x32[i] = 0.0f;
       a.r32[i] = bi;
+      a.da[i] = 0.0f;  // d_{-1}
       ff_add_prod(acc, bi, bi);
     }
-    rr = grid_total(ff_block(acc, sm), a.partials, red, ctl, a.slot, round, sm, ok);
-    bnorm = sqrt(rr);  // ||b~|| = ||r0||
+    const double tot = cgrid_total(block_ff(acc, S), a.partials, red, ctl, a.slot, round, S, ok);
+    if (lead) {
+      S.rr = tot;
+      S.val = sqrt(tot);  // ||b~|| = ||r0||
+      if (lead0) {
+        ctl->bnorm32 = S.val;
+        if (!isfinite(S.val)) set_status(ctl, MPCG_ERR_NAN);
+      }
+    }
+    cbar();
+    rr = S.rr;
+    bnorm = S.val;
     first = 1;
     parity = 0;
     beta = 0.0f;
     it = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      ctl->bnorm32 = bnorm;
-      if (!isfinite(bnorm)) set_status(ctl, MPCG_ERR_NAN);
-    }
     if (!isfinite(bnorm)) ok = false;
   } else {
     rr = ctl->rr;
@@ -310,62 +597,93 @@ __global__ void __launch_bounds__(kCgThreads, 2) k_cg32(CgArgs a) {
   }
   const double eps = a.mode == kCgK0 ? ctl->eps2 : ctl->eps1;
   const int limit = a.mode == kCgK0 ? min(ctl->k0, ctl->max1) : ctl->max1;
-  double vsum = 0.0;
+  double vsum = 0.0;  // thread 0
   int k0done = 0, broke = 0;
-  double m = stop_measure(rr, bnorm, rel);
 
   while (ok) {
-    m = stop_measure(rr, bnorm, rel);
-    if (isnan(m)) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(ctl, MPCG_ERR_NAN);
-      break;
+    if (lead) {
+      const double m = stop_measure(rr, bnorm, rel);
+      int dec = kGo;
+      if (isnan(m)) dec = kNan;
+      else if (m <= eps || it >= limit || (a.mode == kCgK0 && rr == 0.0)) dec = kStop;
+      S.dec = dec;
+      if (dec == kNan && lead0) set_status(ctl, MPCG_ERR_NAN);
     }
-    if (m <= eps || it >= limit) break;
-    if (a.mode == kCgK0 && rr == 0.0) break;
+    cbar();
+    if (S.dec != kGo) break;
 
     // ---- P1: q = A d_k with d_k = r_k + beta_k d_{k-1} formed on the fly ----
     // Plain (coherent) pointers: these vectors change between iterations of
     // this launch, so they must not go through the read-only data path.
     const float* dold = parity ? a.db : a.da;
     float* dnew = parity ? a.da : a.db;
+    const float* r = a.r32;
+    float* q = a.q32;
     FF pdq{0.f, 0.f};
-    if (first)
-      p1_32<true>(a, s_lo, s_hi, lane, a.r32, dold, dnew, beta, pdq);
-    else
-      p1_32<false>(a, s_lo, s_hi, lane, a.r32, dold, dnew, beta, pdq);
-    const double dq = grid_total(ff_block(pdq, sm), a.partials, red, ctl, a.slot, round, sm, ok);
-    if (!ok) break;
-    if (!isfinite(dq)) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(ctl, MPCG_ERR_NAN);
-      break;
+    // d_0 = r_0 is the same formula with beta = 0 and d_{-1} = 0 (zeroed at
+    // the start): fma(0, 0, r) = r.
+    const float bt = first ? 0.0f : beta;
+    auto G = [&](int c) -> float { return __fmaf_rn(bt, dold[c], r[c]); };
+    auto Rw = [&](int i, float acc) {
+      if (i < n) {
+        const float di = __fmaf_rn(bt, dold[i], r[i]);
+        dnew[i] = di;
+        q[i] = acc;
+        ff_add_prod(pdq, di, acc);
+      }
+    };
+    const bool pass_ok = ring_spmv<float>(a, R, C, S0, S1, G, Rw);
+    if (!pass_ok) set_status(ctl, MPCG_ERR_TIMEOUT);
+    {
+      const double dq = cgrid_total(block_ff(pdq, S), a.partials, red, ctl, a.slot, round, S, ok);
+      if (lead) {
+        int dec = kGo;
+        if (!isfinite(dq)) dec = kNan;
+        else if (!(dq > 0.0)) dec = kBroke;  // stage 1 ends here; x and r are unchanged
+        else S.alpha = (float)(rr / dq);
+        S.dec = dec;
+        if (dec == kNan && lead0) set_status(ctl, MPCG_ERR_NAN);
+      }
+      cbar();
     }
-    if (!(dq > 0.0)) {  // stage 1 ends here; x and r are unchanged
+    if (!ok) break;
+    if (S.dec == kBroke) {
       broke = 1;
       break;
     }
-    const float alpha = (float)(rr / dq);
+    if (S.dec != kGo) break;
+    const float alpha = S.alpha;
 
     // ---- P2: x += alpha d_k, r -= alpha q, r^T r ----
     FF prr{0.f, 0.f};
-    p2_32(a, s_lo, s_hi, lane, dnew, alpha, prr);
-    const double rrn = grid_total(ff_block(prr, sm), a.partials, red, ctl, a.slot, round, sm, ok);
-    if (!ok) break;
-    if (!isfinite(rrn)) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(ctl, MPCG_ERR_NAN);
-      break;
+    p2_32(a, R0, R1, lane, dnew, alpha, prr);
+    {
+      const double rrn = cgrid_total(block_ff(prr, S), a.partials, red, ctl, a.slot, round, S, ok);
+      if (lead) {
+        int dec = kGo;
+        if (!isfinite(rrn)) {
+          dec = kNan;
+          if (lead0) set_status(ctl, MPCG_ERR_NAN);
+        } else {
+          if (a.mode == kCgK0) vsum += sqrt(rrn) / sqrt(rr);  // Eq. (13) ratio
+          S.beta = (float)(rrn / rr);
+          S.rr = rrn;
+        }
+        S.dec = dec;
+      }
+      cbar();
     }
-    if (a.mode == kCgK0) {
-      vsum += sqrt(rrn) / sqrt(rr);  // Eq. (13) ratio ||r_i|| / ||r_{i-1}||
-      ++k0done;
-    }
-    beta = (float)(rrn / rr);
-    rr = rrn;
+    if (!ok || S.dec != kGo) break;
+    if (a.mode == kCgK0) ++k0done;
+    beta = S.beta;
+    rr = S.rr;
     parity ^= 1;
     first = 0;
     ++it;
   }
+  if (lead) *R.stop = 1;
 
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (lead0) {
     ctl->rr = rr;
     ctl->beta32 = beta;
     ctl->first = first;
@@ -388,54 +706,87 @@ __global__ void __launch_bounds__(kCgThreads, 2) k_cg32(CgArgs a) {
 // Double-precision stage (restart of Algorithm I/II, or pure FP64 CG).
 // ---------------------------------------------------------------------------------------
 
-// r = b - A v (and d = r) over the warp's rows; returns the partial r^T r.
-// out_r / out_d may be null.
-__device__ __forceinline__ double residual64(const CgArgs& a, int s_lo, int s_hi, int lane,
-                                             const double* v, double* out_r, double* out_d) {
-  double p = 0.0;
-  auto G = [&](int c) -> double { return v[c]; };
-  auto R = [&](int i, double acc) {
-    if (i < a.n) {
-      const double ri = a.b64[i] - acc;
-      if (out_r) out_r[i] = ri;
-      if (out_d) out_d[i] = ri;
-      p = __fma_rn(ri, ri, p);
+// x += alpha d, r -= alpha q over rows [R0, R1): two rows per lane, two
+// pairs in flight; returns this thread's part of r^T r.
+__device__ __forceinline__ double p2_64(const CgArgs& a, int R0, int R1, int lane, double alpha) {
+  double prr = 0.0;
+  for (int base = R0 + 2 * lane; base < R1; base += 4 * kSlice) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = base + h * 2 * kSlice;
+      if (g + 2 <= R1) {
+        const double2 d2 = *reinterpret_cast<const double2*>(a.d64 + g);
+        const double2 q2 = *reinterpret_cast<const double2*>(a.q64 + g);
+        double2 x2 = *reinterpret_cast<const double2*>(a.x64 + g);
+        double2 r2 = *reinterpret_cast<const double2*>(a.r64 + g);
+        x2.x = __fma_rn(alpha, d2.x, x2.x);
+        x2.y = __fma_rn(alpha, d2.y, x2.y);
+        r2.x = __fma_rn(-alpha, q2.x, r2.x);
+        r2.y = __fma_rn(-alpha, q2.y, r2.y);
+        *reinterpret_cast<double2*>(a.x64 + g) = x2;
+        *reinterpret_cast<double2*>(a.r64 + g) = r2;
+        prr = __fma_rn(r2.x, r2.x, prr);
+        prr = __fma_rn(r2.y, r2.y, prr);
+      } else if (g < R1) {
+        a.x64[g] = __fma_rn(alpha, a.d64[g], a.x64[g]);
+        const double ri = __fma_rn(-alpha, a.q64[g], a.r64[g]);
+        a.r64[g] = ri;
+        prr = __fma_rn(ri, ri, prr);
+      }
     }
-  };
-  spmv_slices<double, false>(a, s_lo, s_hi, lane, G, R);
-  return p;
+  }
+  return prr;
 }
 
-// q = A d over the warp's rows; returns the partial d^T q.
-__device__ __forceinline__ double p1_64(const CgArgs& a, int s_lo, int s_hi, int lane) {
-  double pdq = 0.0;
-  const double* d = a.d64;
-  double* q = a.q64;
-  const int n = a.n;
-  auto G = [&](int c) -> double { return d[c]; };
-  auto R = [&](int i, double acc) {
-    if (i < n) {
-      q[i] = acc;
-      pdq = __fma_rn(d[i], acc, pdq);
+// d = r + beta d over rows [R0, R1).
+__device__ __forceinline__ void p3_64(const CgArgs& a, int R0, int R1, int lane, double beta) {
+  for (int base = R0 + 2 * lane; base < R1; base += 4 * kSlice) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = base + h * 2 * kSlice;
+      if (g + 2 <= R1) {
+        double2 d2 = *reinterpret_cast<const double2*>(a.d64 + g);
+        const double2 r2 = *reinterpret_cast<const double2*>(a.r64 + g);
+        d2.x = __fma_rn(beta, d2.x, r2.x);
+        d2.y = __fma_rn(beta, d2.y, r2.y);
+        *reinterpret_cast<double2*>(a.d64 + g) = d2;
+      } else if (g < R1) {
+        a.d64[g] = __fma_rn(beta, a.d64[g], a.r64[g]);
+      }
     }
-  };
-  spmv_slices<double, false>(a, s_lo, s_hi, lane, G, R);
-  return pdq;
+  }
 }
 
-__global__ void __launch_bounds__(kCgThreads, 2) k_cg64(CgArgs a) {
-  __shared__ double sm[33];
+// Kinds of SpMV pass in the double-precision stage.
+enum Pass64 { kRestart = 0, kTrueRes = 1, kIterate = 2, kFinalRes = 3, kDone = 4 };
+
+__global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
+  extern __shared__ __align__(128) char smem[];
+  __shared__ CShared S;
   Ctl* ctl = a.ctl;
-  const int lane = threadIdx.x & 31;
-  int s_lo, s_hi;
-  warp_slices(a.nslices, s_lo, s_hi);
-  const int n = a.n;
-  const int R0 = s_lo * kSlice, R1 = min(s_hi * kSlice, n);
   if (volatile_status(ctl) != 0) return;
+  Ring<double> R;
+  int S0, S1;
+  ring_setup(a, smem, R, S0, S1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = a.n;
   if (ctl->trivial) {  // b = 0: x = 0 solves A x = b exactly
-    for (int i = R0 + lane; i < R1; i += kSlice) a.x64[i] = 0.0;
+    if (warp < kNC) {
+      int R0, R1;
+      warp_rows(S0, S1, n, R0, R1);
+      for (int i = R0 + lane; i < R1; i += kSlice) a.x64[i] = 0.0;
+    }
     return;
   }
+  if (warp == kNC) {
+    if (lane == 0) ring_producer(a, R);
+    return;
+  }
+  const bool lead = threadIdx.x == 0;
+  const bool lead0 = lead && blockIdx.x == 0;
+  Cursor C{0u, 0u, 0u};
+  int R0, R1;
+  warp_rows(S0, S1, n, R0, R1);
   const int rel = ctl->tol_relative;
   const double bnorm = ctl->bnorm64;
   const double eps2 = ctl->eps2;
@@ -444,117 +795,139 @@ __global__ void __launch_bounds__(kCgThreads, 2) k_cg64(CgArgs a) {
   unsigned long long round = 0;
   int red = 0;
   bool ok = true;
-  int it = 0, restarts = 0, failed = 0;
+  int it = 0, restarts = 0;
+  int failed = 0;                  // thread 0
+  double m = 0.0, true_rel = NAN;  // thread 0
+  double rr = 0.0;                 // thread 0
 
-  // Promote: x0 = float64(x~) (or 0); restart: r0 = b - A x0, d0 = r0.
+  // Promote: x0 = float64(x~) (or 0).
   for (int i = R0 + lane; i < R1; i += kSlice) a.x64[i] = a.mode ? 0.0 : (double)a.x32[i];
-  ok = grid_barrier(ctl, a.slot, round);
-  double rr = grid_total(block_sum_warp_values(warp_sum(residual64(a, s_lo, s_hi, lane, a.x64,
-                                                                   a.r64, a.d64)), sm),
-                         a.partials, red, ctl, a.slot, round, sm, ok);
-  double m = stop_measure(rr, bnorm, rel);
-  double true_rel = NAN;
+  ok = cgrid_barrier(ctl, a.slot, round, &S.ok);
 
-  while (ok) {
-    m = stop_measure(rr, bnorm, rel);
-    if (isnan(m)) {
-      failed = MPCG_ERR_NAN;
-      break;
+  // One SpMV pass per step; its kind is decided by thread 0 and broadcast.
+  //   kRestart:  r = b - A x, d = r, r^T r      (CG line 1 from x)
+  //   kTrueRes:  q = b - A x, ||q||^2           (true residual at eps2)
+  //   kIterate:  q = A d, d^T q; then the x, r update and d = r + beta d
+  //   kFinalRes: ||b - A x||^2 after the cap
+  int kind = kRestart;
+  const double* x = a.x64;
+  while (ok && kind != kDone) {
+    const double* gv = kind == kIterate ? a.d64 : x;
+    double p = 0.0;
+    {
+      const int knd = kind;
+      double* r = a.r64;
+      double* d = a.d64;
+      double* q = a.q64;
+      const double* b = a.b64;
+      auto G = [&](int c) -> double { return gv[c]; };
+      auto Rw = [&](int i, double acc) {
+        if (i < n) {
+          if (knd == kIterate) {
+            q[i] = acc;
+            p = __fma_rn(d[i], acc, p);
+          } else {
+            const double ri = b[i] - acc;
+            if (knd == kRestart) {
+              r[i] = ri;
+              d[i] = ri;
+            } else if (knd == kTrueRes) {
+              q[i] = ri;
+            }
+            p = __fma_rn(ri, ri, p);
+          }
+        }
+      };
+      if (!ring_spmv<double>(a, R, C, S0, S1, G, Rw)) set_status(ctl, MPCG_ERR_TIMEOUT);
     }
-    if (m <= eps2) {
-      // True residual ||b - A x|| (FP64); restart from x if it misses eps2.
-      const double tt = grid_total(
-          block_sum_warp_values(warp_sum(residual64(a, s_lo, s_hi, lane, a.x64, a.q64, nullptr)),
-                                sm),
-          a.partials, red, ctl, a.slot, round, sm, ok);
-      if (!ok) break;
-      true_rel = bnorm > 0.0 ? sqrt(tt) / bnorm : sqrt(tt);
-      const double tm = rel ? true_rel : sqrt(tt);
-      if (!(tm > eps2) || restarts >= max_restarts) break;
+    const double tot = cgrid_total(block_d(p, S), a.partials, red, ctl, a.slot, round, S, ok);
+    if (!ok) break;
+
+    // ---- thread 0: the scalars and the next pass ----
+    if (lead) {
+      int next = kDone;
+      if (kind == kFinalRes) {
+        true_rel = bnorm > 0.0 ? sqrt(tot) / bnorm : sqrt(tot);
+      } else if (kind == kTrueRes) {
+        true_rel = bnorm > 0.0 ? sqrt(tot) / bnorm : sqrt(tot);
+        const double tm = rel ? true_rel : sqrt(tot);
+        if ((tm > eps2) && restarts < max_restarts) {
+          next = kTrueRes + 100;  // restart from x: r = d = q, then the loop head
+          rr = tot;
+        }
+      } else if (kind == kIterate) {
+        if (!isfinite(tot)) {
+          failed = MPCG_ERR_NAN;
+        } else if (!(tot > 0.0)) {
+          failed = MPCG_ERR_BREAKDOWN;
+        } else {
+          S.val = rr / tot;  // alpha
+          next = kIterate;
+        }
+      } else {  // kRestart
+        rr = tot;
+        next = -1;  // loop head
+      }
+      S.dec = next;
+    }
+    cbar();
+    int next = S.dec;
+
+    if (kind == kIterate && next == kIterate) {
+      // ---- P2: x += alpha d, r -= alpha q, r^T r ----
+      const double alpha = S.val;
+      const double prr = p2_64(a, R0, R1, lane, alpha);
+      const double rrn = cgrid_total(block_d(prr, S), a.partials, red, ctl, a.slot, round, S, ok);
+      if (lead) {
+        if (!isfinite(rrn)) {
+          failed = MPCG_ERR_NAN;
+          S.dec = kDone;
+        } else {
+          S.val = rrn / rr;  // beta
+          rr = rrn;
+          S.dec = -1;
+        }
+      }
+      cbar();
+      if (!ok || S.dec == kDone) break;
+      // ---- P3: d = r + beta d ----
+      p3_64(a, R0, R1, lane, S.val);
+      ok = cgrid_barrier(ctl, a.slot, round, &S.ok);
+      ++it;
+      next = -1;
+    } else if (next == kTrueRes + 100) {
       ++restarts;
       for (int i = R0 + lane; i < R1; i += kSlice) {
         const double ri = a.q64[i];
         a.r64[i] = ri;
         a.d64[i] = ri;
       }
-      rr = tt;
-      ok = grid_barrier(ctl, a.slot, round);
-      continue;
+      ok = cgrid_barrier(ctl, a.slot, round, &S.ok);
+      next = -1;
     }
-    if (it >= max2) {
-      failed = MPCG_ERR_NOT_CONVERGED;
-      break;
-    }
-    // ---- P1: q = A d, d^T q ----
-    const double pdq = p1_64(a, s_lo, s_hi, lane);
-    const double dq = grid_total(block_sum_warp_values(warp_sum(pdq), sm), a.partials, red, ctl,
-                                 a.slot, round, sm, ok);
-    if (!ok) break;
-    if (!isfinite(dq)) {
-      failed = MPCG_ERR_NAN;
-      break;
-    }
-    if (!(dq > 0.0)) {
-      failed = MPCG_ERR_BREAKDOWN;
-      break;
-    }
-    const double alpha = rr / dq;
-    // ---- P2: x += alpha d, r -= alpha q, r^T r (two rows per lane) ----
-    double prr = 0.0;
-    for (int base = R0 + 2 * lane; base < R1; base += 2 * kSlice) {
-      if (base + 2 <= R1) {
-        const double2 d2 = *reinterpret_cast<const double2*>(a.d64 + base);
-        const double2 q2 = *reinterpret_cast<const double2*>(a.q64 + base);
-        double2 x2 = *reinterpret_cast<const double2*>(a.x64 + base);
-        double2 r2 = *reinterpret_cast<const double2*>(a.r64 + base);
-        x2.x = __fma_rn(alpha, d2.x, x2.x);
-        x2.y = __fma_rn(alpha, d2.y, x2.y);
-        r2.x = __fma_rn(-alpha, q2.x, r2.x);
-        r2.y = __fma_rn(-alpha, q2.y, r2.y);
-        *reinterpret_cast<double2*>(a.x64 + base) = x2;
-        *reinterpret_cast<double2*>(a.r64 + base) = r2;
-        prr = __fma_rn(r2.x, r2.x, prr);
-        prr = __fma_rn(r2.y, r2.y, prr);
-      } else {
-        a.x64[base] = __fma_rn(alpha, a.d64[base], a.x64[base]);
-        const double ri = __fma_rn(-alpha, a.q64[base], a.r64[base]);
-        a.r64[base] = ri;
-        prr = __fma_rn(ri, ri, prr);
+    if (next == -1) {  // loop head: stop test on the recursive residual
+      if (lead) {
+        m = stop_measure(rr, bnorm, rel);
+        int nk = kIterate;
+        if (isnan(m)) {
+          failed = MPCG_ERR_NAN;
+          nk = kDone;
+        } else if (m <= eps2) {
+          nk = kTrueRes;
+        } else if (it >= max2) {
+          failed = MPCG_ERR_NOT_CONVERGED;
+          nk = kFinalRes;
+        }
+        S.dec = nk;
       }
+      cbar();
+      next = S.dec;
     }
-    const double rrn = grid_total(block_sum_warp_values(warp_sum(prr), sm), a.partials, red, ctl,
-                                  a.slot, round, sm, ok);
-    if (!ok) break;
-    if (!isfinite(rrn)) {
-      failed = MPCG_ERR_NAN;
-      break;
-    }
-    const double beta = rrn / rr;
-    rr = rrn;
-    // ---- P3: d = r + beta d ----
-    for (int base = R0 + 2 * lane; base < R1; base += 2 * kSlice) {
-      if (base + 2 <= R1) {
-        double2 d2 = *reinterpret_cast<const double2*>(a.d64 + base);
-        const double2 r2 = *reinterpret_cast<const double2*>(a.r64 + base);
-        d2.x = __fma_rn(beta, d2.x, r2.x);
-        d2.y = __fma_rn(beta, d2.y, r2.y);
-        *reinterpret_cast<double2*>(a.d64 + base) = d2;
-      } else {
-        a.d64[base] = __fma_rn(beta, a.d64[base], a.r64[base]);
-      }
-    }
-    ok = grid_barrier(ctl, a.slot, round);
-    ++it;
+    kind = next;
   }
 
-  if (failed == MPCG_ERR_NOT_CONVERGED && ok) {
-    const double tt = grid_total(
-        block_sum_warp_values(warp_sum(residual64(a, s_lo, s_hi, lane, a.x64, nullptr, nullptr)),
-                              sm),
-        a.partials, red, ctl, a.slot, round, sm, ok);
-    true_rel = bnorm > 0.0 ? sqrt(tt) / bnorm : sqrt(tt);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (lead) *R.stop = 1;
+  if (lead0) {
     if (failed) set_status(ctl, failed);
     ctl->n2 = it;
     ctl->restarts = restarts;
@@ -565,6 +938,7 @@ __global__ void __launch_bounds__(kCgThreads, 2) k_cg64(CgArgs a) {
     ctl->t_fp64 = globaltimer();
   }
 }
+
 
 // Promotion only (stage-1-only solves): x = float64(x~).
 __global__ void k_promote(const Ctl* c, const float* __restrict__ x32, double* __restrict__ x64,
@@ -578,24 +952,28 @@ __global__ void k_promote(const Ctl* c, const float* __restrict__ x32, double* _
 // ---------------------------------------------------------------------------------------
 // Stand-alone SpMV through the sliced layout (verification entry point).
 // ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T spmv_row_direct(const CgArgs& a, int s, int i, const T* x) {
+  const uint32_t wf = a.slice_w[s];
+  const int w = (int)(wf & ~kOverflowBit);
+  const int p = a.slice_ptr[s] + (i & 31);
+  const T* sv = svals<T>(a);
+  T acc = (T)0;
+  for (int k = 0; k < w; ++k) acc = fma(sv[p + kSlice * k], x[a.scol[p + kSlice * k]], acc);
+  if (wf & kOverflowBit)
+    for (int e = a.rp[i] + w; e < a.rp[i + 1]; ++e) acc = fma((T)a.val[e], x[a.col[e]], acc);
+  return acc;
+}
+
 __global__ void k_spmv(CgArgs a, int fp32, const void* xv, void* yv) {
   if (volatile_status(a.ctl) != 0) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = i >> 5, lane = i & 31;
+  const int s = i >> 5;
   if (s >= a.nslices || i >= a.n) return;
-  const uint32_t wf = a.slice_w[s];
-  const int p = a.slice_ptr[s] + lane;
-  if (fp32) {
-    const float* x = (const float*)xv;
-    SliceBuf<float> b;
-    slice_load<float>(a, wf, p, b);
-    ((float*)yv)[i] = slice_row<float>(a, i, wf, p, b, [&](int c) { return x[c]; });
-  } else {
-    const double* x = (const double*)xv;
-    SliceBuf<double> b;
-    slice_load<double>(a, wf, p, b);
-    ((double*)yv)[i] = slice_row<double>(a, i, wf, p, b, [&](int c) { return x[c]; });
-  }
+  if (fp32)
+    ((float*)yv)[i] = spmv_row_direct<float>(a, s, i, (const float*)xv);
+  else
+    ((double*)yv)[i] = spmv_row_direct<double>(a, s, i, (const double*)xv);
 }
 
 static CgArgs make_args(const Launch& L, int slot, int mode) {
@@ -626,14 +1004,40 @@ static CgArgs make_args(const Launch& L, int slot, int mode) {
   return a;
 }
 
+// Blocks of the stage kernels: one per SM (fewer when asked).  0 on failure.
+int cg_grid(int requested) {
+  static int cached = 0;
+  if (!cached) {
+    int g32 = 0, g64 = 0, dev = 0, sms = 0;
+    if (cudaFuncSetAttribute((const void*)k_cg32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ring_smem_bytes<float>()) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)k_cg64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ring_smem_bytes<double>()) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g32, (const void*)k_cg32, kTmaThreads,
+                                                      ring_smem_bytes<float>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g64, (const void*)k_cg64, kTmaThreads,
+                                                      ring_smem_bytes<double>()) != cudaSuccess)
+      return 0;
+    const int per = g32 < g64 ? g32 : g64;
+    cached = per > 0 ? sms * per : -1;
+    if (cached > kMaxGrid) cached = kMaxGrid;
+  }
+  if (cached <= 0) return 0;
+  return (requested > 0 && requested < cached) ? requested : cached;
+}
+
 const void* cg32_kernel() { return (const void*)k_cg32; }
 const void* cg64_kernel() { return (const void*)k_cg64; }
 
 cudaError_t launch_cg32(const Launch& L, int mode, int slot) {
   CgArgs a = make_args(L, slot, mode);
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)k_cg32, dim3(L.grid), dim3(kCgThreads), args, 0,
-                                    L.st);
+  const int g = cg_grid(L.grid_req);
+  if (g <= 0) return cudaErrorInvalidConfiguration;
+  return cudaLaunchCooperativeKernel((const void*)k_cg32, dim3(g), dim3(kTmaThreads), args,
+                                    ring_smem_bytes<float>(), L.st);
 }
 
 cudaError_t launch_cg64(const Launch& L, const double* b, double* x, int from_zero, int slot) {
@@ -641,8 +1045,10 @@ cudaError_t launch_cg64(const Launch& L, const double* b, double* x, int from_ze
   a.b64 = b;
   a.x64 = x;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)k_cg64, dim3(L.grid), dim3(kCgThreads), args, 0,
-                                    L.st);
+  const int g = cg_grid(L.grid_req);
+  if (g <= 0) return cudaErrorInvalidConfiguration;
+  return cudaLaunchCooperativeKernel((const void*)k_cg64, dim3(g), dim3(kTmaThreads), args,
+                                    ring_smem_bytes<double>(), L.st);
 }
 
 cudaError_t launch_promote(const Launch& L, double* x) {

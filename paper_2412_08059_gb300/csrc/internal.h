@@ -22,7 +22,8 @@ struct Launch {
   Ws ws;
   const mpcg_csr_t* A;
   cudaStream_t st;
-  int grid;  // persistent grid blocks
+  int grid;      // persistent grid of the BFS / component kernels
+  int grid_req;  // requested grid (0 = one full wave)
 };
 
 int persistent_grid(const void* kernel, int threads, int requested);
@@ -40,6 +41,7 @@ cudaError_t launch_spmv(const Launch& L, int fp32, const void* x, void* y);
 cudaError_t launch_promote(const Launch& L, double* x);
 const void* cg32_kernel();
 const void* cg64_kernel();
+int cg_grid(int requested);
 
 // bfs.cu
 cudaError_t launch_pseudo_diameter(const Launch& L, int first_slot);

@@ -67,6 +67,7 @@ int persistent_grid(const void* kernel, int threads, int requested) {
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess)
     return 0;
+  if (per_sm > 1) per_sm = 1;  // fewer barrier arrivals: one block per SM
   int full = sms * per_sm;
   if (full > kMaxGrid) full = kMaxGrid;
   if (requested > 0 && requested < full) return requested;
@@ -129,31 +130,50 @@ __global__ void k_rows(Ctl* c, const int32_t* __restrict__ rp, const int32_t* __
   if ((threadIdx.x & 31) == 0) slice_w[s] = (uint32_t)wmax | (any_ovf ? kOverflowBit : 0u);
 }
 
-// Exclusive scan of 32 * width over the slices (one block, fixed order).
+// Exclusive scan of 32 * width over the slices: one block, tiles of
+// kScanTile slices loaded coalesced into shared memory, a running carry.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanThreads * kScanPer;
 __global__ void k_scan(const uint32_t* __restrict__ slice_w, int32_t* __restrict__ slice_ptr,
                        int nslices) {
-  __shared__ long long sm[1024];
-  const int t = threadIdx.x, T = blockDim.x;
-  const long long per = ((long long)nslices + T - 1) / T;
-  long long lo = per * t, hi = lo + per;
-  if (lo > nslices) lo = nslices;
-  if (hi > nslices) hi = nslices;
-  long long s = 0;
-  for (long long k = lo; k < hi; ++k) s += (long long)kSlice * (slice_w[k] & ~kOverflowBit);
-  sm[t] = s;
+  __shared__ int32_t tile[kScanTile];
+  __shared__ long long part[kScanThreads];
+  __shared__ long long carry_s;
+  const int t = threadIdx.x;
+  if (t == 0) carry_s = 0;
   __syncthreads();
-  for (int o = 1; o < T; o <<= 1) {  // Hillis-Steele inclusive scan
-    long long v = t >= o ? sm[t - o] : 0;
+  for (int base = 0; base < nslices; base += kScanTile) {
+    for (int j = t; j < kScanTile; j += kScanThreads) {
+      const int s = base + j;
+      tile[j] = s < nslices ? (int32_t)(kSlice * (slice_w[s] & ~kOverflowBit)) : 0;
+    }
     __syncthreads();
-    sm[t] += v;
+    long long loc = 0;
+    for (int j = 0; j < kScanPer; ++j) loc += tile[t * kScanPer + j];
+    part[t] = loc;
+    __syncthreads();
+    for (int o = 1; o < kScanThreads; o <<= 1) {  // Hillis-Steele inclusive scan
+      const long long v = t >= o ? part[t - o] : 0;
+      __syncthreads();
+      part[t] += v;
+      __syncthreads();
+    }
+    long long run = carry_s + part[t] - loc;
+    for (int j = 0; j < kScanPer; ++j) {
+      const int v = tile[t * kScanPer + j];
+      tile[t * kScanPer + j] = (int32_t)run;
+      run += v;
+    }
+    __syncthreads();
+    for (int j = t; j < kScanTile; j += kScanThreads) {
+      const int s = base + j;
+      if (s < nslices) slice_ptr[s] = tile[j];
+    }
+    if (t == kScanThreads - 1) carry_s += part[kScanThreads - 1];
     __syncthreads();
   }
-  long long run = sm[t] - s;
-  for (long long k = lo; k < hi; ++k) {
-    slice_ptr[k] = (int32_t)run;
-    run += (long long)kSlice * (slice_w[k] & ~kOverflowBit);
-  }
-  if (t == T - 1) slice_ptr[nslices] = (int32_t)sm[T - 1];
+  if (t == 0) slice_ptr[nslices] = (int32_t)carry_s;
 }
 
 // Fill the sliced arrays: entry k of row i of slice s sits at
@@ -228,7 +248,7 @@ cudaError_t launch_prep(const Launch& L, const double* b) {
   const int blocks = (int)(((long long)d.nslices * kSlice + threads - 1) / threads);
   k_rows<<<blocks, threads, 0, L.st>>>(L.ws.ctl, L.A->row_ptr, L.A->col, b, L.ws.b32,
                                        L.ws.slice_w, d.n, d.nnz, d.nslices, d.wcap);
-  k_scan<<<1, 1024, 0, L.st>>>(L.ws.slice_w, L.ws.slice_ptr, d.nslices);
+  k_scan<<<1, kScanThreads, 0, L.st>>>(L.ws.slice_w, L.ws.slice_ptr, d.nslices);
   k_fill<<<blocks, threads, 0, L.st>>>(L.ws.ctl, L.A->row_ptr, L.A->col, L.A->val, L.ws.slice_w,
                                        L.ws.slice_ptr, L.ws.scol, L.ws.sv32, L.ws.sv64, d.n,
                                        d.nslices);
