@@ -12,7 +12,7 @@ using namespace mpcg;
 namespace {
 
 // Barrier-counter slots of the persistent launches within one call.
-enum Slot { kSlotCg64 = 0, kSlotPd = 1 /* .. 5 */, kSlotCgK0 = 6, kSlotCg32 = 7, kSlotBfs = 8 };
+enum Slot { kSlotCg64 = 0, kSlotPd = 1, kSlotCgK0 = 2, kSlotCg32 = 3, kSlotBfs = 4 };
 
 bool options_ok(const mpcg_options_t* o) {
   if (!o) return false;
@@ -27,7 +27,7 @@ bool sample_ok(const mpcg_sample_t* s) {
 }
 
 int grid_size(int requested) {
-  const void* kernels[2] = {bfs_kernel(), cc_kernel()};
+  const void* kernels[1] = {bfs_kernel()};
   int g = kMaxGrid;
   for (const void* k : kernels) {
     int gk = persistent_grid(k, kCgThreads, requested);
@@ -141,13 +141,9 @@ int32_t mpcg_solve(const mpcg_csr_t* A, const double* b, double* x, const mpcg_s
   if ((e = launch_init(L, *opts, fp64_only)) != cudaSuccess) return cuda_status(e);
   if ((e = launch_prep(L, b)) != cudaSuccess) return cuda_status(e);
   if (!fp64_only) {
-    if (auto_eps1) {  // Algorithm II
-      if ((e = launch_pseudo_diameter(L, kSlotPd)) != cudaSuccess) return cuda_status(e);
-      if ((e = launch_cg32(L, kCgK0, kSlotCgK0)) != cudaSuccess) return cuda_status(e);
-      if ((e = launch_knn(L.st, nullptr, *sample, *opts, L.ws.ctl, nullptr, nullptr)) !=
-          cudaSuccess)
+    if (auto_eps1) {  // Algorithm II: features, kNN and stage 1 in one fused launch
+      if ((e = launch_stage1(L, *sample, *opts, kSlotCg32, kSlotPd)) != cudaSuccess)
         return cuda_status(e);
-      if ((e = launch_cg32(L, kCgContinue, kSlotCg32)) != cudaSuccess) return cuda_status(e);
     } else {  // Algorithm I
       if ((e = launch_cg32(L, kCgToEps1, kSlotCg32)) != cudaSuccess) return cuda_status(e);
     }

@@ -1,0 +1,284 @@
+// bfs_core.cuh -- sparsity-graph features of Sec. 6 as device routines that
+// any group of whole warps can run: breadth-first search, connected
+// components and the 2BFS pseudo-diameter.  The group is given by a thread
+// index tid in [0, T) (warp-aligned) and a bounded barrier `sync` over the
+// group; the standalone kernels use a grid barrier over whole blocks, the
+// fused stage-1 kernel one warp per block.
+//
+// BFS is level-synchronous: the frontier of level L is a queue; each thread
+// expands one frontier vertex with a warp-uniform trip count, claims
+// neighbours in groups of 8 with atomicCAS on dist, and reserves queue space
+// for a whole warp with one atomicAdd.  Distances are exact and do not
+// depend on scheduling.
+//
+// 2BFS readings: s = vertex 0 (the smallest vertex of its component); the
+// farthest vertex t is the smallest index at maximal distance (atomicMax over
+// the key (dist, ~index)).  If the first BFS misses vertices, components are
+// labelled by their smallest vertex (label propagation with pointer
+// jumping) and 2BFS runs in every component at once from multi-source
+// frontiers; l~ is the largest second-BFS level.
+#pragma once
+#include "common.cuh"
+
+namespace mpcg {
+
+enum BfsSources { kSrcSingle = 0, kSrcRoots = 2, kSrcRootFar = 3 };
+enum BfsRole { kRoleFirst = 0, kRoleSecond = 1, kRoleComponentFirst = 2, kRolePlain = 3 };
+
+struct BfsGraph {
+  Ctl* ctl;
+  const int32_t* rp;
+  const int32_t* col;
+  int n;
+  int32_t *fq0, *fq1, *label;
+  unsigned long long* ckey;
+};
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Whole blocks, every thread of the grid: the library's grid barrier.
+struct GridSync {
+  Ctl* ctl;
+  int slot;
+  unsigned long long round;
+  __device__ bool operator()() { return grid_barrier(ctl, slot, round); }
+};
+
+// One warp per block: lane 0 arrives on the counter and polls (bounded).
+struct WarpGroupSync {
+  Ctl* ctl;
+  int slot;
+  unsigned long long round;
+  __device__ bool operator()() {
+    __syncwarp();
+    round += 1;
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+      const unsigned long long target = round * (unsigned long long)gridDim.x;
+      red_release_add(&ctl->bar[slot], 1ull);
+      if (ld_acquire(&ctl->bar[slot]) < target) {
+        const unsigned long long t0 = globaltimer();
+        unsigned spins = 0;
+        while (ld_acquire(&ctl->bar[slot]) < target) {
+          if ((++spins & 1023u) == 0) {
+            if (volatile_status(ctl) != 0) {
+              ok = 0;
+              break;
+            }
+            if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
+              set_status(ctl, MPCG_ERR_TIMEOUT);
+              ok = 0;
+              break;
+            }
+          }
+        }
+      }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+  }
+};
+
+// One BFS over the group.  Writes dist (all n entries), and by role: the
+// farthest-vertex key and the reached count (first), per-component keys
+// (component-first) or the largest level (second) in the control block.
+template <class Sync>
+__device__ bool bfs_run(const BfsGraph& g, int32_t* dist, int sources, int src, int role, int tid,
+                        int T, Sync& sync) {
+  Ctl* ctl = g.ctl;
+  const int n = g.n;
+  const int lane = threadIdx.x & 31;
+  const int wbase = tid - lane;
+  for (int v = tid; v < n; v += T) dist[v] = -1;
+  if (tid == 0) {
+    ctl->qsize[0] = 0;
+    ctl->qsize[1] = 0;
+    ctl->qsize[2] = 0;
+  }
+  if (!sync()) return false;
+  if (sources == kSrcSingle) {
+    if (tid == 0) {
+      dist[src] = 0;
+      g.fq0[0] = src;
+      ctl->qsize[0] = 1;
+    }
+  } else {
+    for (int base = wbase; base < n; base += T) {  // warp-uniform bound
+      const int v = base + lane;
+      const bool root = v < n && g.label[v] == v;
+      int s = v;
+      if (root && sources == kSrcRootFar) s = far_key_vertex(g.ckey[v]);
+      if (root) dist[s] = 0;
+      const unsigned mask = __ballot_sync(0xffffffffu, root);
+      if (mask) {
+        int b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&ctl->qsize[0], __popc(mask));
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        if (root) g.fq0[b0 + __popc(mask & ((1u << lane) - 1u))] = s;
+      }
+    }
+  }
+  if (!sync()) return false;
+
+  int level = 0;
+  long long reached = 0;
+  for (;;) {
+    const int32_t* in = (level & 1) ? g.fq1 : g.fq0;
+    int32_t* out = (level & 1) ? g.fq0 : g.fq1;
+    const int size = *reinterpret_cast<volatile int*>(&ctl->qsize[level % 3]);
+    if (size == 0) break;
+    reached += size;
+    if (tid == 0) ctl->qsize[(level + 2) % 3] = 0;
+    int* cnt = &ctl->qsize[(level + 1) % 3];
+    for (int base = wbase; base < size; base += T) {
+      const int idx = base + lane;
+      int u = -1, e0 = 0, deg = 0;
+      if (idx < size) {
+        u = in[idx];
+        e0 = g.rp[u];
+        deg = g.rp[u + 1] - e0;
+      }
+      const int maxdeg = __reduce_max_sync(0xffffffffu, deg);
+      for (int k0 = 0; k0 < maxdeg; k0 += 8) {
+        int w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = (k0 + j < deg) ? g.col[e0 + k0 + j] : -1;
+        bool push[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          push[j] = w[j] >= 0 && w[j] != u && atomicCAS(&dist[w[j]], -1, level + 1) == -1;
+        int mine = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mine += push[j] ? 1 : 0;
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total > 0) {
+          int b0 = 0;
+          if (lane == 0) b0 = atomicAdd(cnt, total);
+          int pos = __shfl_sync(0xffffffffu, b0, 0) + incl - mine;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (push[j]) out[pos++] = w[j];
+        }
+      }
+    }
+    ++level;
+    if (!sync()) return false;
+  }
+  const int maxlevel = level - 1;  // levels 0 .. level-1 were non-empty
+
+  if (role == kRoleFirst) {
+    unsigned long long best = 0;
+    for (int v = tid; v < n; v += T) {
+      const int d = dist[v];
+      if (d >= 0) {
+        const unsigned long long k = far_key(d, v);
+        best = k > best ? k : best;
+      }
+    }
+    best = warp_max_u64(best);
+    if (lane == 0 && best) atomicMax(&ctl->key, best);
+    if (tid == 0) ctl->reached = (int)reached;
+  } else if (role == kRoleComponentFirst) {
+    for (int v = tid; v < n; v += T) {
+      const int d = dist[v];
+      if (d >= 0) atomicMax(&g.ckey[g.label[v]], far_key(d, v));
+    }
+  } else if (role == kRoleSecond) {
+    if (tid == 0) ctl->pdiam = maxlevel > 0 ? maxlevel : 0;
+  }
+  return true;
+}
+
+// Connected components: label[v] = smallest vertex of v's component.
+// Rounds of (hook: for every edge with differing labels, lower the larger
+// label's entry to the smaller label) and (pointer jumping to the root),
+// until a hook round changes nothing.  Labels only decrease and always name
+// a vertex of the same component, so a component's root is its smallest
+// vertex.
+template <class Sync>
+__device__ bool cc_run(const BfsGraph& g, int tid, int T, Sync& sync) {
+  Ctl* ctl = g.ctl;
+  const int n = g.n;
+  const int lane = threadIdx.x & 31;
+  int32_t* label = g.label;
+  for (int v = tid; v < n; v += T) {
+    label[v] = v;
+    g.ckey[v] = 0ull;
+  }
+  if (tid == 0) {
+    ctl->ccflag[0] = 0;
+    ctl->ccflag[1] = 0;
+  }
+  if (!sync()) return false;
+  for (int r = 0;; ++r) {
+    int changed = 0;
+    for (int u = tid; u < n; u += T) {
+      const int e1 = g.rp[u + 1];
+      for (int e = g.rp[u]; e < e1; ++e) {
+        const int v = g.col[e];
+        if (v == u) continue;
+        const int lu = label[u], lv = label[v];
+        if (lu < lv) {
+          atomicMin(&label[lv], lu);
+          changed = 1;
+        } else if (lv < lu) {
+          atomicMin(&label[lu], lv);
+          changed = 1;
+        }
+      }
+    }
+    if (__any_sync(0xffffffffu, changed) && lane == 0) atomicExch(&ctl->ccflag[r & 1], 1);
+    if (!sync()) return false;
+    if (tid == 0) ctl->ccflag[(r + 1) & 1] = 0;
+    for (int v = tid; v < n; v += T) {
+      int l = label[v];
+      for (int ll = label[l]; ll != l; ll = label[l]) l = ll;
+      label[v] = l;
+    }
+    if (!sync()) return false;
+    if (*reinterpret_cast<volatile int*>(&ctl->ccflag[r & 1]) == 0) break;
+  }
+  return true;
+}
+
+// 2BFS pseudo-diameter with the per-component rule.  On return (true),
+// ctl->pdiam holds l~ and ctl->far_t the farthest vertex found from vertex 0.
+template <class Sync>
+__device__ bool pseudo_diameter_run(const BfsGraph& g, int32_t* d1, int32_t* d2, int tid, int T,
+                                    Sync& sync) {
+  Ctl* ctl = g.ctl;
+  if (tid == 0) ctl->key = 0ull;
+  if (!sync()) return false;
+  if (!bfs_run(g, d1, kSrcSingle, 0, kRoleFirst, tid, T, sync)) return false;
+  if (!sync()) return false;
+  const bool connected = *reinterpret_cast<volatile int*>(&ctl->reached) == g.n;
+  if (connected) {
+    const int t = far_key_vertex(*reinterpret_cast<volatile unsigned long long*>(&ctl->key));
+    if (tid == 0) ctl->far_t = t;
+    if (!bfs_run(g, d2, kSrcSingle, t, kRoleSecond, tid, T, sync)) return false;
+  } else {
+    if (!cc_run(g, tid, T, sync)) return false;
+    if (!bfs_run(g, d1, kSrcRoots, 0, kRoleComponentFirst, tid, T, sync)) return false;
+    if (!sync()) return false;
+    if (!bfs_run(g, d2, kSrcRootFar, 0, kRoleSecond, tid, T, sync)) return false;
+    if (tid == 0) ctl->far_t = far_key_vertex(g.ckey[0]);
+  }
+  if (tid == 0) ctl->connected = connected ? 1 : 0;
+  return true;
+}
+
+}  // namespace mpcg

@@ -79,6 +79,7 @@ struct CgArgs {
   float *x32, *r32, *da, *db, *q32;
   const double* b64;
   double *x64, *r64, *d64, *q64;
+  float* snap;  // stage-1 snapshots of x~ ([slot][n]); ctl->x32_src picks one
 };
 
 template <typename T>
@@ -95,8 +96,9 @@ __device__ __forceinline__ double stop_measure(double rr, double bnorm, int rel)
 // ---------------------------------------------------------------------------------------
 // Consumer-group synchronisation (named barrier 1, consumer warps only).
 // ---------------------------------------------------------------------------------------
+template <int NC>
 __device__ __forceinline__ void cbar() {
-  asm volatile("bar.sync 1, %0;" ::"r"(kNC * 32) : "memory");
+  asm volatile("bar.sync 1, %0;" ::"r"(NC * 32) : "memory");
 }
 
 // Shared scratch of the consumer group: per-thread partials and the values
@@ -104,28 +106,31 @@ __device__ __forceinline__ void cbar() {
 // (alpha, beta, the stop test) are computed once per block by thread 0 (they
 // are the same in every block: same totals, same operations), which keeps
 // the slow FP64 units free of redundant work.
+template <int NC>
 struct CShared {
-  double part[kNC * 32];
-  float ffp[2 * kNC];
+  double part[NC * 32];
+  float ffp[2 * NC];
   double rr, val;
   float alpha, beta;
   int dec;
   int ok;
+  int aux;
 };
 
 // Block partial of float-float sums, valid in thread 0 (float ops only until
 // the final conversion).
-__device__ __forceinline__ double block_ff(FF v, CShared& S) {
+template <int NC>
+__device__ __forceinline__ double block_ff(FF v, CShared<NC>& S) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   v = ff_warp_sum(v);
   if (lane == 0) {
     S.ffp[2 * warp] = v.hi;
     S.ffp[2 * warp + 1] = v.lo;
   }
-  cbar();
+  cbar<NC>();
   double r = 0.0;
   if (warp == 0) {
-    FF t = lane < kNC ? FF{S.ffp[2 * lane], S.ffp[2 * lane + 1]} : FF{0.f, 0.f};
+    FF t = lane < NC ? FF{S.ffp[2 * lane], S.ffp[2 * lane + 1]} : FF{0.f, 0.f};
     t = ff_warp_sum(t);
     r = (double)t.hi + (double)t.lo;
   }
@@ -134,15 +139,16 @@ __device__ __forceinline__ double block_ff(FF v, CShared& S) {
 
 // Block partial of per-thread doubles, valid in thread 0 (one warp adds them
 // in a fixed order).
-__device__ __forceinline__ double block_d(double p, CShared& S) {
+template <int NC>
+__device__ __forceinline__ double block_d(double p, CShared<NC>& S) {
   const int lane = threadIdx.x & 31;
   S.part[threadIdx.x] = p;
-  cbar();
+  cbar<NC>();
   double r = 0.0;
   if (threadIdx.x < 32) {
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < kNC; ++j) s += S.part[lane + 32 * j];
+    for (int j = 0; j < NC; ++j) s += S.part[lane + 32 * j];
     r = warp_sum(s);
   }
   return r;
@@ -150,9 +156,10 @@ __device__ __forceinline__ double block_d(double p, CShared& S) {
 
 // Grid barrier among the consumer groups of all blocks; bounded; also stops
 // when another block has recorded an error.
+template <int NC>
 __device__ __forceinline__ bool cgrid_barrier(Ctl* ctl, int slot, unsigned long long& round,
                                               int* s_ok) {
-  cbar();
+  cbar<NC>();
   round += 1;
   if (threadIdx.x == 0) {
     const unsigned long long target = round * (unsigned long long)gridDim.x;
@@ -177,20 +184,21 @@ __device__ __forceinline__ bool cgrid_barrier(Ctl* ctl, int slot, unsigned long 
     }
     *s_ok = ok;
   }
-  cbar();
+  cbar<NC>();
   return *s_ok != 0;
 }
 
 // Grid-wide sum of the block partials (block partial valid in thread 0;
 // alternating halves of `partials`).  The total is valid in thread 0; the
 // caller derives its scalars there and broadcasts them with cbar().
+template <int NC>
 __device__ __forceinline__ double cgrid_total(double block_part, double* partials, int& red,
                                               Ctl* ctl, int slot, unsigned long long& round,
-                                              CShared& S, bool& ok) {
+                                              CShared<NC>& S, bool& ok) {
   double* buf = partials + (red & 1) * kMaxGrid;
   ++red;
   if (threadIdx.x == 0) buf[blockIdx.x] = block_part;
-  ok = cgrid_barrier(ctl, slot, round, &S.ok);
+  ok = cgrid_barrier<NC>(ctl, slot, round, &S.ok);
   double s = 0.0;
   if (threadIdx.x < 32) {
     for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) s += buf[i];
@@ -358,13 +366,13 @@ __device__ __forceinline__ bool fast_w(uint32_t wf) {
 // flight together; a step never needs more than two chunks at once (the ring
 // has at least four), which keeps the producer/consumer ring free of
 // deadlock.  Returns false if a wait failed.
-template <typename T, class Gather, class Row>
+template <int NC, typename T, class Gather, class Row>
 __device__ __forceinline__ bool ring_spmv(const CgArgs& a, Ring<T>& R, Cursor& C, int S0, int S1,
                                           Gather G, Row Rw) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   bool ok = true;
-  for (int s0 = S0 + warp; s0 < S1; s0 += 2 * kNC) {
-    const int s1 = s0 + kNC;
+  for (int s0 = S0 + warp; s0 < S1; s0 += 2 * NC) {
+    const int s1 = s0 + NC;
     const bool h1 = s1 < S1;
     const uint32_t wf0 = a.slice_w[s0];
     const uint32_t wf1 = h1 ? a.slice_w[s1] : 0u;
@@ -430,7 +438,7 @@ __device__ __forceinline__ bool ring_spmv(const CgArgs& a, Ring<T>& R, Cursor& C
 
 // Set-up common to both stages: the ring in dynamic shared memory, the
 // block's slice range and element range, barrier initialisation.
-template <typename T>
+template <int NC, typename T>
 __device__ __forceinline__ void ring_setup(const CgArgs& a, char* smem, Ring<T>& R, int& S0,
                                            int& S1) {
   constexpr int S = Ring<T>::S;
@@ -446,7 +454,7 @@ __device__ __forceinline__ void ring_setup(const CgArgs& a, char* smem, Ring<T>&
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&R.full[s], 1);
-      mbar_init(&R.empty[s], kNC);
+      mbar_init(&R.empty[s], NC);
     }
     *R.stop = 0;
     mbar_fence_init();
@@ -455,14 +463,15 @@ __device__ __forceinline__ void ring_setup(const CgArgs& a, char* smem, Ring<T>&
 }
 
 // Rows [R0, R1) of consumer warp `warp` inside the block's row range.
+template <int NC>
 __device__ __forceinline__ void warp_rows(int S0, int S1, int n, int& R0, int& R1) {
   const int warp = threadIdx.x >> 5;
   const int B0 = S0 * kSlice, B1 = min(S1 * kSlice, n);
   const int rows = max(0, B1 - B0);
   // split in multiples of 4 rows so that 16-byte vectors stay aligned
   const int q4 = (rows + 3) >> 2;
-  R0 = B0 + 4 * (int)((long long)q4 * warp / kNC);
-  R1 = min(B1, B0 + 4 * (int)((long long)q4 * (warp + 1) / kNC));
+  R0 = B0 + 4 * (int)((long long)q4 * warp / NC);
+  R1 = min(B1, B0 + 4 * (int)((long long)q4 * (warp + 1) / NC));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -527,8 +536,9 @@ __device__ __forceinline__ void p2_32(const CgArgs& a, int R0, int R1, int lane,
 enum Dec { kGo = 0, kStop = 1, kNan = 2, kBroke = 3, kBreakdown = 4 };
 
 __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
+  constexpr int NC = kNC;
   extern __shared__ __align__(128) char smem[];
-  __shared__ CShared S;
+  __shared__ CShared<NC> S;
   Ctl* ctl = a.ctl;
   if (volatile_status(ctl) != 0 || ctl->trivial) return;
   if (a.mode == kCgContinue && ctl->broke32) {  // stage 1 already ended in the k0 phase
@@ -540,9 +550,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
   }
   Ring<float> R;
   int S0, S1;
-  ring_setup(a, smem, R, S0, S1);
+  ring_setup<NC>(a, smem, R, S0, S1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp == kNC) {
+  if (warp == NC) {
     if (lane == 0) ring_producer(a, R);
     return;
   }
@@ -550,7 +560,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
   const bool lead0 = lead && blockIdx.x == 0;   // writes the control block
   Cursor C{0u, 0u, 0u};
   int R0, R1;
-  warp_rows(S0, S1, a.n, R0, R1);
+  warp_rows<NC>(S0, S1, a.n, R0, R1);
   const int n = a.n;
   const int rel = ctl->tol_relative;
   unsigned long long round = 0;
@@ -579,7 +589,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
         if (!isfinite(S.val)) set_status(ctl, MPCG_ERR_NAN);
       }
     }
-    cbar();
+    cbar<NC>();
     rr = S.rr;
     bnorm = S.val;
     first = 1;
@@ -609,7 +619,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
       S.dec = dec;
       if (dec == kNan && lead0) set_status(ctl, MPCG_ERR_NAN);
     }
-    cbar();
+    cbar<NC>();
     if (S.dec != kGo) break;
 
     // ---- P1: q = A d_k with d_k = r_k + beta_k d_{k-1} formed on the fly ----
@@ -632,7 +642,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
         ff_add_prod(pdq, di, acc);
       }
     };
-    const bool pass_ok = ring_spmv<float>(a, R, C, S0, S1, G, Rw);
+    const bool pass_ok = ring_spmv<NC, float>(a, R, C, S0, S1, G, Rw);
     if (!pass_ok) set_status(ctl, MPCG_ERR_TIMEOUT);
     {
       const double dq = cgrid_total(block_ff(pdq, S), a.partials, red, ctl, a.slot, round, S, ok);
@@ -644,7 +654,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
         S.dec = dec;
         if (dec == kNan && lead0) set_status(ctl, MPCG_ERR_NAN);
       }
-      cbar();
+      cbar<NC>();
     }
     if (!ok) break;
     if (S.dec == kBroke) {
@@ -671,7 +681,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
         }
         S.dec = dec;
       }
-      cbar();
+      cbar<NC>();
     }
     if (!ok || S.dec != kGo) break;
     if (a.mode == kCgK0) ++k0done;
@@ -761,24 +771,25 @@ __device__ __forceinline__ void p3_64(const CgArgs& a, int R0, int R1, int lane,
 enum Pass64 { kRestart = 0, kTrueRes = 1, kIterate = 2, kFinalRes = 3, kDone = 4 };
 
 __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
+  constexpr int NC = kNC;
   extern __shared__ __align__(128) char smem[];
-  __shared__ CShared S;
+  __shared__ CShared<NC> S;
   Ctl* ctl = a.ctl;
   if (volatile_status(ctl) != 0) return;
   Ring<double> R;
   int S0, S1;
-  ring_setup(a, smem, R, S0, S1);
+  ring_setup<NC>(a, smem, R, S0, S1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = a.n;
   if (ctl->trivial) {  // b = 0: x = 0 solves A x = b exactly
-    if (warp < kNC) {
+    if (warp < NC) {
       int R0, R1;
-      warp_rows(S0, S1, n, R0, R1);
+      warp_rows<NC>(S0, S1, n, R0, R1);
       for (int i = R0 + lane; i < R1; i += kSlice) a.x64[i] = 0.0;
     }
     return;
   }
-  if (warp == kNC) {
+  if (warp == NC) {
     if (lane == 0) ring_producer(a, R);
     return;
   }
@@ -786,7 +797,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
   const bool lead0 = lead && blockIdx.x == 0;
   Cursor C{0u, 0u, 0u};
   int R0, R1;
-  warp_rows(S0, S1, n, R0, R1);
+  warp_rows<NC>(S0, S1, n, R0, R1);
   const int rel = ctl->tol_relative;
   const double bnorm = ctl->bnorm64;
   const double eps2 = ctl->eps2;
@@ -801,8 +812,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
   double rr = 0.0;                 // thread 0
 
   // Promote: x0 = float64(x~) (or 0).
-  for (int i = R0 + lane; i < R1; i += kSlice) a.x64[i] = a.mode ? 0.0 : (double)a.x32[i];
-  ok = cgrid_barrier(ctl, a.slot, round, &S.ok);
+  {
+    const int src = ctl->x32_src;
+    const float* xs = src >= 0 ? a.snap + (size_t)src * n : a.x32;
+    for (int i = R0 + lane; i < R1; i += kSlice) a.x64[i] = a.mode ? 0.0 : (double)xs[i];
+  }
+  ok = cgrid_barrier<NC>(ctl, a.slot, round, &S.ok);
 
   // One SpMV pass per step; its kind is decided by thread 0 and broadcast.
   //   kRestart:  r = b - A x, d = r, r^T r      (CG line 1 from x)
@@ -838,7 +853,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
           }
         }
       };
-      if (!ring_spmv<double>(a, R, C, S0, S1, G, Rw)) set_status(ctl, MPCG_ERR_TIMEOUT);
+      if (!ring_spmv<NC, double>(a, R, C, S0, S1, G, Rw)) set_status(ctl, MPCG_ERR_TIMEOUT);
     }
     const double tot = cgrid_total(block_d(p, S), a.partials, red, ctl, a.slot, round, S, ok);
     if (!ok) break;
@@ -870,7 +885,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
       }
       S.dec = next;
     }
-    cbar();
+    cbar<NC>();
     int next = S.dec;
 
     if (kind == kIterate && next == kIterate) {
@@ -888,11 +903,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
           S.dec = -1;
         }
       }
-      cbar();
+      cbar<NC>();
       if (!ok || S.dec == kDone) break;
       // ---- P3: d = r + beta d ----
       p3_64(a, R0, R1, lane, S.val);
-      ok = cgrid_barrier(ctl, a.slot, round, &S.ok);
+      ok = cgrid_barrier<NC>(ctl, a.slot, round, &S.ok);
       ++it;
       next = -1;
     } else if (next == kTrueRes + 100) {
@@ -902,7 +917,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
         a.r64[i] = ri;
         a.d64[i] = ri;
       }
-      ok = cgrid_barrier(ctl, a.slot, round, &S.ok);
+      ok = cgrid_barrier<NC>(ctl, a.slot, round, &S.ok);
       next = -1;
     }
     if (next == -1) {  // loop head: stop test on the recursive residual
@@ -920,7 +935,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
         }
         S.dec = nk;
       }
-      cbar();
+      cbar<NC>();
       next = S.dec;
     }
     kind = next;
@@ -940,13 +955,394 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
 }
 
 
+// ---------------------------------------------------------------------------------------
+// Fused single-precision stage of Algorithm II.
+//
+// The 2BFS of Sec. 6 is a chain of grid-wide levels (latency-bound); CG is
+// bandwidth-bound.  This kernel runs them side by side: in every block one
+// feature warp runs the 2BFS (with the component rule) on its own bounded
+// barrier, and in block 0 it then runs the kNN vote once v (Eq. 13) is
+// known; fourteen consumer warps run CG from x~0 = 0 meanwhile.
+//
+// Past the k0 iterations the consumers keep iterating before the label is
+// known.  For every class t present in the sample they record the first
+// iteration j >= k0 whose stop measure is <= 10^-t and keep a snapshot of x~
+// there.  Once the label t is known, stage 1 ends at its recorded iteration
+// with its snapshot, or iterates on until 10^-t is met.  The iterates of CG
+// do not depend on when eps1 becomes known, so this gives the same N1 and the
+// same x~ as running k0 iterations, the kNN, and CG from iterate k0 to eps1.
+// When every present class has been met, or the snapshot slots run out, or
+// the iteration cap is reached, the consumers wait for the label (bounded).
+// The label reaches every block at the same reduction through the reduction
+// buffer (one extra slot written by block 0), so all blocks take the same
+// decisions.
+// ---------------------------------------------------------------------------------------
+constexpr int kNC1 = 14;      // consumer warps; warp 14 = feature warp, warp 15 = producer
+constexpr int kSnapSlots = 6; // snapshots of x~ kept in the workspace
+
+struct Stage1Args {
+  CgArgs a;
+  BfsGraph g;
+  int32_t *d1, *d2;
+  KnnSpec knn;
+  int bfs_slot;
+};
+
+// Thread 0: wait (bounded) until the feature warp has published the label.
+// Returns t >= 0, or -1 on failure (status set).
+__device__ __forceinline__ int wait_label(Ctl* ctl) {
+  const volatile int* p = &ctl->eps1_ready;
+  const unsigned long long t0 = globaltimer();
+  unsigned spins = 0;
+  while (true) {
+    const int label = *p;
+    if (label > 0) return label - 1;
+    if (label < 0) return -1;
+    if ((++spins & 255u) == 0) {
+      if (volatile_status(ctl) != 0) return -1;
+      if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
+        set_status(ctl, MPCG_ERR_TIMEOUT);
+        return -1;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
+  constexpr int NC = kNC1;
+  extern __shared__ __align__(128) char smem[];
+  __shared__ CShared<NC> S;
+  __shared__ volatile int s_k0_ready;
+  __shared__ double s_v;
+  __shared__ unsigned s_cmask;
+  const CgArgs& a = sa.a;
+  Ctl* ctl = a.ctl;
+  if (volatile_status(ctl) != 0 || ctl->trivial) return;
+  if (threadIdx.x == 0) {
+    s_k0_ready = 0;
+    s_cmask = 0u;
+  }
+  Ring<float> R;
+  int S0, S1;
+  ring_setup<NC>(a, smem, R, S0, S1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == NC + 1) {
+    if (lane == 0) ring_producer(a, R);
+    return;
+  }
+  if (warp == NC) {
+    // ---- feature warp: 2BFS over the grid's feature warps ----
+    WarpGroupSync sync{ctl, sa.bfs_slot, 0ull};
+    const bool ok = pseudo_diameter_run(sa.g, sa.d1, sa.d2, blockIdx.x * 32 + lane,
+                                        gridDim.x * 32, sync);
+    if (blockIdx.x != 0) return;
+    // ---- block 0: wait for v from this block's consumers, then the kNN ----
+    int have_v = 0;
+    if (ok && lane == 0) {
+      const unsigned long long t0 = globaltimer();
+      unsigned spins = 0;
+      while (true) {
+        if (s_k0_ready) {
+          have_v = 1;
+          break;
+        }
+        if ((++spins & 255u) == 0) {
+          if (volatile_status(ctl) != 0) break;
+          if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
+            set_status(ctl, MPCG_ERR_TIMEOUT);
+            break;
+          }
+        }
+      }
+    }
+    // lane 0 wrote l~ (the last 2BFS level) and observed v; it broadcasts both
+    double pd = 0.0, v = 0.0;
+    if (have_v) {
+      __threadfence_block();
+      pd = (double)*reinterpret_cast<volatile int*>(&ctl->pdiam);
+      v = *reinterpret_cast<volatile double*>(&s_v);
+    }
+    have_v = __shfl_sync(0xffffffffu, have_v, 0);
+    pd = __shfl_sync(0xffffffffu, pd, 0);
+    v = __shfl_sync(0xffffffffu, v, 0);
+    int t = -1;
+    if (have_v) {
+      const double chi[4] = {(double)a.n, (double)ctl->nnz, pd, v};
+      t = knn_warp(sa.knn, chi);
+    }
+    if (lane == 0) {
+      if (t >= 0) {
+        ctl->cls = t;
+        ctl->eps1 = pow10_neg(t);
+      } else if (have_v) {
+        set_status(ctl, MPCG_ERR_INVALID_ARG);  // invalid query, sample or label
+      }
+      ctl->t_features = globaltimer();
+      __threadfence();
+      atomicExch(&ctl->eps1_ready, t >= 0 ? t + 1 : -1);
+    }
+    return;
+  }
+
+  // ---- consumers ----
+  const bool lead = threadIdx.x == 0;
+  const bool lead0 = lead && blockIdx.x == 0;
+  Cursor C{0u, 0u, 0u};
+  int R0, R1;
+  warp_rows<NC>(S0, S1, a.n, R0, R1);
+  const int n = a.n;
+  const int rel = ctl->tol_relative;
+  const int k0 = ctl->k0, max1 = ctl->max1;
+  const double eps2 = ctl->eps2;
+  unsigned long long round = 0;
+  int red = 0;
+  bool ok = true;
+
+  // Classes present in the sample (block 0 reads the labels; the mask rides
+  // along the first reduction).
+  if (blockIdx.x == 0) {
+    unsigned cm = 0u;
+    for (int i = threadIdx.x; i < sa.knn.count; i += NC * 32) {
+      const int c = sa.knn.cls[i];
+      if (c >= 0 && c < 16) cm |= 1u << c;
+    }
+    cm = __reduce_or_sync(0xffffffffu, cm);
+    if (lane == 0 && cm) atomicOr(&s_cmask, cm);
+  }
+
+  // CG line 1: x0 = 0, r0 = b~, d_{-1} = 0 (so that d_0 = fma(0, 0, r0) = r0).
+  FF acc{0.f, 0.f};
+  for (int i = R0 + lane; i < R1; i += kSlice) {
+    const float bi = a.b32[i];
+    a.x32[i] = 0.0f;
+    a.r32[i] = bi;
+    a.da[i] = 0.0f;
+    ff_add_prod(acc, bi, bi);
+  }
+  double rr, bnorm;
+  unsigned cmask = 0u;  // thread 0
+  {
+    double* buf = a.partials + (red & 1) * kMaxGrid;
+    const double bp = block_ff(acc, S);  // all consumer warps past the mask
+    if (lead0) buf[gridDim.x] = (double)s_cmask;
+    const double tot = cgrid_total(bp, a.partials, red, ctl, a.slot, round, S, ok);
+    if (lead) {
+      cmask = (unsigned)buf[gridDim.x];
+      S.rr = tot;
+      S.val = sqrt(tot);
+      if (lead0) {
+        ctl->bnorm32 = S.val;
+        if (!isfinite(S.val)) set_status(ctl, MPCG_ERR_NAN);
+      }
+    }
+    cbar<NC>();
+    rr = S.rr;
+    bnorm = S.val;
+    if (!isfinite(bnorm)) ok = false;
+  }
+  float beta = 0.0f;
+  int parity = 0, first = 1, it = 0;
+  // thread 0 only:
+  double vsum = 0.0, m = 0.0;
+  int k0done = 0, in_k0 = 1, cls = -1, nslots = 0;
+  int nt[16], snap_it[kSnapSlots];
+  double res_at[16];
+  for (int t = 0; t < 16; ++t) {
+    nt[t] = -1;
+    res_at[t] = 0.0;
+  }
+  enum { kGoOn = 0, kEnd = 1, kFailed = 2, kBrokeDown = 3 };
+  int broke = 0;
+
+  while (ok) {
+    if (lead) {
+      m = stop_measure(rr, bnorm, rel);
+      int dec = kGoOn, snap_slot = -1;
+      if (isnan(m)) {
+        dec = kFailed;
+        if (lead0) set_status(ctl, MPCG_ERR_NAN);
+      } else {
+        if (in_k0 && (it >= min(k0, max1) || m <= eps2 || rr == 0.0)) {
+          in_k0 = 0;  // end of the k0 phase: v of Eq. (13) for the kNN
+          if (lead0) {
+            ctl->k0_done = k0done;
+            ctl->vsum = vsum;
+            ctl->v = k0done > 0 ? vsum / (double)k0done : 0.0;
+            s_v = ctl->v;
+            __threadfence_block();
+            s_k0_ready = 1;
+          }
+        }
+        if (!in_k0) {
+          bool fresh = false, all = true;
+          for (int t = 0; t < 16; ++t) {
+            if (!((cmask >> t) & 1u)) continue;
+            if (nt[t] < 0 && m <= pow10_neg(t)) {
+              nt[t] = it;
+              res_at[t] = m;
+              fresh = true;
+            }
+            if (nt[t] < 0) all = false;
+          }
+          if (cls < 0 && (all || it >= max1 || (fresh && nslots >= kSnapSlots))) {
+            cls = wait_label(ctl);
+            if (cls < 0) dec = kFailed;
+          }
+          if (dec == kGoOn) {
+            if (cls < 0) {
+              if (fresh) {
+                snap_slot = nslots;
+                snap_it[nslots++] = it;
+              }
+            } else if (nt[cls] >= 0 || it >= max1) {
+              dec = kEnd;
+            }
+          }
+        }
+      }
+      S.dec = dec;
+      S.aux = snap_slot;
+    }
+    cbar<NC>();
+    const int dec = S.dec;
+    const int snap_slot = S.aux;
+    if (snap_slot >= 0) {
+      float* dst = a.snap + (size_t)snap_slot * n;
+      for (int i = R0 + lane; i < R1; i += kSlice) dst[i] = a.x32[i];
+    }
+    if (dec != kGoOn) {
+      if (dec == kFailed) ok = false;
+      break;
+    }
+
+    // ---- P1: q = A d_k with d_k = r_k + beta_k d_{k-1} formed on the fly ----
+    const float* dold = parity ? a.db : a.da;
+    float* dnew = parity ? a.da : a.db;
+    const float* r = a.r32;
+    float* q = a.q32;
+    FF pdq{0.f, 0.f};
+    const float bt = first ? 0.0f : beta;
+    auto G = [&](int c) -> float { return __fmaf_rn(bt, dold[c], r[c]); };
+    auto Rw = [&](int i, float accv) {
+      if (i < n) {
+        const float di = __fmaf_rn(bt, dold[i], r[i]);
+        dnew[i] = di;
+        q[i] = accv;
+        ff_add_prod(pdq, di, accv);
+      }
+    };
+    if (!ring_spmv<NC, float>(a, R, C, S0, S1, G, Rw)) set_status(ctl, MPCG_ERR_TIMEOUT);
+    {
+      const double dq = cgrid_total(block_ff(pdq, S), a.partials, red, ctl, a.slot, round, S, ok);
+      if (lead) {
+        int d2 = kGoOn;
+        if (!isfinite(dq)) {
+          d2 = kFailed;
+          if (lead0) set_status(ctl, MPCG_ERR_NAN);
+        } else if (!(dq > 0.0)) {
+          d2 = kBrokeDown;  // stage 1 ends here; x~ and r are unchanged
+        } else {
+          S.alpha = (float)(rr / dq);
+        }
+        S.dec = d2;
+      }
+      cbar<NC>();
+    }
+    if (!ok || S.dec == kFailed) {
+      ok = false;
+      break;
+    }
+    if (S.dec == kBrokeDown) {
+      broke = 1;
+      break;
+    }
+    const float alpha = S.alpha;
+
+    // ---- P2: x += alpha d_k, r -= alpha q, r^T r; the label rides along ----
+    FF prr{0.f, 0.f};
+    p2_32(a, R0, R1, lane, dnew, alpha, prr);
+    {
+      double* buf = a.partials + (red & 1) * kMaxGrid;
+      const double bp = block_ff(prr, S);
+      if (lead0) buf[gridDim.x] = (double)*reinterpret_cast<volatile int*>(&ctl->eps1_ready);
+      const double rrn = cgrid_total(bp, a.partials, red, ctl, a.slot, round, S, ok);
+      if (lead) {
+        const int label = (int)buf[gridDim.x];
+        int d3 = kGoOn;
+        if (label < 0) {
+          d3 = kFailed;
+        } else if (!isfinite(rrn)) {
+          d3 = kFailed;
+          if (lead0) set_status(ctl, MPCG_ERR_NAN);
+        } else {
+          if (label > 0) cls = label - 1;
+          if (in_k0) {
+            vsum += sqrt(rrn) / sqrt(rr);  // Eq. (13) ratio ||r_i|| / ||r_{i-1}||
+            ++k0done;
+          }
+          S.beta = (float)(rrn / rr);
+          S.rr = rrn;
+        }
+        S.dec = d3;
+      }
+      cbar<NC>();
+    }
+    if (!ok || S.dec != kGoOn) {
+      ok = false;
+      break;
+    }
+    beta = S.beta;
+    rr = S.rr;
+    parity ^= 1;
+    first = 0;
+    ++it;
+  }
+
+  if (lead) {
+    if (ok && broke && in_k0 && lead0) {  // breakdown in the k0 phase: v over completed ratios
+      ctl->k0_done = k0done;
+      ctl->vsum = vsum;
+      ctl->v = k0done > 0 ? vsum / (double)k0done : 0.0;
+      s_v = ctl->v;
+      __threadfence_block();
+      s_k0_ready = 1;
+    }
+    if (ok && cls < 0) {
+      cls = wait_label(ctl);
+      if (cls < 0) ok = false;
+    }
+    if (lead0 && ok) {
+      // Stage 1 ends at the first iteration >= k0 that met eps1 = 10^-t, with
+      // its iterate; otherwise (iteration cap, breakdown) at the current one.
+      const double eps1 = pow10_neg(cls);
+      int n1 = it, src = -1;
+      double res = m;
+      if (!in_k0 && nt[cls] >= 0 && nt[cls] < it) {
+        n1 = nt[cls];
+        res = res_at[cls];
+        for (int k = 0; k < nslots; ++k)
+          if (snap_it[k] == n1) src = k;
+        if (src < 0) set_status(ctl, MPCG_ERR_INVALID_ARG);  // cannot happen: crossings are snapshotted
+      }
+      ctl->n1 = n1;
+      ctl->x32_src = src;
+      ctl->res32 = res;
+      ctl->rr = rr;
+      if (res > eps1) ctl->warn_eps1 = 1;
+      ctl->t_fp32 = globaltimer();
+    }
+    *R.stop = 1;
+  }
+}
+
 // Promotion only (stage-1-only solves): x = float64(x~).
-__global__ void k_promote(const Ctl* c, const float* __restrict__ x32, double* __restrict__ x64,
-                          int n) {
+__global__ void k_promote(const Ctl* c, const float* __restrict__ x32,
+                          const float* __restrict__ snap, double* __restrict__ x64, int n) {
   const bool zero = c->trivial != 0;
   if (c->status != 0) return;
+  const float* xs = c->x32_src >= 0 ? snap + (size_t)c->x32_src * n : x32;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x64[i] = zero ? 0.0 : (double)x32[i];
+    x64[i] = zero ? 0.0 : (double)xs[i];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1001,6 +1397,7 @@ static CgArgs make_args(const Launch& L, int slot, int mode) {
   a.r64 = L.ws.r64;
   a.d64 = L.ws.d64;
   a.q64 = L.ws.q64;
+  a.snap = L.ws.snap;
   return a;
 }
 
@@ -1008,21 +1405,27 @@ static CgArgs make_args(const Launch& L, int slot, int mode) {
 int cg_grid(int requested) {
   static int cached = 0;
   if (!cached) {
-    int g32 = 0, g64 = 0, dev = 0, sms = 0;
-    if (cudaFuncSetAttribute((const void*)k_cg32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ring_smem_bytes<float>()) != cudaSuccess ||
-        cudaFuncSetAttribute((const void*)k_cg64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ring_smem_bytes<double>()) != cudaSuccess ||
-        cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g32, (const void*)k_cg32, kTmaThreads,
-                                                      ring_smem_bytes<float>()) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g64, (const void*)k_cg64, kTmaThreads,
-                                                      ring_smem_bytes<double>()) != cudaSuccess)
+    struct K {
+      const void* f;
+      size_t smem;
+    } ks[3] = {{(const void*)k_cg32, ring_smem_bytes<float>()},
+               {(const void*)k_cg64, ring_smem_bytes<double>()},
+               {(const void*)k_stage1, ring_smem_bytes<float>()}};
+    int dev = 0, sms = 0, per = 1 << 30;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return 0;
-    const int per = g32 < g64 ? g32 : g64;
+    for (const K& k : ks) {
+      int g = 0;
+      if (cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem) !=
+              cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k.f, kTmaThreads, k.smem) !=
+              cudaSuccess)
+        return 0;
+      if (g < per) per = g;
+    }
     cached = per > 0 ? sms * per : -1;
-    if (cached > kMaxGrid) cached = kMaxGrid;
+    if (cached > kMaxGrid - 1) cached = kMaxGrid - 1;  // one reduction slot stays free
   }
   if (cached <= 0) return 0;
   return (requested > 0 && requested < cached) ? requested : cached;
@@ -1030,6 +1433,7 @@ int cg_grid(int requested) {
 
 const void* cg32_kernel() { return (const void*)k_cg32; }
 const void* cg64_kernel() { return (const void*)k_cg64; }
+const void* stage1_kernel() { return (const void*)k_stage1; }
 
 cudaError_t launch_cg32(const Launch& L, int mode, int slot) {
   CgArgs a = make_args(L, slot, mode);
@@ -1051,10 +1455,26 @@ cudaError_t launch_cg64(const Launch& L, const double* b, double* x, int from_ze
                                     ring_smem_bytes<double>(), L.st);
 }
 
+cudaError_t launch_stage1(const Launch& L, const mpcg_sample_t& S, const mpcg_options_t& o,
+                          int slot, int bfs_slot) {
+  Stage1Args sa{};
+  sa.a = make_args(L, slot, kCgToEps1);
+  sa.g = bfs_graph(L);
+  sa.d1 = L.ws.dist;
+  sa.d2 = L.ws.dist2;
+  sa.knn = knn_spec(S, o);
+  sa.bfs_slot = bfs_slot;
+  void* args[] = {&sa};
+  const int g = cg_grid(L.grid_req);
+  if (g <= 0) return cudaErrorInvalidConfiguration;
+  return cudaLaunchCooperativeKernel((const void*)k_stage1, dim3(g), dim3(kTmaThreads), args,
+                                    ring_smem_bytes<float>(), L.st);
+}
+
 cudaError_t launch_promote(const Launch& L, double* x) {
   int blocks = (L.d.n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  k_promote<<<blocks, 256, 0, L.st>>>(L.ws.ctl, L.ws.x32, x, L.d.n);
+  k_promote<<<blocks, 256, 0, L.st>>>(L.ws.ctl, L.ws.x32, L.ws.snap, x, L.d.n);
   return cudaGetLastError();
 }
 

@@ -47,6 +47,8 @@ struct Ctl {
   int qsize[3];
   int ccflag[2];
   int cls;
+  int eps1_ready;  // fused stage 1: 0 pending, t + 1 when the kNN chose t, -1 on failure
+  int x32_src;     // stage-1 result: -1 = x32, s >= 0 = snapshot slot s
   // device clock marks (ns)
   unsigned long long t_start, t_prep, t_features, t_fp32, t_fp64, t_end;
 };
@@ -66,6 +68,7 @@ struct Ws {
   double *r64, *d64, *q64;
   int32_t *dist, *dist2, *fq0, *fq1, *label;
   unsigned long long* ckey;  // per-component farthest-vertex keys
+  float* snap;               // stage-1 snapshots of x~ at candidate crossings [6][n]
   size_t bytes;
 };
 

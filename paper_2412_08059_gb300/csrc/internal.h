@@ -2,7 +2,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "bfs_core.cuh"
 #include "common.cuh"
+#include "knn_core.cuh"
 
 namespace mpcg {
 
@@ -39,18 +41,23 @@ cudaError_t launch_cg32(const Launch& L, int mode, int slot);
 cudaError_t launch_cg64(const Launch& L, const double* b, double* x, int from_zero, int slot);
 cudaError_t launch_spmv(const Launch& L, int fp32, const void* x, void* y);
 cudaError_t launch_promote(const Launch& L, double* x);
+// Fused stage 1 of Algorithm II: 2BFS + k0 iterations + kNN + CG to eps1.
+cudaError_t launch_stage1(const Launch& L, const mpcg_sample_t& S, const mpcg_options_t& o,
+                          int slot, int bfs_slot);
+const void* stage1_kernel();
 const void* cg32_kernel();
 const void* cg64_kernel();
 int cg_grid(int requested);
 
 // bfs.cu
-cudaError_t launch_pseudo_diameter(const Launch& L, int first_slot);
+BfsGraph bfs_graph(const Launch& L);
+cudaError_t launch_pseudo_diameter(const Launch& L, int slot);
 cudaError_t launch_bfs_only(const Launch& L, int src, int32_t* dist, int slot);
 cudaError_t launch_copy_pdiam(const Launch& L, int32_t* out);
 const void* bfs_kernel();
-const void* cc_kernel();
 
 // knn.cu
+KnnSpec knn_spec(const mpcg_sample_t& S, const mpcg_options_t& o);
 cudaError_t launch_knn(cudaStream_t st, const double* feat4, const mpcg_sample_t& S,
                        const mpcg_options_t& o, Ctl* ctl, double* eps1_out, int32_t* cls_out);
 

@@ -56,6 +56,7 @@ size_t carve(const Dims& d, char* base, Ws* ws) {
   w.fq1 = (int32_t*)take(sizeof(int32_t) * n);
   w.label = (int32_t*)take(sizeof(int32_t) * n);
   w.ckey = (unsigned long long*)take(sizeof(unsigned long long) * n);
+  w.snap = (float*)take(sizeof(float) * 6 * n);
   w.bytes = off;
   if (ws) *ws = w;
   return off;
@@ -92,6 +93,7 @@ __global__ void k_init(Ctl* c, int n, int nnz, int nslices, int wcap, mpcg_optio
   c->timeout_ns = (long long)(o.timeout_ms > 0 ? o.timeout_ms : 20000) * 1000000ll;
   c->cls = -1;
   c->first = 1;
+  c->x32_src = -1;
 }
 
 // One thread per row (padded to whole slices): checks the CSR rules, writes
