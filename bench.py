@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = ("time-to-solution & equiv-FP64-iters/s, mixed vs pure-FP64 CG on 1 GB300 at "
           "eps2=1e-10; HBM %")
 UNIT = "solves/s"
-KERNELS_PER_SOLVE_AUTO = 18   # kernels one Algorithm II solve launches (see DESIGN.md)
+KERNELS_PER_SOLVE_AUTO = 18   # kernels one Algorithm II solve launches
 KERNELS_PER_SOLVE_FP64 = 8
 
 

@@ -166,8 +166,8 @@ int32_t mpcg_solve(const mpcg_csr_t* A, const double* b, double* x, const mpcg_s
                    const mpcg_options_t* opts, void* ws, size_t ws_bytes, mpcg_result_t* res,
                    mpcg_stream_t stream);
 
-/* Independent systems solved together (spec batching pattern, not in
- * the paper).  A: host array of nsys CSR descriptors (device pointers);
+/* Independent systems solved together (a batching pattern, not in the
+ * paper).  A: host array of nsys CSR descriptors (device pointers);
  * b, x: host arrays of nsys device pointers; res: device array of nsys
  * records.  Workspace: mpcg_batch_workspace_bytes.  Every system gets its own
  * eps1 and features; systems run concurrently on disjoint parts of the GPU. */
