@@ -178,6 +178,30 @@ int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const double* const*
                          const mpcg_options_t* opts, void* ws, size_t ws_bytes,
                          mpcg_result_t* res, mpcg_stream_t stream);
 
+/* Size of the library's fixed scratch array used by mpcg_solve_static. */
+#define MPCG_STATIC_WS_BYTES (64u << 20) /* 64 MiB */
+
+/* mpcg_solve without a caller workspace and without any allocation.  The
+ * paper has no counterpart: this is a deployment variant of mpcg_solve for
+ * callers that must not allocate device memory.  Same arguments, results
+ * and status codes as mpcg_solve, minus ws and ws_bytes; the scratch is a
+ * fixed array of MPCG_STATIC_WS_BYTES bytes in the library's device code,
+ * one per device, whose address is looked up once per device (with that
+ * device current).
+ *   Limit: systems whose mpcg_workspace_bytes(n, nnz, opts) exceeds
+ *   MPCG_STATIC_WS_BYTES are rejected with MPCG_ERR_WORKSPACE before
+ *   anything is launched (about n <= 200000 for a 7-point stencil).
+ *   The control block is cleared on `stream` at the start of every call.
+ *   Overlapping calls race: two calls on the same device whose work may run
+ *   at the same time (different streams, or host threads) share the one
+ *   array and corrupt each other's results.  Issue the calls of one device
+ *   on one stream, or order them.
+ * Errors: as mpcg_solve; MPCG_ERR_CUDA if the array's address cannot be
+ * obtained on the current device. */
+int32_t mpcg_solve_static(const mpcg_csr_t* A, const double* b, double* x,
+                          const mpcg_sample_t* sample, const mpcg_options_t* opts,
+                          mpcg_result_t* res, mpcg_stream_t stream);
+
 /* ---- building blocks exposed for verification (same kernels as above) ---- */
 
 /* y = A x through the library's SpMV (single or double precision, chosen by

@@ -75,7 +75,7 @@ class Result(C.Structure):
 
 SYMBOLS = ("mpcg_options_default", "mpcg_status_string", "mpcg_workspace_bytes", "mpcg_features",
            "mpcg_choose_eps1", "mpcg_solve", "mpcg_batch_workspace_bytes", "mpcg_solve_batch",
-           "mpcg_spmv", "mpcg_bfs", "mpcg_pseudo_diameter")
+           "mpcg_spmv", "mpcg_bfs", "mpcg_pseudo_diameter", "mpcg_solve_static")
 
 
 def load(path: str = LIB_PATH):
@@ -113,6 +113,9 @@ def load(path: str = LIB_PATH):
         L.mpcg_bfs.argtypes = [C.POINTER(CsrDesc), I32, P, P, SZ, P]
         L.mpcg_pseudo_diameter.restype = I32
         L.mpcg_pseudo_diameter.argtypes = [C.POINTER(CsrDesc), P, P, SZ, P]
+        L.mpcg_solve_static.restype = I32
+        L.mpcg_solve_static.argtypes = [C.POINTER(CsrDesc), P, P, C.POINTER(SampleDesc),
+                                        C.POINTER(Options), P, P]
         _lib = L
         return L
 
@@ -208,6 +211,18 @@ def solve_async(A: DeviceCSR, b: torch.Tensor, x: torch.Tensor, opts: Options, w
                            C.byref(sample.desc) if sample is not None else None, C.byref(opts),
                            _ptr(ws), ws.numel(), _ptr(res), _stream(stream))
     _check(st, "mpcg_solve")
+
+
+STATIC_WS_BYTES = 64 << 20  # MPCG_STATIC_WS_BYTES
+
+
+def solve_static_async(A: DeviceCSR, b: torch.Tensor, x: torch.Tensor, opts: Options,
+                       res: torch.Tensor, sample: DeviceSample | None = None, stream=None) -> int:
+    """Enqueue mpcg_solve_static (the library's fixed scratch array, no
+    workspace, no allocation); returns the call's status without raising."""
+    return int(load().mpcg_solve_static(C.byref(A.desc), _ptr(b), _ptr(x),
+                                        C.byref(sample.desc) if sample is not None else None,
+                                        C.byref(opts), _ptr(res), _stream(stream)))
 
 
 def solve(A: DeviceCSR, b: torch.Tensor, sample: DeviceSample | None = None, ws=None, **kw):
