@@ -132,7 +132,11 @@ typedef struct {
   double v;                  /* Eq. (13) */
   double res_fp32;           /* stop measure at the end of stage 1 */
   double res_fp64;           /* stop measure at the end of stage 2 */
-  uint64_t t_start_ns, t_features_ns, t_fp32_ns, t_fp64_ns, t_end_ns; /* device clock marks */
+  /* Device clock marks (ns): call start; eps1 known (features and kNN done;
+   * in Algorithm II they run alongside stage 1); end of stage 1; end of
+   * stage 2; result written; end of the set-up (demotion, sliced layout,
+   * ||b||). */
+  uint64_t t_start_ns, t_features_ns, t_fp32_ns, t_fp64_ns, t_end_ns, t_prep_ns;
 } mpcg_result_t;
 
 mpcg_options_t mpcg_options_default(void);
@@ -166,11 +170,21 @@ int32_t mpcg_solve(const mpcg_csr_t* A, const double* b, double* x, const mpcg_s
                    const mpcg_options_t* opts, void* ws, size_t ws_bytes, mpcg_result_t* res,
                    mpcg_stream_t stream);
 
-/* Independent systems solved together (a batching pattern, not in the
- * paper).  A: host array of nsys CSR descriptors (device pointers);
- * b, x: host arrays of nsys device pointers; res: device array of nsys
- * records.  Workspace: mpcg_batch_workspace_bytes.  Every system gets its own
- * eps1 and features; systems run concurrently on disjoint parts of the GPU. */
+/* Independent systems solved together in one persistent launch (a batching
+ * pattern; the paper solves one system at a time).  A: host array of nsys
+ * CSR descriptors (device pointers); b, x: host arrays of nsys device
+ * pointers; res: device array of nsys records.  Every system gets its own
+ * features, eps1 (Algorithm II when opts->eps1 <= 0, with `sample`) and
+ * result record, with the same options; fp64_only and stage1_only are not
+ * supported here (MPCG_ERR_UNIMPLEMENTED).  The grid is split into teams of
+ * 1..16 blocks; each team takes systems from size-class queues (largest
+ * first) and runs the whole method on each, so systems of uneven size run
+ * concurrently.  Workspace: mpcg_batch_workspace_bytes (a descriptor table,
+ * then one region per system).  The descriptor table is copied from host
+ * memory on `stream`; that copy may wait for earlier work on the stream.
+ * Errors of one system (invalid CSR, NaN, breakdown) go to its own record;
+ * a device-side wait that times out ends the launch, and the records of the
+ * systems not finished stay as they were. */
 size_t mpcg_batch_workspace_bytes(int32_t nsys, const int32_t* n, const int32_t* nnz,
                                   const mpcg_options_t* opts);
 int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const double* const* b,

@@ -14,6 +14,10 @@ namespace {
 // Barrier-counter slots of the persistent launches within one call.
 enum Slot { kSlotCg64 = 0, kSlotPd = 1, kSlotCgK0 = 2, kSlotCg32 = 3, kSlotBfs = 4 };
 
+}  // namespace
+
+namespace mpcg {
+
 bool options_ok(const mpcg_options_t* o) {
   if (!o) return false;
   if (!(o->eps2 >= 0.0)) return false;
@@ -25,6 +29,10 @@ bool options_ok(const mpcg_options_t* o) {
 bool sample_ok(const mpcg_sample_t* s) {
   return s && s->feat && s->cls && s->count >= 1 && s->count <= MPCG_KNN_MAX_SAMPLE;
 }
+
+}  // namespace mpcg
+
+namespace {
 
 int grid_size(int requested) {
   const void* kernels[1] = {bfs_kernel()};
@@ -154,35 +162,6 @@ int32_t mpcg_solve(const mpcg_csr_t* A, const double* b, double* x, const mpcg_s
     if ((e = launch_cg64(L, b, x, fp64_only, kSlotCg64)) != cudaSuccess) return cuda_status(e);
   }
   return cuda_status(launch_finalize(L, res, nullptr));
-}
-
-size_t mpcg_batch_workspace_bytes(int32_t nsys, const int32_t* n, const int32_t* nnz,
-                                  const mpcg_options_t* opts) {
-  if (nsys <= 0 || !n || !nnz) return 0;
-  size_t total = 0;
-  for (int32_t i = 0; i < nsys; ++i) {
-    size_t w = mpcg_workspace_bytes(n[i], nnz[i], opts);
-    if (!w) return 0;
-    total += (w + 255) & ~(size_t)255;
-  }
-  return total;
-}
-
-int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const double* const* b,
-                         double* const* x, const mpcg_sample_t* sample,
-                         const mpcg_options_t* opts, void* ws, size_t ws_bytes,
-                         mpcg_result_t* res, mpcg_stream_t stream) {
-  if (nsys <= 0 || !A || !b || !x || !res || !options_ok(opts)) return MPCG_ERR_INVALID_ARG;
-  size_t off = 0;
-  for (int32_t i = 0; i < nsys; ++i) {
-    const size_t w = mpcg_workspace_bytes(A[i].n, A[i].nnz, opts);
-    if (!w) return MPCG_ERR_INVALID_ARG;
-    if (off + w > ws_bytes) return MPCG_ERR_WORKSPACE;
-    int32_t st = mpcg_solve(&A[i], b[i], x[i], sample, opts, (char*)ws + off, w, &res[i], stream);
-    if (st != MPCG_OK) return st;
-    off += (w + 255) & ~(size_t)255;
-  }
-  return MPCG_OK;
 }
 
 int32_t mpcg_spmv(const mpcg_csr_t* A, int32_t fp32, const void* x, void* y, void* ws,

@@ -89,9 +89,6 @@ __device__ __forceinline__ const float* svals<float>(const CgArgs& a) { return a
 template <>
 __device__ __forceinline__ const double* svals<double>(const CgArgs& a) { return a.sv64; }
 
-__device__ __forceinline__ double stop_measure(double rr, double bnorm, int rel) {
-  return rel ? sqrt(rr) / bnorm : sqrt(rr);
-}
 
 // ---------------------------------------------------------------------------------------
 // Consumer-group synchronisation (named barrier 1, consumer warps only).

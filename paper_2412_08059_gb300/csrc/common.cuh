@@ -93,6 +93,11 @@ __device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned 
 
 __device__ __forceinline__ void set_status(Ctl* c, int s) { atomicCAS(&c->status, 0, s); }
 
+// Stop measure of the CG procedure: ||r|| / ||b|| (relative) or ||r||.
+__device__ __forceinline__ double stop_measure(double rr, double bnorm, int rel) {
+  return rel ? sqrt(rr) / bnorm : sqrt(rr);
+}
+
 __device__ __forceinline__ int volatile_status(const Ctl* c) {
   return *reinterpret_cast<const volatile int*>(&c->status);
 }

@@ -30,6 +30,10 @@ struct Launch {
 
 int persistent_grid(const void* kernel, int threads, int requested);
 
+// api.cu: host checks shared by the entry points
+bool options_ok(const mpcg_options_t* o);
+bool sample_ok(const mpcg_sample_t* s);
+
 // prep.cu
 cudaError_t launch_init(const Launch& L, const mpcg_options_t& o, int fp64_only);
 cudaError_t launch_prep(const Launch& L, const double* b);

@@ -287,6 +287,7 @@ __global__ void k_finalize(const Ctl* c, mpcg_result_t* res, mpcg_features_t* fe
     res->t_fp32_ns = c->t_fp32 ? c->t_fp32 : res->t_features_ns;
     res->t_fp64_ns = c->t_fp64 ? c->t_fp64 : res->t_fp32_ns;
     res->t_end_ns = now;
+    res->t_prep_ns = t0;
   }
   if (feat) {
     feat->n = (double)c->n;

@@ -62,12 +62,18 @@ class Result(C.Structure):
                 ("true_rel_resid", C.c_double), ("pdiam", C.c_double), ("v", C.c_double),
                 ("res_fp32", C.c_double), ("res_fp64", C.c_double),
                 ("t_start_ns", C.c_uint64), ("t_features_ns", C.c_uint64),
-                ("t_fp32_ns", C.c_uint64), ("t_fp64_ns", C.c_uint64), ("t_end_ns", C.c_uint64)]
+                ("t_fp32_ns", C.c_uint64), ("t_fp64_ns", C.c_uint64), ("t_end_ns", C.c_uint64),
+                ("t_prep_ns", C.c_uint64)]
 
     def as_dict(self) -> dict:
+        """Fields plus phase durations from the device clock marks: ms_prep (set-up),
+        ms_features (set-up end to eps1 known; overlapped with stage 1 in
+        Algorithm II), ms_fp32 (set-up end to end of stage 1, features included),
+        ms_fp64 (stage 2), ms_total."""
         d = {k: getattr(self, k) for k, _ in self._fields_}
-        d["ms_features"] = (self.t_features_ns - self.t_start_ns) / 1e6
-        d["ms_fp32"] = (self.t_fp32_ns - self.t_features_ns) / 1e6
+        d["ms_prep"] = (self.t_prep_ns - self.t_start_ns) / 1e6
+        d["ms_features"] = (self.t_features_ns - self.t_prep_ns) / 1e6
+        d["ms_fp32"] = (self.t_fp32_ns - self.t_prep_ns) / 1e6
         d["ms_fp64"] = (self.t_fp64_ns - self.t_fp32_ns) / 1e6
         d["ms_total"] = (self.t_end_ns - self.t_start_ns) / 1e6
         return d

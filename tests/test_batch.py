@@ -1,0 +1,172 @@
+"""GPU parity of the batched solve (mpcg_solve_batch): every system of a batch
+against the CPU oracle, with the bars of the single-system tests (labels,
+l~ and statuses exact; N1, N2 within 2 %; x within 1e-6; true residual <= eps2),
+across team sizes, queue stealing, a small grid and per-system failures."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_08059_gb300 import build, mpcg
+    build.build()
+    mpcg.load()
+    return mpcg
+
+
+def close_count(a, b):
+    return abs(a - b) <= max(1, int(0.02 * max(a, b)))
+
+
+def parity(r, ro, x, xo, eps2=1e-10):
+    assert r["status"] == ro["status"], (r, ro)
+    assert close_count(r["n1"], ro["n1"]), (r["n1"], ro["n1"])
+    assert close_count(r["n2"], ro["n2"]), (r["n2"], ro["n2"])
+    if ro["status"] >= 0:
+        assert r["true_rel_resid"] <= eps2
+        assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+def union(*mats):
+    rp, cols, vals, off, base = [np.zeros(1, np.int64)], [], [], 0, 0
+    for A in mats:
+        rp.append(A.row_ptr[1:].astype(np.int64) + base)
+        cols.append(A.col.astype(np.int64) + off)
+        vals.append(A.val)
+        off += A.n
+        base += A.nnz
+    return synth.CSR(np.concatenate(rp).astype(np.int32), np.concatenate(cols).astype(np.int32),
+                     np.concatenate(vals))
+
+
+def mixed_systems():
+    """Small and medium systems of several families; the medium ones go to
+    teams of 2, 4 and 8 blocks (16384 rows per block)."""
+    return [
+        synth.laplacian_2d(37, 29),
+        synth.laplacian_3d(13, eps=1e-2, sigma=1e-3),
+        synth.random_regular_laplacian(3000, 8, 1e-3, seed=4),
+        synth.star(1001, 1.1),
+        synth.extended_star(20, 50, 1.1, extra=None, seed=3),
+        synth.random_tree_plus(1000, 10.0, 1.1, seed=2),
+        synth.banded(1000, 29, 0.6, 1.1, seed=7),
+        synth.path(700),
+        synth.from_edges(1, [], [], np.zeros(0), np.full(1, 2.0)),
+        synth.laplacian_2d(3, 2),
+        union(synth.path(50), synth.star(40), synth.laplacian_2d(9, 7)),
+        synth.laplacian_3d(32),                     # 32768 rows: team of 2
+        synth.laplacian_2d(200, 200),               # 40000 rows: team of 4
+        synth.laplacian_2d(300, 250, sigma=1e-4),   # 75000 rows: team of 8
+    ]
+
+
+def sample_over(mats, seed=1, count=200):
+    """A sample whose (n, m) span the batch, so that every feature matters."""
+    feat, cls = synth.random_sample(count, seed=seed)
+    ns = np.array([A.n for A in mats], float)
+    feat[:, 0] = np.exp(np.linspace(np.log(0.5 * ns.min()), np.log(2 * ns.max()), count))
+    feat[:, 1] = feat[:, 0] * np.linspace(3.0, 9.0, count)[::-1]
+    return feat, cls
+
+
+def run_batch(mp, mats, bs, sample=None, **kw):
+    dmats = [mp.DeviceCSR.from_host(A) for A in mats]
+    dbs = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in bs]
+    xs = [torch.full((A.n,), np.nan, dtype=torch.float64, device="cuda") for A in mats]
+    ws = torch.empty(mp.batch_workspace_bytes(dmats), dtype=torch.uint8, device="cuda")
+    res = mp.result_buffer(len(mats))
+    mp.solve_batch_async(dmats, dbs, xs, mp.options(**kw), ws, res, sample)
+    torch.cuda.synchronize()
+    return [x.cpu().numpy() for x in xs], mp.read_results(res, len(mats))
+
+
+def test_batch_algorithm_ii_parity(mp):
+    mats = mixed_systems()
+    bs = [synth.rhs(A, seed=20 + i)[1] for i, A in enumerate(mats)]
+    feat, cls = sample_over(mats)
+    S = mp.DeviceSample(feat, cls)
+    xs, rs = run_batch(mp, mats, bs, S)
+    for A, b, x, r in zip(mats, bs, xs, rs):
+        xo, ro = oracle.solve(A, b, S=(feat, cls))
+        assert r["pdiam"] == ro["pdiam"], (A.n, r["pdiam"], ro["pdiam"])
+        assert abs(r["v"] - ro["v"]) <= 1e-12, (A.n, r["v"], ro["v"])
+        assert r["k0_done"] == ro["k0_done"]
+        # the kNN on the GPU's own features gives the oracle's label
+        assert r["cls"] == oracle.knn([A.n, A.nnz, r["pdiam"], r["v"]], (feat, cls))
+        assert r["cls"] == ro["cls"] and r["eps1"] == ro["eps1"]
+        parity(r, ro, x, xo)
+
+
+@pytest.mark.parametrize("eps1", [1e-3, 1e-6])
+def test_batch_algorithm_i_parity(mp, eps1):
+    mats = mixed_systems()
+    bs = [synth.rhs(A, seed=40 + i)[1] for i, A in enumerate(mats)]
+    xs, rs = run_batch(mp, mats, bs, None, eps1=eps1)
+    for A, b, x, r in zip(mats, bs, xs, rs):
+        xo, ro = oracle.solve(A, b, eps1=eps1)
+        assert r["cls"] == -1 and r["eps1"] == eps1
+        parity(r, ro, x, xo)
+
+
+def test_batch_matches_single_solves(mp):
+    mats = mixed_systems()[:8] + [synth.laplacian_2d(200, 200)]
+    bs = [synth.rhs(A, seed=60 + i)[1] for i, A in enumerate(mats)]
+    feat, cls = sample_over(mats, seed=3)
+    S = mp.DeviceSample(feat, cls)
+    xs, rs = run_batch(mp, mats, bs, S)
+    for A, b, x, r in zip(mats, bs, xs, rs):
+        x1, r1 = mp.solve(mp.DeviceCSR.from_host(A), torch.from_numpy(b).cuda(), S)
+        assert (r["status"], r["cls"], r["pdiam"], r["k0_done"]) == \
+            (r1["status"], r1["cls"], r1["pdiam"], r1["k0_done"])
+        assert close_count(r["n1"], r1["n1"]) and close_count(r["n2"], r1["n2"])
+        assert np.linalg.norm(x - x1.cpu().numpy()) <= 1e-6 * np.linalg.norm(x)
+
+
+def test_batch_small_grid_and_failures(mp):
+    """Eight blocks (the class of the 75000-row system is demoted), a system
+    with b = 0, one with a NaN in b, one that is not SPD and one with a CSR
+    error: each gets its own status, the others are unaffected."""
+    good = [synth.laplacian_2d(300, 250, sigma=1e-4), synth.laplacian_2d(40, 30),
+            synth.random_regular_laplacian(2000, 6, 1e-2, seed=9)]
+    A0 = synth.laplacian_2d(20, 10)
+    bad_col = A0.col.copy()
+    bad_col[5] = A0.n + 7
+    bad = synth.CSR(A0.row_ptr, bad_col, A0.val)
+    neg = synth.CSR(A0.row_ptr, A0.col, -A0.val)
+    mats = good + [A0, A0, neg, bad]
+    bs = [synth.rhs(A, seed=80 + i)[1] for i, A in enumerate(good)]
+    nan_b = np.ones(A0.n)
+    nan_b[3] = np.nan
+    bs += [np.zeros(A0.n), nan_b, np.ones(A0.n), np.ones(A0.n)]
+    xs, rs = run_batch(mp, mats, bs, None, eps1=1e-4, grid_blocks=8)
+    for A, b, x, r in zip(good, bs, xs, rs):
+        xo, ro = oracle.solve(A, b, eps1=1e-4)
+        parity(r, ro, x, xo)
+    r_zero, r_nan, r_neg, r_bad = rs[3:]
+    assert r_zero["status"] == 0 and not np.any(xs[3]) and r_zero["n1"] == r_zero["n2"] == 0
+    assert r_nan["status"] == mp.ERR_NAN
+    _, ro = oracle.solve(neg, np.ones(A0.n), eps1=1e-4)
+    assert r_neg["status"] == ro["status"] == mp.ERR_BREAKDOWN
+    assert r_bad["status"] == mp.ERR_INVALID_ARG
+
+
+def test_batch_many_small_systems_steal(mp):
+    """More systems than teams, of one size class, plus one large system:
+    the large-team queue empties first and its team takes small systems."""
+    mats = [synth.laplacian_2d(300, 300)] + [synth.laplacian_2d(10 + i % 7, 9 + i % 5)
+                                            for i in range(300)]
+    bs = [synth.rhs(A, seed=100 + i)[1] for i, A in enumerate(mats)]
+    xs, rs = run_batch(mp, mats, bs, None, eps1=1e-5)
+    for k in [0, 1, 2, 150, 299, 300]:
+        xo, ro = oracle.solve(mats[k], bs[k], eps1=1e-5)
+        parity(rs[k], ro, xs[k], xo)
+    assert all(r["status"] in (0, 1) for r in rs)
+    assert all(r["true_rel_resid"] <= 1e-10 for r in rs)
