@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sample", default=None, help="load a kNN sample (json) instead of building")
     ap.add_argument("--save-sample", default=None)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve section")
+    ap.add_argument("--batch-only", action="store_true", help="run only the batched-solve section")
+    ap.add_argument("--batch-systems", type=int, default=512)
     return ap.parse_args()
 
 
@@ -198,6 +201,106 @@ def reference_arm(args, rank):
 
 
 # ------------------------------------------------------------------------------------------
+# Batched solve: many uneven systems in one persistent launch
+# ------------------------------------------------------------------------------------------
+def batch_section(args, dev, steps, warmup):
+    """512 systems (n log-uniform in [1e3, 2.6e5]; 2-D, 3-D, anisotropic and
+    shifted Laplacians), each with x* ~ U[-1, 1] and b = A x*, eps2 = 1e-10,
+    auto eps1 from a kNN sample built on 64 other systems of the same
+    families.  Timed: mpcg_solve_batch (mixed, Algorithm II), the same batch
+    in pure FP64, and the systems solved one at a time with mpcg_solve."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2412_08059_gb300 import mpcg, sample
+
+    descs = synth.batch_family(args.batch_systems, seed=11)
+    mats, dmats, dbs, xs = [], [], [], []
+    for i, d in enumerate(descs):
+        A = synth.build_desc(d)
+        _, b = synth.rhs(A, seed=1000 + i)
+        mats.append(A)
+        dmats.append(mpcg.DeviceCSR.from_host(A, dev))
+        dbs.append(torch.from_numpy(b).to(dev))
+        xs.append(torch.empty(A.n, dtype=torch.float64, device=dev))
+    train = []
+    for i, d in enumerate(synth.batch_family(64, seed=12)):
+        A = synth.build_desc(d)
+        _, b = synth.rhs(A, seed=5000 + i)
+        train.append((f"train{i}", A, b))
+    t = time.time()
+    feat, cls, _ = sample.build(train, device=dev)
+    t_sample = time.time() - t
+    S = mpcg.DeviceSample(feat, cls, device=dev)
+    nsys = len(mats)
+    ws = torch.empty(mpcg.batch_workspace_bytes(dmats), dtype=torch.uint8, device=dev)
+    res = mpcg.result_buffer(nsys, dev)
+    o_mixed = mpcg.options()
+    o_fp64 = mpcg.options(fp64_only=1)
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    ms_mixed = timed(lambda: mpcg.solve_batch_async(dmats, dbs, xs, o_mixed, ws, res, S), steps, warmup)
+    r_mixed = mpcg.read_results(res, nsys)
+    ms_fp64 = timed(lambda: mpcg.solve_batch_async(dmats, dbs, xs, o_fp64, ws, res, S), steps,
+                    max(1, warmup // 2))
+    r_fp64 = mpcg.read_results(res, nsys)
+    # one system at a time through mpcg_solve (one step)
+    ws1 = torch.empty(max(mpcg.workspace_bytes(A.n, A.nnz) for A in mats), dtype=torch.uint8,
+                      device=dev)
+    res1 = mpcg.result_buffer(nsys, dev)
+    rsz = res1.numel() // nsys
+
+    def seq():
+        for i in range(nsys):
+            mpcg.solve_async(dmats[i], dbs[i], xs[i], o_mixed, ws1, res1[i * rsz:(i + 1) * rsz], S)
+    ms_seq = timed(seq, 1, 1)
+    r_seq = mpcg.read_results(res1, nsys)
+    bad = [r["status"] for r in r_mixed + r_fp64 + r_seq if r["status"] < 0]
+    n1 = np.array([r["n1"] for r in r_mixed])
+    n2 = np.array([r["n2"] for r in r_mixed])
+    ndp = np.array([r["n2"] for r in r_fp64])
+    sum_n = int(sum(A.n for A in mats))
+    sum_nnz = int(sum(A.nnz for A in mats))
+    # algorithmic bytes: per iteration the sliced matrix and six vector passes
+    by = lambda A, p: A.nnz * (p + 4) + 4 * (A.n + 1) + 6 * p * A.n
+    bytes_mixed = sum(by(A, 4) * r["n1"] + by(A, 8) * (r["n2"] + 2) for A, r in zip(mats, r_mixed))
+    bytes_fp64 = sum(by(A, 8) * (r["n2"] + 2) for A, r in zip(mats, r_fp64))
+    flops64 = sum(2.0 * (A.nnz + 5 * A.n) * r["n2"] for A, r in zip(mats, r_fp64))
+    return {
+        "workload": f"{nsys} systems, n log-uniform [1e3, 2.6e5] (2D/3D/aniso/shifted Laplacians), "
+                    "eps2 1e-10, auto eps1 (kNN sample: 64 other systems of the families)",
+        "systems": nsys, "sum_n": sum_n, "sum_nnz": sum_nnz,
+        "solves_per_s": {"batch_mixed": nsys / (ms_mixed / 1e3), "batch_fp64": nsys / (ms_fp64 / 1e3),
+                         "one_at_a_time_mixed": nsys / (ms_seq / 1e3)},
+        "ms_per_batch": {"batch_mixed": round(ms_mixed, 3), "batch_fp64": round(ms_fp64, 3),
+                         "one_at_a_time_mixed": round(ms_seq, 3)},
+        "speedup_mixed_over_fp64": ms_fp64 / ms_mixed,
+        "speedup_batch_over_one_at_a_time": ms_seq / ms_mixed,
+        "equiv_fp64_iters_per_s": {"mixed_omega_1_3": float((n1 / 3.0 + n2).sum() / (ms_mixed / 1e3)),
+                                   "fp64": float(ndp.sum() / (ms_fp64 / 1e3))},
+        "mean_iters": {"n1": float(n1.mean()), "n2": float(n2.mean()), "n_dp": float(ndp.mean())},
+        "eps1_labels": np.bincount([max(0, r["cls"]) for r in r_mixed], minlength=8).tolist(),
+        "algorithmic_GBps": {"batch_mixed": bytes_mixed / (ms_mixed / 1e3) / 1e9,
+                             "batch_fp64": bytes_fp64 / (ms_fp64 / 1e3) / 1e9},
+        "fp64_TFLOPs_batch_fp64": flops64 / (ms_fp64 / 1e3) / 1e12,
+        "failed_statuses": bad, "sample_seconds": round(t_sample, 1),
+        "kernels_per_batch": 1,
+    }
+
+
 # Native arm
 # ------------------------------------------------------------------------------------------
 def native_arm(args, rank, world, local_rank):
@@ -215,6 +318,11 @@ def native_arm(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     mpcg.load()
+
+    if args.batch_only:
+        if rank == 0:
+            print(json.dumps({"batch": batch_section(args, dev, args.steps, args.warmup)}), flush=True)
+        return
 
     def barrier():
         if world > 1:
@@ -445,6 +553,10 @@ def native_arm(args, rank, world, local_rank):
                                     "fp64": round(costs["t_it64"] * 1e3, 2)},
                "host_cores_available": os.cpu_count()}
 
+    batch = None
+    if not args.no_batch and rank == 0 and world == 1:
+        batch = batch_section(args, dev, max(1, args.steps // 3), 1)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
@@ -462,7 +574,7 @@ def native_arm(args, rank, world, local_rank):
                                            / (ms_fp64 / 1000.0)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": KERNELS_PER_SOLVE_AUTO * nsys * args.steps,
-                "clocks": clocks, "systems": per, "eps1_sweep": sweep,
+                "clocks": clocks, "systems": per, "eps1_sweep": sweep, "batch": batch,
                 "sample": {"desc": sample_desc, "seconds_to_build": round(t_sample, 1),
                            "labels": np.bincount(cls, minlength=8)[2:].tolist()}}
         print(json.dumps(line), flush=True)

@@ -226,7 +226,7 @@ __device__ void sys_init(const Team& t, const BatchSys& s, const BatchArgs& a) {
     c->max2 = m2 > 0x7fffffffll ? 0x7fffffff : (int)m2;
     c->max_restarts = o.max_true_restarts > 0 ? o.max_true_restarts : 0;
     c->tol_relative = o.tol_relative ? 1 : 0;
-    c->eps1 = a.auto_eps1 ? -1.0 : o.eps1;
+    c->eps1 = o.fp64_only ? 0.0 : (a.auto_eps1 ? -1.0 : o.eps1);
     c->eps2 = s.eps2;
     c->timeout_ns = (long long)(o.timeout_ms > 0 ? o.timeout_ms : 20000) * 1000000ll;
     c->cls = -1;
@@ -362,22 +362,64 @@ __device__ __forceinline__ const float* bvals<float>(const BatchSys& s) { return
 template <>
 __device__ __forceinline__ const double* bvals<double>(const BatchSys& s) { return s.w.sv64; }
 
-// Row i (= 32 sl + lane) of A times the vector given by G, in stored order.
+// Overflow tail of row i (entries past the slice width, from the CSR).
 template <typename T, class Gather>
-__device__ __forceinline__ T brow(const BatchSys& s, int sl, int i, int lane, Gather G) {
-  const uint32_t wf = s.w.slice_w[sl];
-  const int w = (int)(wf & ~kOverflowBit);
-  const int p = s.w.slice_ptr[sl] + lane;
+__device__ __forceinline__ T btail(const BatchSys& s, int i, int w, T acc, Gather G) {
+  const int e1 = s.A.row_ptr[i + 1];
+  for (int e = s.A.row_ptr[i] + w; e < e1; ++e) acc = fma((T)s.A.val[e], G(s.A.col[e]), acc);
+  return acc;
+}
+
+__device__ __forceinline__ int team_warp(const Team& t);
+__device__ __forceinline__ int team_warps(const Team& t);
+
+// SpMV over the team's slices: warp gw owns slices gw, gw + W, ...; lane l
+// owns row 32 s + l.  Rw(i, acc) receives row i's sum in stored order (fused
+// multiply-adds from zero, padding rows included).  The metadata of 32 of
+// the warp's slices is loaded at once (one slice per lane) and two slices
+// are summed together so that their loads and gathers overlap.
+template <typename T, class Gather, class Row>
+__device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gather G, Row Rw) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int gw = team_warp(t), W = team_warps(t);
   const T* sv = bvals<T>(s);
   const int32_t* sc = s.w.scol;
-  T acc = (T)0;
+  for (int base = gw; base < s.nslices; base += 32 * W) {
+    const int mine = base + lane * W;
+    uint32_t mwf = 0u;
+    int mp = 0;
+    if (mine < s.nslices) {
+      mwf = s.w.slice_w[mine];
+      mp = s.w.slice_ptr[mine];
+    }
+    const int cnt = min(32, (s.nslices - base + W - 1) / W);
+    for (int j = 0; j < cnt; j += 2) {
+      const int j1 = min(j + 1, 31);
+      const bool h1 = j + 1 < cnt;
+      const uint32_t wf0 = __shfl_sync(full, mwf, j);
+      const uint32_t wf1 = __shfl_sync(full, mwf, j1);
+      const int p0 = __shfl_sync(full, mp, j) + lane;
+      const int p1 = __shfl_sync(full, mp, j1) + lane;
+      const int w0 = (int)(wf0 & ~kOverflowBit);
+      const int w1 = h1 ? (int)(wf1 & ~kOverflowBit) : 0;
+      const int i0 = (base + j * W) * kSlice + lane;
+      const int i1 = (base + (j + 1) * W) * kSlice + lane;
+      T a0 = (T)0, a1 = (T)0;
+      const int wm = max(w0, w1);
 #pragma unroll 4
-  for (int k = 0; k < w; ++k) acc = fma(sv[p + kSlice * k], G(sc[p + kSlice * k]), acc);
-  if ((wf & kOverflowBit) && i < s.n) {
-    const int e1 = s.A.row_ptr[i + 1];
-    for (int e = s.A.row_ptr[i] + w; e < e1; ++e) acc = fma((T)s.A.val[e], G(s.A.col[e]), acc);
+      for (int k = 0; k < wm; ++k) {
+        if (k < w0) a0 = fma(sv[p0 + kSlice * k], G(sc[p0 + kSlice * k]), a0);
+        if (k < w1) a1 = fma(sv[p1 + kSlice * k], G(sc[p1 + kSlice * k]), a1);
+      }
+      if ((wf0 & kOverflowBit) && i0 < s.n) a0 = btail<T>(s, i0, w0, a0, G);
+      Rw(i0, a0);
+      if (h1) {
+        if ((wf1 & kOverflowBit) && i1 < s.n) a1 = btail<T>(s, i1, w1, a1, G);
+        Rw(i1, a1);
+      }
+    }
   }
-  return acc;
 }
 
 __device__ __forceinline__ int team_warp(const Team& t) { return t.rank * kBatchWarps + (threadIdx.x >> 5); }
@@ -473,17 +515,16 @@ __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red) {
     float* dnew = parity ? s.w.d32a : s.w.d32b;
     const float bt = first ? 0.0f : beta;
     FF pdq{0.f, 0.f};
-    for (int sl = gw; sl < s.nslices; sl += W) {
-      const int i = sl * kSlice + lane;
-      const float acc =
-          brow<float>(s, sl, i, lane, [&](int c) -> float { return __fmaf_rn(bt, dold[c], r[c]); });
-      if (i < n) {
-        const float di = __fmaf_rn(bt, dold[i], r[i]);
-        dnew[i] = di;
-        q[i] = acc;
-        ff_add_prod(pdq, di, acc);
-      }
-    }
+    team_spmv<float>(
+        t, s, [&](int c) -> float { return __fmaf_rn(bt, dold[c], r[c]); },
+        [&](int i, float acc) {
+          if (i < n) {
+            const float di = __fmaf_rn(bt, dold[i], r[i]);
+            dnew[i] = di;
+            q[i] = acc;
+            ff_add_prod(pdq, di, acc);
+          }
+        });
     double dq;
     if (!team_sum_ff(t, pdq, s.w.partials, red, dq)) return false;
     dec = kBGo;
@@ -582,16 +623,16 @@ __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& red) {
   for (;;) {
     // restart (CG line 1 from x): r = b - A x, d = r, r^T r
     double p = 0.0;
-    for (int sl = gw; sl < s.nslices; sl += W) {
-      const int i = sl * kSlice + lane;
-      const double acc = brow<double>(s, sl, i, lane, [&](int c) -> double { return x[c]; });
-      if (i < n) {
-        const double ri = b[i] - acc;
-        r[i] = ri;
-        d[i] = ri;
-        p = __fma_rn(ri, ri, p);
-      }
-    }
+    team_spmv<double>(
+        t, s, [&](int c) -> double { return x[c]; },
+        [&](int i, double acc) {
+          if (i < n) {
+            const double ri = b[i] - acc;
+            r[i] = ri;
+            d[i] = ri;
+            p = __fma_rn(ri, ri, p);
+          }
+        });
     if (!team_sum_d(t, p, s.w.partials, red, rr)) return false;
     bool converged = false;
     for (;;) {
@@ -617,14 +658,14 @@ __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& red) {
       }
       // P1: q = A d, d^T q
       double pq = 0.0;
-      for (int sl = gw; sl < s.nslices; sl += W) {
-        const int i = sl * kSlice + lane;
-        const double acc = brow<double>(s, sl, i, lane, [&](int c) -> double { return d[c]; });
-        if (i < n) {
-          q[i] = acc;
-          pq = __fma_rn(d[i], acc, pq);
-        }
-      }
+      team_spmv<double>(
+          t, s, [&](int c) -> double { return d[c]; },
+          [&](int i, double acc) {
+            if (i < n) {
+              q[i] = acc;
+              pq = __fma_rn(d[i], acc, pq);
+            }
+          });
       double dq;
       if (!team_sum_d(t, pq, s.w.partials, red, dq)) return false;
       dec = kBGo;
@@ -675,14 +716,14 @@ __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& red) {
     if (failed && failed != MPCG_ERR_NOT_CONVERGED) break;
     // true residual ||b - A x|| (also after the iteration cap)
     double pt = 0.0;
-    for (int sl = gw; sl < s.nslices; sl += W) {
-      const int i = sl * kSlice + lane;
-      const double acc = brow<double>(s, sl, i, lane, [&](int c) -> double { return x[c]; });
-      if (i < n) {
-        const double ri = b[i] - acc;
-        pt = __fma_rn(ri, ri, pt);
-      }
-    }
+    team_spmv<double>(
+        t, s, [&](int c) -> double { return x[c]; },
+        [&](int i, double acc) {
+          if (i < n) {
+            const double ri = b[i] - acc;
+            pt = __fma_rn(ri, ri, pt);
+          }
+        });
     double tot;
     if (!team_sum_d(t, pt, s.w.partials, red, tot)) return false;
     int again = 0;
@@ -772,6 +813,8 @@ __device__ bool sys_solve(Team& t, const BatchSys& s, const BatchArgs& a) {
   const bool trivial = ctl->trivial != 0;
   if (sys_status(s) == 0 && trivial) {  // b = 0: x = 0 solves A x = b exactly
     for (int i = team_tid(t); i < s.n; i += team_threads(t)) s.x[i] = 0.0;
+  } else if (sys_status(s) == 0 && a.o.fp64_only) {  // pure FP64 CG from x0 = 0
+    if (!sys_cg64(t, s, 1, red)) return false;
   } else if (sys_status(s) == 0) {
     if (a.auto_eps1) {
       // Algorithm II: l~ by 2BFS, v over the first k0 iterations, eps1 by kNN
@@ -989,8 +1032,8 @@ extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const dou
                                     const mpcg_options_t* opts, void* ws, size_t ws_bytes,
                                     mpcg_result_t* res, mpcg_stream_t stream) {
   if (nsys <= 0 || !A || !b || !x || !res || !options_ok(opts)) return MPCG_ERR_INVALID_ARG;
-  if (opts->fp64_only || opts->stage1_only) return MPCG_ERR_UNIMPLEMENTED;
-  const int auto_eps1 = !(opts->eps1 > 0.0);
+  if (opts->stage1_only) return MPCG_ERR_UNIMPLEMENTED;
+  const int auto_eps1 = !opts->fp64_only && !(opts->eps1 > 0.0);
   if (auto_eps1 && !sample_ok(sample)) return MPCG_ERR_INVALID_ARG;
   if (!ws || ((uintptr_t)ws & 255u)) return MPCG_ERR_WORKSPACE;
   std::vector<int> nv(nsys), mv(nsys);
