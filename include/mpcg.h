@@ -192,6 +192,66 @@ int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const double* const*
                          const mpcg_options_t* opts, void* ws, size_t ws_bytes,
                          mpcg_result_t* res, mpcg_stream_t stream);
 
+/* ---- serving: continuous batching over a slot table (not in the paper) ----
+ *
+ * A server admits systems into slots and keeps each admitted system's
+ * workspace (sliced matrix, Krylov vectors, control block) resident in a
+ * device pool carved from the caller's workspace.  mpcg_batch_step advances
+ * every admitted system in one persistent launch by at most max_iters CG
+ * iterations per stage, through the phases below; systems in different
+ * phases (set-up and features, single precision, double precision) run side
+ * by side.  Between steps the host retires finished systems and admits new
+ * ones.  Each system's result record, x and status are those of the same
+ * method as mpcg_solve (Algorithm II with `sample` when opts->eps1 <= 0,
+ * Algorithm I otherwise; fp64_only gives pure FP64 CG); its own eps2 is
+ * given at admission.  The server handle is host memory and is not
+ * thread-safe; all steps of one server go to one stream. */
+typedef struct mpcg_server mpcg_server_t;
+
+enum {
+  MPCG_PHASE_NEW = 0,      /* admitted, nothing run yet */
+  MPCG_PHASE_STAGE1 = 1,   /* single-precision stage under way */
+  MPCG_PHASE_STAGE2 = 2,   /* double-precision stage next */
+  MPCG_PHASE_STAGE2_RUN = 3, /* double-precision stage under way */
+  MPCG_PHASE_DONE = 4      /* result record, x and status written */
+};
+
+/* Workspace for a server of max_slots slots and a pool of pool_bytes (each
+ * admitted system takes mpcg_workspace_bytes(n, nnz) of it, rounded up to
+ * 256 bytes).  0 if max_slots <= 0. */
+size_t mpcg_server_workspace_bytes(int32_t max_slots, size_t pool_bytes);
+
+/* Create a server on the caller's device workspace (256-byte aligned, size
+ * from mpcg_server_workspace_bytes).  `sample` (device arrays, kept alive
+ * by the caller) and `opts` apply to every system; stage1_only is refused.
+ * *out: host handle, freed by mpcg_server_destroy. */
+int32_t mpcg_server_create(void* ws, size_t ws_bytes, int32_t max_slots,
+                           const mpcg_sample_t* sample, const mpcg_options_t* opts,
+                           mpcg_server_t** out);
+void mpcg_server_destroy(mpcg_server_t* srv);
+
+/* Admit one system: A, b, x, res as for mpcg_solve (device memory kept
+ * valid until the system is retired), final tolerance eps2.  *slot receives
+ * its slot.  MPCG_ERR_WORKSPACE when no slot is free or the pool has no
+ * contiguous block of the system's workspace size (the caller retries after
+ * retiring).  Host only; the system starts at the next step. */
+int32_t mpcg_server_admit(mpcg_server_t* srv, const mpcg_csr_t* A, const double* b, double* x,
+                          double eps2, mpcg_result_t* res, int32_t* slot);
+
+/* One step on `stream`: copies the slot tables, advances every admitted
+ * system by at most max_iters iterations per stage, then copies the phase
+ * of every slot (int32[max_slots], MPCG_PHASE_*) to slot_phase (host memory,
+ * pinned for an asynchronous copy; may be NULL), valid after the stream has
+ * synchronised.  Entries of slots that are not admitted are meaningless.
+ * The table copy is from host memory and may wait for earlier work on the
+ * stream. */
+int32_t mpcg_batch_step(mpcg_server_t* srv, int32_t max_iters, int32_t* slot_phase,
+                        mpcg_stream_t stream);
+
+/* Free the slot and the pool block of an admitted system (after its phase
+ * is MPCG_PHASE_DONE, or to cancel it between steps). */
+int32_t mpcg_server_retire(mpcg_server_t* srv, int32_t slot);
+
 /* Size of the library's fixed scratch array used by mpcg_solve_static. */
 #define MPCG_STATIC_WS_BYTES (64u << 20) /* 64 MiB */
 

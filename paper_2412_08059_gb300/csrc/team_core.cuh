@@ -1,0 +1,833 @@
+// team_core.cuh -- the whole method for one system, run by a team of blocks
+// of a persistent launch (the batched solve and the serving steps).
+//
+// A team is 1, 2, 4, 8 or 16 blocks of one cooperative launch.  Teams
+// synchronise with a bounded barrier over their own blocks (a block barrier
+// for one-block teams).  Scalars are computed from team-wide sums that every
+// block of the team forms in the same order, so all blocks take the same
+// decisions.  The arithmetic is that of the single-system kernels: SpMV rows
+// summed in stored order with fused multiply-adds, float-float dot products
+// in single precision, alpha and beta rounded once to float.  The CG stages
+// can stop after an iteration budget and continue in a later launch from
+// the state kept in the system's workspace and control block.
+#pragma once
+#include <math.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace mpcg {
+
+constexpr int kBatchThreads = 512;
+constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr int kTeamClasses = 5;                // team sizes 1, 2, 4, 8, 16
+constexpr int kRowsPerBlock = 16384;           // planner: target rows per block of a team
+constexpr int kNoBudget = 0x7fffffff;          // iteration budget of a run-to-completion call
+
+// One system of the batch (device copy written by the host).
+struct BatchSys {
+  mpcg_csr_t A;
+  const double* b;
+  double* x;
+  mpcg_result_t* res;
+  Ws w;  // the system's own workspace, carved by the host
+  int n, nnz, nslices, wcap;
+  double eps2;  // per-system final tolerance
+};
+
+// Shared state of the launch (device, zeroed by the host copy).
+struct BatchHdr {
+  unsigned long long bar[kMaxGrid];  // per-team barrier counters
+  int next[kMaxGrid];                // system index broadcast by each team leader
+  int head[kTeamClasses];            // queue heads (atomic)
+  int qbase[kTeamClasses], qlen[kTeamClasses];
+  int abort;                         // a team barrier timed out: every block leaves
+  int pad;
+};
+
+struct BatchArgs {
+  BatchHdr* h;
+  const BatchSys* sys;
+  const int* order;            // systems by class queue
+  const int* team_of_block;    // [grid]
+  const int* rank_of_block;    // [grid]
+  const int* team_size;        // [nteams]
+  const int* team_class;       // [nteams]
+  KnnSpec knn;
+  mpcg_options_t o;
+  int auto_eps1;
+};
+
+// ---------------------------------------------------------------------------------------
+// Team context: barrier, block-level scratch, deterministic team sums.
+// ---------------------------------------------------------------------------------------
+struct TeamShared {
+  double dpart[kBatchWarps];
+  float ffp[2 * kBatchWarps];
+  double val[4];
+  float fval[2];
+  int ival[4];
+  int ok;
+};
+
+struct Team {
+  BatchHdr* h;
+  unsigned long long* bar;
+  int rank, size, team;
+  unsigned long long round;
+  long long timeout_ns;
+  TeamShared* S;
+};
+
+// Bounded barrier over the team's blocks.  False (in every thread of the
+// block) on timeout or when another team has aborted the launch.
+static __device__ bool team_sync(Team& t) {
+  __syncthreads();
+  if (t.size == 1) {
+    if (threadIdx.x == 0) t.S->ok = *reinterpret_cast<volatile int*>(&t.h->abort) == 0;
+    __syncthreads();
+    return t.S->ok != 0;
+  }
+  t.round += 1;
+  if (threadIdx.x == 0) {
+    const unsigned long long target = t.round * (unsigned long long)t.size;
+    red_release_add(t.bar, 1ull);
+    int ok = 1;
+    if (ld_acquire(t.bar) < target) {
+      const unsigned long long t0 = globaltimer();
+      unsigned spins = 0;
+      while (ld_acquire(t.bar) < target) {
+        if ((++spins & 1023u) == 0) {
+          if (*reinterpret_cast<volatile int*>(&t.h->abort)) {
+            ok = 0;
+            break;
+          }
+          if (globaltimer() - t0 > (unsigned long long)t.timeout_ns) {
+            atomicExch(&t.h->abort, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    t.S->ok = ok;
+  }
+  __syncthreads();
+  return t.S->ok != 0;
+}
+
+struct TeamSyncFn {
+  Team* t;
+  __device__ bool operator()() { return team_sync(*t); }
+};
+
+// Team-wide sum of one double per thread, identical in every block: block
+// partials in warp order, then the team's partials in rank order.  `buf`
+// alternates between two halves of the system's partials array.
+static __device__ bool team_sum_d(Team& t, double v, double* partials, int& red, double& out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) t.S->dpart[warp] = v;
+  __syncthreads();
+  double* buf = partials + (red & 1) * kMaxGrid;
+  ++red;
+  if (threadIdx.x < 32) {
+    double s = lane < kBatchWarps ? t.S->dpart[lane] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) {
+      if (t.size == 1) t.S->val[0] = s;
+      else buf[t.rank] = s;
+    }
+  }
+  if (t.size > 1) {
+    if (!team_sync(t)) return false;
+    if (threadIdx.x < 32) {
+      double s = 0.0;
+      for (int i = lane; i < t.size; i += 32) s += buf[i];
+      s = warp_sum(s);
+      if (threadIdx.x == 0) t.S->val[0] = s;
+    }
+  }
+  __syncthreads();
+  out = t.S->val[0];
+  __syncthreads();
+  return true;
+}
+
+// Same for float-float partial sums (single-precision stage).
+static __device__ bool team_sum_ff(Team& t, FF v, double* partials, int& red, double& out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = ff_warp_sum(v);
+  if (lane == 0) {
+    t.S->ffp[2 * warp] = v.hi;
+    t.S->ffp[2 * warp + 1] = v.lo;
+  }
+  __syncthreads();
+  double* buf = partials + (red & 1) * kMaxGrid;
+  ++red;
+  if (threadIdx.x < 32) {
+    FF s = lane < kBatchWarps ? FF{t.S->ffp[2 * lane], t.S->ffp[2 * lane + 1]} : FF{0.f, 0.f};
+    s = ff_warp_sum(s);
+    const double bs = (double)s.hi + (double)s.lo;
+    if (threadIdx.x == 0) {
+      if (t.size == 1) t.S->val[0] = bs;
+      else buf[t.rank] = bs;
+    }
+  }
+  if (t.size > 1) {
+    if (!team_sync(t)) return false;
+    if (threadIdx.x < 32) {
+      double s = 0.0;
+      for (int i = lane; i < t.size; i += 32) s += buf[i];
+      s = warp_sum(s);
+      if (threadIdx.x == 0) t.S->val[0] = s;
+    }
+  }
+  __syncthreads();
+  out = t.S->val[0];
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Per-system set-up by the team (the same steps as the set-up kernels of the
+// single-system path).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int team_tid(const Team& t) { return t.rank * kBatchThreads + threadIdx.x; }
+__device__ __forceinline__ int team_threads(const Team& t) { return t.size * kBatchThreads; }
+
+// Control block of the system: zeroed and initialised by the team leader block.
+static __device__ void sys_init(const Team& t, const BatchSys& s, const BatchArgs& a) {
+  Ctl* c = s.w.ctl;
+  if (t.rank != 0) return;
+  int* ci = reinterpret_cast<int*>(c);
+  for (int k = threadIdx.x; k < (int)(sizeof(Ctl) / sizeof(int)); k += blockDim.x) ci[k] = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const mpcg_options_t& o = a.o;
+    c->t_start = globaltimer();
+    c->n = s.n;
+    c->nnz = s.nnz;
+    c->nslices = s.nslices;
+    c->wcap = s.wcap;
+    c->k0 = o.k0 > 0 ? o.k0 : 0;
+    c->max1 = o.max_it_fp32 > 0 ? o.max_it_fp32 : s.n;
+    const long long m2 = o.max_it_fp64 > 0 ? (long long)o.max_it_fp64 : 10ll * s.n;
+    c->max2 = m2 > 0x7fffffffll ? 0x7fffffff : (int)m2;
+    c->max_restarts = o.max_true_restarts > 0 ? o.max_true_restarts : 0;
+    c->tol_relative = o.tol_relative ? 1 : 0;
+    c->eps1 = o.fp64_only ? 0.0 : (a.auto_eps1 ? -1.0 : o.eps1);
+    c->eps2 = s.eps2;
+    c->timeout_ns = (long long)(o.timeout_ms > 0 ? o.timeout_ms : 20000) * 1000000ll;
+    c->cls = -1;
+    c->first = 1;
+    c->x32_src = -1;
+  }
+}
+
+// CSR check, b~ = float32(b), slice widths (one warp per slice).
+static __device__ void sys_rows(const Team& t, const BatchSys& s) {
+  Ctl* c = s.w.ctl;
+  const int lane = threadIdx.x & 31;
+  const int T = team_threads(t);
+  const int32_t* rp = s.A.row_ptr;
+  const int32_t* col = s.A.col;
+  for (int base = team_tid(t) - lane; base < s.nslices * kSlice; base += T) {
+    const int i = base + lane;
+    int len = 0, ok = 1;
+    if (i < s.n) {
+      const int a0 = rp[i], e = rp[i + 1];
+      if (a0 < 0 || e < a0 || e > s.nnz) {
+        ok = 0;
+      } else {
+        len = e - a0;
+        int prev = -1;
+        for (int k = a0; k < e; ++k) {
+          const int cc = col[k];
+          if (cc < 0 || cc >= s.n || cc <= prev) {
+            ok = 0;
+            break;
+          }
+          prev = cc;
+        }
+      }
+      if (i == 0 && a0 != 0) ok = 0;
+      if (i == s.n - 1 && e != s.nnz) ok = 0;
+      s.w.b32[i] = (float)s.b[i];
+    }
+    if (!ok) {
+      set_status(c, MPCG_ERR_INVALID_ARG);
+      len = 0;
+    }
+    const int w = len < s.wcap ? len : s.wcap;
+    const int wmax = __reduce_max_sync(0xffffffffu, w);
+    const int any_ovf = __any_sync(0xffffffffu, len > s.wcap);
+    if (lane == 0) s.w.slice_w[i >> 5] = (uint32_t)wmax | (any_ovf ? kOverflowBit : 0u);
+  }
+}
+
+// Exclusive scan of 32 * width over the slices, by one block.
+constexpr int kBScanPer = 8;
+constexpr int kBScanTile = kBatchThreads * kBScanPer;
+static __device__ void block_scan_slices(const uint32_t* slice_w, int32_t* slice_ptr, int nslices) {
+  __shared__ int32_t tile[kBScanTile];
+  __shared__ long long part[kBatchThreads];
+  __shared__ long long carry_s;
+  const int t = threadIdx.x;
+  if (t == 0) carry_s = 0;
+  __syncthreads();
+  for (int base = 0; base < nslices; base += kBScanTile) {
+    for (int j = t; j < kBScanTile; j += kBatchThreads) {
+      const int sidx = base + j;
+      tile[j] = sidx < nslices ? (int32_t)(kSlice * (slice_w[sidx] & ~kOverflowBit)) : 0;
+    }
+    __syncthreads();
+    long long loc = 0;
+    for (int j = 0; j < kBScanPer; ++j) loc += tile[t * kBScanPer + j];
+    part[t] = loc;
+    __syncthreads();
+    for (int o = 1; o < kBatchThreads; o <<= 1) {
+      const long long v = t >= o ? part[t - o] : 0;
+      __syncthreads();
+      part[t] += v;
+      __syncthreads();
+    }
+    long long run = carry_s + part[t] - loc;
+    for (int j = 0; j < kBScanPer; ++j) {
+      const int v = tile[t * kBScanPer + j];
+      tile[t * kBScanPer + j] = (int32_t)run;
+      run += v;
+    }
+    __syncthreads();
+    for (int j = t; j < kBScanTile; j += kBatchThreads) {
+      const int sidx = base + j;
+      if (sidx < nslices) slice_ptr[sidx] = tile[j];
+    }
+    if (t == kBatchThreads - 1) carry_s += part[kBatchThreads - 1];
+    __syncthreads();
+  }
+  if (t == 0) slice_ptr[nslices] = (int32_t)carry_s;
+  __syncthreads();
+}
+
+// Sliced arrays: entry k of row i at slice_ptr[s] + 32 k + (i mod 32); short
+// rows padded with value 0 and their own column.
+static __device__ void sys_fill(const Team& t, const BatchSys& s) {
+  const int T = team_threads(t);
+  const int32_t* rp = s.A.row_ptr;
+  for (int i = team_tid(t); i < s.nslices * kSlice; i += T) {
+    const int sl = i >> 5, lane = i & 31;
+    const int w = (int)(s.w.slice_w[sl] & ~kOverflowBit);
+    const int base = s.w.slice_ptr[sl] + lane;
+    int a0 = 0, len = 0;
+    if (i < s.n) {
+      a0 = rp[i];
+      len = rp[i + 1] - a0;
+    }
+    for (int k = 0; k < w; ++k) {
+      const int e = base + kSlice * k;
+      if (k < len) {
+        const double v = s.A.val[a0 + k];
+        s.w.scol[e] = s.A.col[a0 + k];
+        s.w.sv64[e] = v;
+        s.w.sv32[e] = (float)v;
+      } else {
+        s.w.scol[e] = i < s.n ? i : 0;
+        s.w.sv64[e] = 0.0;
+        s.w.sv32[e] = 0.0f;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// CG stages over the team.  Warp gw of the team owns slices gw, gw + W, ...;
+// lane l owns row 32 s + l of slice s in every phase, so the vector updates
+// of a row are done by the thread that produced its SpMV result.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ const T* bvals(const BatchSys& s);
+template <>
+__device__ __forceinline__ const float* bvals<float>(const BatchSys& s) { return s.w.sv32; }
+template <>
+__device__ __forceinline__ const double* bvals<double>(const BatchSys& s) { return s.w.sv64; }
+
+// Overflow tail of row i (entries past the slice width, from the CSR).
+template <typename T, class Gather>
+__device__ __forceinline__ T btail(const BatchSys& s, int i, int w, T acc, Gather G) {
+  const int e1 = s.A.row_ptr[i + 1];
+  for (int e = s.A.row_ptr[i] + w; e < e1; ++e) acc = fma((T)s.A.val[e], G(s.A.col[e]), acc);
+  return acc;
+}
+
+__device__ __forceinline__ int team_warp(const Team& t);
+__device__ __forceinline__ int team_warps(const Team& t);
+
+// SpMV over the team's slices: warp gw owns slices gw, gw + W, ...; lane l
+// owns row 32 s + l.  Rw(i, acc) receives row i's sum in stored order (fused
+// multiply-adds from zero, padding rows included).  The metadata of 32 of
+// the warp's slices is loaded at once (one slice per lane) and two slices
+// are summed together so that their loads and gathers overlap.
+template <typename T, class Gather, class Row>
+__device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gather G, Row Rw) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int gw = team_warp(t), W = team_warps(t);
+  const T* sv = bvals<T>(s);
+  const int32_t* sc = s.w.scol;
+  for (int base = gw; base < s.nslices; base += 32 * W) {
+    const int mine = base + lane * W;
+    uint32_t mwf = 0u;
+    int mp = 0;
+    if (mine < s.nslices) {
+      mwf = s.w.slice_w[mine];
+      mp = s.w.slice_ptr[mine];
+    }
+    const int cnt = min(32, (s.nslices - base + W - 1) / W);
+    for (int j = 0; j < cnt; j += 2) {
+      const int j1 = min(j + 1, 31);
+      const bool h1 = j + 1 < cnt;
+      const uint32_t wf0 = __shfl_sync(full, mwf, j);
+      const uint32_t wf1 = __shfl_sync(full, mwf, j1);
+      const int p0 = __shfl_sync(full, mp, j) + lane;
+      const int p1 = __shfl_sync(full, mp, j1) + lane;
+      const int w0 = (int)(wf0 & ~kOverflowBit);
+      const int w1 = h1 ? (int)(wf1 & ~kOverflowBit) : 0;
+      const int i0 = (base + j * W) * kSlice + lane;
+      const int i1 = (base + (j + 1) * W) * kSlice + lane;
+      T a0 = (T)0, a1 = (T)0;
+      const int wm = max(w0, w1);
+#pragma unroll 4
+      for (int k = 0; k < wm; ++k) {
+        if (k < w0) a0 = fma(sv[p0 + kSlice * k], G(sc[p0 + kSlice * k]), a0);
+        if (k < w1) a1 = fma(sv[p1 + kSlice * k], G(sc[p1 + kSlice * k]), a1);
+      }
+      if ((wf0 & kOverflowBit) && i0 < s.n) a0 = btail<T>(s, i0, w0, a0, G);
+      Rw(i0, a0);
+      if (h1) {
+        if ((wf1 & kOverflowBit) && i1 < s.n) a1 = btail<T>(s, i1, w1, a1, G);
+        Rw(i1, a1);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ int team_warp(const Team& t) { return t.rank * kBatchWarps + (threadIdx.x >> 5); }
+__device__ __forceinline__ int team_warps(const Team& t) { return t.size * kBatchWarps; }
+
+// Broadcast of thread 0's decision (and scalars) to the block.
+__device__ __forceinline__ int bcast_dec(Team& t, int dec) {
+  if (threadIdx.x == 0) t.S->ival[0] = dec;
+  __syncthreads();
+  const int d = t.S->ival[0];
+  __syncthreads();
+  return d;
+}
+
+enum BDec { kBGo = 0, kBStop = 1, kBNan = 2, kBBroke = 3, kBBreakdown = 4, kBCap = 5, kBSuspend = 6 };
+
+// Single-precision stage; modes as in the single-system kernel (kCgK0,
+// kCgToEps1, kCgContinue).  The state needed to continue is kept in the
+// control block.  Outside the k0 phase at most `budget` iterations run;
+// *done is false when the budget ended the call before the stage ended.
+// Returns false if the launch aborted.
+static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, int budget, bool* done) {
+  *done = true;
+  Ctl* ctl = s.w.ctl;
+  const int lane = threadIdx.x & 31;
+  const int gw = team_warp(t), W = team_warps(t);
+  const int n = s.n, rel = ctl->tol_relative;
+  const bool lead = threadIdx.x == 0, lead0 = lead && t.rank == 0;
+  if (mode == kCgContinue && ctl->broke32) {  // stage 1 already ended in the k0 phase
+    if (lead0) {
+      if (ctl->res32 > ctl->eps1) ctl->warn_eps1 = 1;
+      ctl->t_fp32 = globaltimer();
+    }
+    return true;
+  }
+  float* x = s.w.x32;
+  float* r = s.w.r32;
+  float* q = s.w.q32;
+  double rr, bnorm;
+  float beta;
+  int first, parity, it;
+  if (mode != kCgContinue) {
+    FF acc{0.f, 0.f};
+    for (int sl = gw; sl < s.nslices; sl += W) {
+      const int i = sl * kSlice + lane;
+      if (i < n) {
+        const float bi = s.w.b32[i];
+        x[i] = 0.0f;
+        r[i] = bi;
+        s.w.d32a[i] = 0.0f;  // d_{-1}
+        ff_add_prod(acc, bi, bi);
+      }
+    }
+    double tot;
+    if (!team_sum_ff(t, acc, s.w.partials, red, tot)) return false;
+    rr = tot;
+    if (lead) t.S->val[1] = sqrt(tot);
+    __syncthreads();
+    bnorm = t.S->val[1];
+    __syncthreads();
+    if (lead0) {
+      ctl->bnorm32 = bnorm;
+      if (!isfinite(bnorm)) set_status(ctl, MPCG_ERR_NAN);
+    }
+    if (!isfinite(bnorm)) return true;
+    first = 1;
+    parity = 0;
+    beta = 0.0f;
+    it = 0;
+  } else {
+    rr = ctl->rr;
+    bnorm = ctl->bnorm32;
+    beta = ctl->beta32;
+    first = ctl->first;
+    parity = ctl->parity;
+    it = ctl->n1;
+  }
+  const double eps = mode == kCgK0 ? ctl->eps2 : ctl->eps1;
+  const int limit = mode == kCgK0 ? min(ctl->k0, ctl->max1) : ctl->max1;
+  const int it_start = it;
+  double vsum = 0.0;  // thread 0
+  int k0done = 0, broke = 0, suspended = 0;
+  while (true) {
+    int dec = kBGo;
+    if (lead) {
+      const double m = stop_measure(rr, bnorm, rel);
+      if (isnan(m)) dec = kBNan;
+      else if (m <= eps || it >= limit || (mode == kCgK0 && rr == 0.0)) dec = kBStop;
+      else if (mode != kCgK0 && it - it_start >= budget) dec = kBSuspend;
+    }
+    dec = bcast_dec(t, dec);
+    if (dec == kBSuspend) {
+      suspended = 1;
+      break;
+    }
+    if (dec != kBGo) {
+      if (dec == kBNan && lead0) set_status(ctl, MPCG_ERR_NAN);
+      break;
+    }
+    // P1: q = A d_k, d_k = r_k + beta_k d_{k-1} formed for every gathered column
+    const float* dold = parity ? s.w.d32b : s.w.d32a;
+    float* dnew = parity ? s.w.d32a : s.w.d32b;
+    const float bt = first ? 0.0f : beta;
+    FF pdq{0.f, 0.f};
+    team_spmv<float>(
+        t, s, [&](int c) -> float { return __fmaf_rn(bt, dold[c], r[c]); },
+        [&](int i, float acc) {
+          if (i < n) {
+            const float di = __fmaf_rn(bt, dold[i], r[i]);
+            dnew[i] = di;
+            q[i] = acc;
+            ff_add_prod(pdq, di, acc);
+          }
+        });
+    double dq;
+    if (!team_sum_ff(t, pdq, s.w.partials, red, dq)) return false;
+    dec = kBGo;
+    if (lead) {
+      if (!isfinite(dq)) dec = kBNan;
+      else if (!(dq > 0.0)) dec = kBBroke;
+      else t.S->fval[0] = (float)(rr / dq);
+    }
+    dec = bcast_dec(t, dec);
+    if (dec == kBNan) {
+      if (lead0) set_status(ctl, MPCG_ERR_NAN);
+      break;
+    }
+    if (dec == kBBroke) {  // stage 1 ends here; x~ and r unchanged
+      broke = 1;
+      break;
+    }
+    const float alpha = t.S->fval[0];
+    // P2: x += alpha d_k, r -= alpha q, r^T r
+    FF prr{0.f, 0.f};
+    for (int sl = gw; sl < s.nslices; sl += W) {
+      const int i = sl * kSlice + lane;
+      if (i < n) {
+        x[i] = __fmaf_rn(alpha, dnew[i], x[i]);
+        const float ri = __fmaf_rn(-alpha, q[i], r[i]);
+        r[i] = ri;
+        ff_add_prod(prr, ri, ri);
+      }
+    }
+    double rrn;
+    if (!team_sum_ff(t, prr, s.w.partials, red, rrn)) return false;
+    dec = kBGo;
+    if (lead) {
+      if (!isfinite(rrn)) {
+        dec = kBNan;
+      } else {
+        if (mode == kCgK0) vsum += sqrt(rrn) / sqrt(rr);  // Eq. (13) ratio
+        t.S->fval[1] = (float)(rrn / rr);
+      }
+    }
+    dec = bcast_dec(t, dec);
+    if (dec == kBNan) {
+      if (lead0) set_status(ctl, MPCG_ERR_NAN);
+      break;
+    }
+    beta = t.S->fval[1];
+    rr = rrn;
+    if (mode == kCgK0) ++k0done;
+    parity ^= 1;
+    first = 0;
+    ++it;
+  }
+  if (suspended) *done = false;
+  if (lead0) {
+    ctl->rr = rr;
+    ctl->beta32 = beta;
+    ctl->first = first;
+    ctl->parity = parity;
+    ctl->n1 = it;
+  }
+  if (lead0 && !suspended) {
+    ctl->res32 = stop_measure(rr, bnorm, rel);
+    if (broke) ctl->broke32 = 1;
+    if (mode == kCgK0) {
+      ctl->k0_done = k0done;
+      ctl->vsum = vsum;
+      ctl->v = k0done > 0 ? vsum / (double)k0done : 0.0;
+    } else {
+      if (ctl->res32 > ctl->eps1) ctl->warn_eps1 = 1;
+      ctl->t_fp32 = globaltimer();
+    }
+  }
+  return true;
+}
+
+// Double-precision stage: x0 = float64(x~) (or 0), restart r = b - A x0,
+// d = r; CG to eps2 on the recursive residual; then the true residual, and a
+// restart from x when it misses eps2 (at most max_restarts times).  At most
+// `budget` iterations run per call; with `resume` the call continues the
+// iteration state kept in the workspace (x, r, d) and the control block
+// (r^T r, iterations, restarts).  *done is false when the budget ended it.
+static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& red, int budget,
+                         bool resume, bool* done) {
+  *done = true;
+  Ctl* ctl = s.w.ctl;
+  const int lane = threadIdx.x & 31;
+  const int gw = team_warp(t), W = team_warps(t);
+  const int n = s.n, rel = ctl->tol_relative;
+  const bool lead = threadIdx.x == 0, lead0 = lead && t.rank == 0;
+  const double bnorm = ctl->bnorm64, eps2 = ctl->eps2;
+  const int max2 = ctl->max2, max_restarts = ctl->max_restarts;
+  double* x = s.x;
+  double* r = s.w.r64;
+  double* d = s.w.d64;
+  double* q = s.w.q64;
+  const double* b = s.b;
+  if (!resume) {
+    for (int sl = gw; sl < s.nslices; sl += W) {
+      const int i = sl * kSlice + lane;
+      if (i < n) x[i] = from_zero ? 0.0 : (double)s.w.x32[i];
+    }
+    if (!team_sync(t)) return false;
+  }
+  int it = resume ? ctl->n2 : 0, restarts = resume ? ctl->restarts : 0, failed = 0;
+  const int it_start = it;
+  double rr = resume ? ctl->rr : 0.0, m = 0.0, true_rel = NAN;
+  bool skip_restart = resume;
+  for (;;) {
+    // restart (CG line 1 from x): r = b - A x, d = r, r^T r
+    if (!skip_restart) {
+    double p = 0.0;
+    team_spmv<double>(
+        t, s, [&](int c) -> double { return x[c]; },
+        [&](int i, double acc) {
+          if (i < n) {
+            const double ri = b[i] - acc;
+            r[i] = ri;
+            d[i] = ri;
+            p = __fma_rn(ri, ri, p);
+          }
+        });
+    if (!team_sum_d(t, p, s.w.partials, red, rr)) return false;
+    }
+    skip_restart = false;
+    bool converged = false;
+    for (;;) {
+      int dec = kBGo;
+      if (lead) {
+        m = stop_measure(rr, bnorm, rel);
+        if (isnan(m)) dec = kBNan;
+        else if (m <= eps2) dec = kBStop;
+        else if (it >= max2) dec = kBCap;
+        else if (it - it_start >= budget) dec = kBSuspend;
+      }
+      dec = bcast_dec(t, dec);
+      if (dec == kBSuspend) {  // keep the iteration state for the next call
+        if (lead0) {
+          ctl->rr = rr;
+          ctl->n2 = it;
+          ctl->restarts = restarts;
+        }
+        *done = false;
+        return true;
+      }
+      if (dec == kBNan) {
+        failed = MPCG_ERR_NAN;
+        break;
+      }
+      if (dec == kBStop) {
+        converged = true;
+        break;
+      }
+      if (dec == kBCap) {
+        failed = MPCG_ERR_NOT_CONVERGED;
+        break;
+      }
+      // P1: q = A d, d^T q
+      double pq = 0.0;
+      team_spmv<double>(
+          t, s, [&](int c) -> double { return d[c]; },
+          [&](int i, double acc) {
+            if (i < n) {
+              q[i] = acc;
+              pq = __fma_rn(d[i], acc, pq);
+            }
+          });
+      double dq;
+      if (!team_sum_d(t, pq, s.w.partials, red, dq)) return false;
+      dec = kBGo;
+      if (lead) {
+        if (!isfinite(dq)) dec = kBNan;
+        else if (!(dq > 0.0)) dec = kBBreakdown;
+        else t.S->val[2] = rr / dq;
+      }
+      dec = bcast_dec(t, dec);
+      if (dec != kBGo) {
+        failed = dec == kBNan ? MPCG_ERR_NAN : MPCG_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = t.S->val[2];
+      // P2: x += alpha d, r -= alpha q, r^T r
+      double pr = 0.0;
+      for (int sl = gw; sl < s.nslices; sl += W) {
+        const int i = sl * kSlice + lane;
+        if (i < n) {
+          x[i] = __fma_rn(alpha, d[i], x[i]);
+          const double ri = __fma_rn(-alpha, q[i], r[i]);
+          r[i] = ri;
+          pr = __fma_rn(ri, ri, pr);
+        }
+      }
+      double rrn;
+      if (!team_sum_d(t, pr, s.w.partials, red, rrn)) return false;
+      dec = kBGo;
+      if (lead) {
+        if (!isfinite(rrn)) dec = kBNan;
+        else t.S->val[3] = rrn / rr;
+      }
+      dec = bcast_dec(t, dec);
+      if (dec == kBNan) {
+        failed = MPCG_ERR_NAN;
+        break;
+      }
+      const double beta = t.S->val[3];
+      rr = rrn;
+      // P3: d = r + beta d
+      for (int sl = gw; sl < s.nslices; sl += W) {
+        const int i = sl * kSlice + lane;
+        if (i < n) d[i] = __fma_rn(beta, d[i], r[i]);
+      }
+      if (!team_sync(t)) return false;
+      ++it;
+    }
+    if (failed && failed != MPCG_ERR_NOT_CONVERGED) break;
+    // true residual ||b - A x|| (also after the iteration cap)
+    double pt = 0.0;
+    team_spmv<double>(
+        t, s, [&](int c) -> double { return x[c]; },
+        [&](int i, double acc) {
+          if (i < n) {
+            const double ri = b[i] - acc;
+            pt = __fma_rn(ri, ri, pt);
+          }
+        });
+    double tot;
+    if (!team_sum_d(t, pt, s.w.partials, red, tot)) return false;
+    int again = 0;
+    if (lead) {
+      true_rel = bnorm > 0.0 ? sqrt(tot) / bnorm : sqrt(tot);
+      const double tm = rel ? true_rel : sqrt(tot);
+      again = converged && tm > eps2 && restarts < max_restarts;
+    }
+    again = bcast_dec(t, again);
+    if (!again) break;
+    ++restarts;
+  }
+  if (lead0) {
+    if (failed) set_status(ctl, failed);
+    ctl->n2 = it;
+    ctl->restarts = restarts;
+    if (restarts) ctl->warn_restart = 1;
+    ctl->res64 = m;
+    ctl->true_rel = true_rel;
+    ctl->rr = rr;
+    ctl->t_fp64 = globaltimer();
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// One system, start to finish, by the team.
+// ---------------------------------------------------------------------------------------
+static __device__ void sys_finalize(const Team& t, const BatchSys& s) {
+  if (t.rank != 0 || threadIdx.x != 0) return;
+  const Ctl* c = s.w.ctl;
+  mpcg_result_t* res = s.res;
+  int st = c->status;
+  if (st == 0) st = c->warn_restart ? MPCG_WARN_TRUE_RESID_RESTARTED
+                                    : (c->warn_eps1 ? MPCG_WARN_EPS1_NOT_REACHED : MPCG_OK);
+  res->status = st;
+  res->n1 = c->n1;
+  res->n2 = c->n2;
+  res->cls = c->cls;
+  res->k0_done = c->k0_done;
+  res->restarts = c->restarts;
+  res->eps1 = c->eps1;
+  res->true_rel_resid = c->true_rel;
+  res->pdiam = (double)c->pdiam;
+  res->v = c->v;
+  res->res_fp32 = c->res32;
+  res->res_fp64 = c->res64;
+  res->t_start_ns = c->t_start;
+  const unsigned long long t0 = c->t_prep ? c->t_prep : c->t_start;
+  res->t_features_ns = c->t_features ? c->t_features : t0;
+  res->t_fp32_ns = c->t_fp32 ? c->t_fp32 : res->t_features_ns;
+  res->t_fp64_ns = c->t_fp64 ? c->t_fp64 : res->t_fp32_ns;
+  res->t_end_ns = globaltimer();
+  res->t_prep_ns = t0;
+}
+
+// Status of the system as seen after a team barrier (identical in every block).
+__device__ __forceinline__ int sys_status(const BatchSys& s) { return volatile_status(s.w.ctl); }
+
+// Leader: next system for a team of class c -- its own queue first, then
+// the queues of smaller classes.  -1 when all are empty.
+static __device__ int batch_take(BatchHdr* h, const int* order, int c) {
+  for (int cc = c; cc >= 0; --cc) {
+    if (*reinterpret_cast<volatile int*>(&h->head[cc]) >= h->qlen[cc]) continue;
+    const int i = atomicAdd(&h->head[cc], 1);
+    if (i < h->qlen[cc]) return order[h->qbase[cc] + i];
+  }
+  return -1;
+}
+
+// ---------------------------------------------------------------------------------------
+// Host: plan of a team launch (batch.cu).
+// ---------------------------------------------------------------------------------------
+struct Plan {
+  std::vector<int> team_of_block, rank_of_block, team_size, team_class, order;
+  int qbase[kTeamClasses], qlen[kTeamClasses];
+};
+// Teams for a grid of `grid` blocks and the class queues of nsys systems of
+// n rows with estimated work `work` (largest first within a class).
+Plan make_plan(int nsys, const int* n, const double* work, int grid);
+
+}  // namespace mpcg

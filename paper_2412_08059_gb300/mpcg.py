@@ -28,6 +28,7 @@ ERR_NAN = -4
 ERR_NOT_CONVERGED = -5
 ERR_TIMEOUT = -6
 ERR_CUDA = -7
+PHASE_NEW, PHASE_STAGE1, PHASE_STAGE2, PHASE_STAGE2_RUN, PHASE_DONE = 0, 1, 2, 3, 4
 KNN_MAX_SAMPLE = 65536
 KNN_MAX_K = 64
 
@@ -81,7 +82,9 @@ class Result(C.Structure):
 
 SYMBOLS = ("mpcg_options_default", "mpcg_status_string", "mpcg_workspace_bytes", "mpcg_features",
            "mpcg_choose_eps1", "mpcg_solve", "mpcg_batch_workspace_bytes", "mpcg_solve_batch",
-           "mpcg_spmv", "mpcg_bfs", "mpcg_pseudo_diameter", "mpcg_solve_static")
+           "mpcg_spmv", "mpcg_bfs", "mpcg_pseudo_diameter", "mpcg_solve_static",
+           "mpcg_server_workspace_bytes", "mpcg_server_create", "mpcg_server_destroy",
+           "mpcg_server_admit", "mpcg_batch_step", "mpcg_server_retire")
 
 
 def load(path: str = LIB_PATH):
@@ -119,6 +122,20 @@ def load(path: str = LIB_PATH):
         L.mpcg_bfs.argtypes = [C.POINTER(CsrDesc), I32, P, P, SZ, P]
         L.mpcg_pseudo_diameter.restype = I32
         L.mpcg_pseudo_diameter.argtypes = [C.POINTER(CsrDesc), P, P, SZ, P]
+        L.mpcg_server_workspace_bytes.restype = SZ
+        L.mpcg_server_workspace_bytes.argtypes = [I32, SZ]
+        L.mpcg_server_create.restype = I32
+        L.mpcg_server_create.argtypes = [P, SZ, I32, C.POINTER(SampleDesc), C.POINTER(Options),
+                                         C.POINTER(C.c_void_p)]
+        L.mpcg_server_destroy.restype = None
+        L.mpcg_server_destroy.argtypes = [P]
+        L.mpcg_server_admit.restype = I32
+        L.mpcg_server_admit.argtypes = [P, C.POINTER(CsrDesc), P, P, C.c_double, P,
+                                        C.POINTER(I32)]
+        L.mpcg_batch_step.restype = I32
+        L.mpcg_batch_step.argtypes = [P, I32, P, P]
+        L.mpcg_server_retire.restype = I32
+        L.mpcg_server_retire.argtypes = [P, I32]
         L.mpcg_solve_static.restype = I32
         L.mpcg_solve_static.argtypes = [C.POINTER(CsrDesc), P, P, C.POINTER(SampleDesc),
                                         C.POINTER(Options), P, P]
@@ -307,3 +324,57 @@ def batch_workspace_bytes(mats: list[DeviceCSR]) -> int:
     ns = (C.c_int32 * n)(*[m.n for m in mats])
     nz = (C.c_int32 * n)(*[m.nnz for m in mats])
     return int(load().mpcg_batch_workspace_bytes(n, ns, nz, None))
+
+
+class Server:
+    """Continuous batching over a slot table (mpcg_server_* and mpcg_batch_step).
+    The caller keeps each admitted system's CSR, b, x and result record alive
+    until it retires the slot."""
+
+    def __init__(self, max_slots: int, pool_bytes: int, opts: Options,
+                 sample: DeviceSample | None = None, device="cuda"):
+        L = load()
+        nb = int(L.mpcg_server_workspace_bytes(max_slots, pool_bytes))
+        if nb == 0:
+            raise ValueError("invalid server size")
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=device)
+        self.max_slots = max_slots
+        self.sample = sample
+        h = C.c_void_p()
+        st = L.mpcg_server_create(_ptr(self.ws), nb, max_slots,
+                                  C.byref(sample.desc) if sample is not None else None,
+                                  C.byref(opts), C.byref(h))
+        _check(st, "mpcg_server_create")
+        self.h = h
+        self.phase = torch.full((max_slots,), -1, dtype=torch.int32).pin_memory()
+
+    def admit(self, A: DeviceCSR, b: torch.Tensor, x: torch.Tensor, eps2: float,
+              res: torch.Tensor):
+        """Slot number, or None when no slot or pool block is free."""
+        slot = C.c_int32(-1)
+        st = load().mpcg_server_admit(self.h, C.byref(A.desc), _ptr(b), _ptr(x), float(eps2),
+                                      _ptr(res), C.byref(slot))
+        if st == ERR_WORKSPACE:
+            return None
+        _check(st, "mpcg_server_admit")
+        return slot.value
+
+    def step(self, max_iters: int, stream=None) -> None:
+        """Enqueue one step; self.phase holds the slot phases after a synchronise."""
+        st = load().mpcg_batch_step(self.h, int(max_iters), C.c_void_p(self.phase.data_ptr()),
+                                    _stream(stream))
+        _check(st, "mpcg_batch_step")
+
+    def retire(self, slot: int) -> None:
+        _check(load().mpcg_server_retire(self.h, int(slot)), "mpcg_server_retire")
+
+    def close(self) -> None:
+        if self.h is not None:
+            load().mpcg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
