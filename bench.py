@@ -10,8 +10,10 @@ grid sizes and coefficients, FP32 CG to eps1, FP64 restart to eps2, true
 residual.  value = solves per second over all ranks (inputs resident in HBM).
 
 Also reported: the same systems by pure FP64 CG (the baseline), a fixed-eps1
-sweep 1e-2..1e-7, the end-to-end rate with host buffers, the HBM roofline of
-the dominant kernel, and the CPU oracle timed on the host.
+sweep 1e-2..1e-7, the end-to-end rate with host buffers, the roofline of the
+dominant kernel (k_cg64, bound by the FP64 pipe), the CPU oracle timed on the
+host, a batch of 512 uneven systems (one launch) and a serving run (Poisson
+arrivals, continuous batching, p50/p99 latency).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 """
@@ -36,6 +38,9 @@ UNIT = "solves/s"
 KERNELS_PER_SOLVE_AUTO = 9    # k_init, k_rows, k_scan, k_fill, k_bnorm_*(2), k_stage1, k_cg64,
                                # k_finalize: the kernels one Algorithm II solve launches
 KERNELS_PER_SOLVE_FP64 = 8
+# DRAM bytes per FP64 iteration of k_cg64 at 128^3 from one ncu capture (65.64 GB over 307
+# passes of the captured launch); profiles/k_cg64_lap3d128.md.
+K_CG64_DRAM_BYTES_PER_ITER = 65.64e9 / 307
 
 
 def parse():
@@ -53,6 +58,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve section")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched-solve section")
     ap.add_argument("--batch-systems", type=int, default=512)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving section")
+    ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
 
 
@@ -301,6 +309,141 @@ def batch_section(args, dev, steps, warmup):
     }
 
 
+# Serving: Poisson arrivals, continuous batching
+# ------------------------------------------------------------------------------------------
+def serve_section(args, dev):
+    """A seeded Poisson stream of solve requests over 32 resident matrices
+    (n lognormal between 1e3 and 2e6; 2-D, 3-D, anisotropic and shifted
+    Laplacians; two right-hand sides each; eps2 1e-8 or 1e-10).  The offered
+    load is 80 % of the capacity measured with every request arriving at
+    once.  Served three ways: continuous batching (mpcg_batch_step, mixed
+    precision with auto eps1), the same in pure FP64, and one request at a
+    time in arrival order (mpcg_solve).  Latency = completion - arrival."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2412_08059_gb300 import mpcg, sample
+
+    rng = np.random.default_rng(21)
+    lo, hi = np.log(1e3), np.log(2e6)
+    sizes = np.clip(np.exp(rng.normal((lo + hi) / 2, (hi - lo) / 6, 32)), 1e3, 2e6)
+    mats, dmats, rhs = [], [], []
+    for k, nsz in enumerate(sizes):
+        fam = k % 4
+        if fam == 0:
+            sd = max(2, int(round(np.sqrt(nsz))))
+            A = synth.laplacian_2d(sd, sd)
+        else:
+            sd = max(2, int(round(nsz ** (1 / 3))))
+            A = synth.laplacian_3d(sd, eps=(1.0, 1.0, 1e-2, 1.0)[fam],
+                                   sigma=(0.0, 0.0, 0.0, 1e-2)[fam])
+        mats.append(A)
+        dmats.append(mpcg.DeviceCSR.from_host(A, dev))
+        rhs.append([torch.from_numpy(synth.rhs(A, seed=7000 + 2 * k + j)[1]).to(dev) for j in range(2)])
+    train = []
+    for i, d in enumerate(synth.batch_family(48, seed=22, n_lo=1e3, n_hi=5e5)):
+        A = synth.build_desc(d)
+        train.append((f"t{i}", A, synth.rhs(A, seed=9000 + i)[1]))
+    feat, cls, _ = sample.build(train, device=dev)
+    S = mpcg.DeviceSample(feat, cls, device=dev)
+    R = args.serve_requests
+    req_m = rng.integers(0, len(mats), R)
+    req_b = rng.integers(0, 2, R)
+    req_e = np.where(rng.random(R) < 0.5, 1e-8, 1e-10)
+    xs = [torch.empty(mats[m].n, dtype=torch.float64, device=dev) for m in req_m]
+    ress = [mpcg.result_buffer(1, dev) for _ in range(R)]
+    pool = int(sum(sorted((mpcg.workspace_bytes(A.n, A.nnz) for A in mats), reverse=True)[:24]))
+    max_iters = 40
+
+    def run_server(opts, arrivals):
+        srv = mpcg.Server(256, pool, opts, S, dev)
+        t0 = time.perf_counter()
+        done_t = np.zeros(R)
+        adm_t = np.zeros(R)
+        nxt, live, steps = 0, [], 0
+        order = np.argsort(arrivals, kind="stable")
+        while nxt < R or live:
+            now = time.perf_counter() - t0
+            while nxt < R and arrivals[order[nxt]] <= now:
+                i = order[nxt]
+                slot = srv.admit(dmats[req_m[i]], rhs[req_m[i]][req_b[i]], xs[i], float(req_e[i]), ress[i])
+                if slot is None:
+                    break
+                adm_t[i] = now
+                live.append((i, slot))
+                nxt += 1
+            if not live:
+                if nxt < R:
+                    time.sleep(max(0.0, arrivals[order[nxt]] - (time.perf_counter() - t0)))
+                continue
+            srv.step(max_iters)
+            torch.cuda.synchronize()
+            steps += 1
+            ph = srv.phase.numpy()
+            t_now = time.perf_counter() - t0
+            for i, slot in list(live):
+                if ph[slot] == mpcg.PHASE_DONE:
+                    srv.retire(slot)
+                    done_t[i] = t_now
+                    live.remove((i, slot))
+        makespan = time.perf_counter() - t0
+        srv.close()
+        res = [mpcg.read_results(r)[0] for r in ress]
+        return done_t, adm_t, makespan, steps, res
+
+    def run_fifo(opts, arrivals):
+        ws = torch.empty(max(mpcg.workspace_bytes(A.n, A.nnz) for A in mats), dtype=torch.uint8,
+                         device=dev)
+        t0 = time.perf_counter()
+        done_t = np.zeros(R)
+        for i in np.argsort(arrivals, kind="stable"):
+            now = time.perf_counter() - t0
+            if arrivals[i] > now:
+                time.sleep(arrivals[i] - now)
+            o = mpcg.options(eps2=float(req_e[i]))
+            mpcg.solve_async(dmats[req_m[i]], rhs[req_m[i]][req_b[i]], xs[i], o, ws, ress[i], S)
+            torch.cuda.synchronize()
+            done_t[i] = time.perf_counter() - t0
+        return done_t, time.perf_counter() - t0
+
+    o_mixed, o_fp64 = mpcg.options(), mpcg.options(fp64_only=1)
+    run_server(o_mixed, np.zeros(R))  # warm-up
+    _, _, burst, _, _ = run_server(o_mixed, np.zeros(R))
+    capacity = R / burst
+    rate = 0.8 * capacity
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, R))
+    arrivals -= arrivals[0]
+
+    def stats(done_t, adm_t, makespan, steps=None, res=None):
+        lat = (done_t - arrivals) * 1e3
+        out = {"solves_per_s": R / makespan, "latency_ms_p50": float(np.percentile(lat, 50)),
+               "latency_ms_p99": float(np.percentile(lat, 99)), "latency_ms_mean": float(lat.mean())}
+        if adm_t is not None:
+            out["queue_wait_ms_mean"] = float(((adm_t - arrivals) * 1e3).mean())
+        if steps is not None:
+            out["steps"] = steps
+            out["gpu_launches"] = steps
+        if res is not None:
+            out["failed"] = int(sum(r["status"] < 0 for r in res))
+            out["max_true_rel_resid_over_eps2"] = float(max(r["true_rel_resid"] / e for r, e in zip(res, req_e)))
+        return out
+
+    d, a, mk, st, res = run_server(o_mixed, arrivals)
+    mixed = stats(d, a, mk, st, res)
+    d, a, mk, st, res = run_server(o_fp64, arrivals)
+    fp64 = stats(d, a, mk, st, res)
+    d, mk = run_fifo(o_mixed, arrivals)
+    fifo = stats(d, None, mk)
+    return {"workload": f"{R} requests, Poisson arrivals at 80% of burst capacity "
+                        f"({rate:.0f}/s), 32 resident matrices n lognormal [1e3, 2e6] "
+                        "(2D/3D/aniso/shifted Laplacians), eps2 in {1e-8, 1e-10}",
+            "sum_n_resident": int(sum(A.n for A in mats)), "max_iters_per_step": max_iters,
+            "burst_capacity_solves_per_s": capacity,
+            "continuous_batching_mixed": mixed, "continuous_batching_fp64": fp64,
+            "one_at_a_time_mixed": fifo}
+
+
 # Native arm
 # ------------------------------------------------------------------------------------------
 def native_arm(args, rank, world, local_rank):
@@ -322,6 +465,10 @@ def native_arm(args, rank, world, local_rank):
     if args.batch_only:
         if rank == 0:
             print(json.dumps({"batch": batch_section(args, dev, args.steps, args.warmup)}), flush=True)
+        return
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"serve": serve_section(args, dev)}), flush=True)
         return
 
     def barrier():
@@ -483,17 +630,36 @@ def native_arm(args, rank, world, local_rank):
            "iters": r_s1["n1"]}
     k64 = {"kernel": "k_cg64", "bytes_per_launch": B64 * (r_d["n2"] + 2), "ms": k64_ms,
            "iters": r_d["n2"]}
-    dk = k64 if "k_cg64" in dominant else k32
-    achieved = dk["bytes_per_launch"] / (dk["ms"] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": dk["kernel"], "peak_source": peak_src,
-                "time_share_in_step": {k: round(v / sum(share.values()), 3) for k, v in share.items()},
-                "per_kernel": {k["kernel"]: {"GBps": round(k["bytes_per_launch"] / (k["ms"] * 1e-3) / 1e9, 1),
-                                             "frac": round(k["bytes_per_launch"] / (k["ms"] * 1e-3) / 1e9 / peak, 4),
-                                             "ms": round(k["ms"], 3), "iters": k["iters"],
-                                             "algorithmic_bytes_per_iter": B32 if k is k32 else B64}
-                               for k in (k32, k64)}}
+    # The dominant kernel is k_cg64; its busiest unit is the FP64 pipe (ncu: 64 % FP64 pipe,
+    # 38 % DRAM), so it is reported against the FP64 ALU peak: 2 FP64 FMA per clock per SM.
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    fp64_peak = 2 * 2 * props.multi_processor_count * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    flops64 = 2.0 * (nnz + 5 * n) * r_d["n2"] + 2.0 * 2 * (nnz + 2 * n)   # iterations + 2 passes
+    k64_tflops = flops64 / (k64_ms * 1e-3) / 1e12
+    per_kernel = {k["kernel"]: {"GBps": round(k["bytes_per_launch"] / (k["ms"] * 1e-3) / 1e9, 1),
+                                "frac_of_hbm": round(k["bytes_per_launch"] / (k["ms"] * 1e-3) / 1e9 / peak, 4),
+                                "ms": round(k["ms"], 3), "iters": k["iters"],
+                                "algorithmic_bytes_per_iter": B32 if k is k32 else B64}
+                  for k in (k32, k64)}
+    per_kernel["k_cg64"]["TFLOPs_fp64"] = round(k64_tflops, 4)
+    if "k_cg64" in dominant:
+        roofline = {"bound": "alu", "achieved": round(k64_tflops, 4), "peak": round(fp64_peak, 4),
+                    "unit": "TFLOP/s", "frac": round(k64_tflops / fp64_peak, 4),
+                    "traffic": round(K_CG64_DRAM_BYTES_PER_ITER * (r_d["n2"] + 2)),
+                    "kernel": "k_cg64",
+                    "peak_source": "derived: 2 FP64 FMA/clk/SM x %d SMs x %.0f MHz (nominal 1.25 TFLOP/s)" % (
+                        props.multi_processor_count, sm_mhz),
+                    "flops_per_iter": 2 * (nnz + 5 * n),
+                    "traffic_source": "ncu capture, DRAM bytes per iteration x iterations (profiles/k_cg64_lap3d128.md)"}
+    else:
+        achieved = k32["bytes_per_launch"] / (k32["ms"] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_cg32",
+                    "peak_source": peak_src}
+    roofline["time_share_in_step"] = {k: round(v / sum(share.values()), 3) for k, v in share.items()}
+    roofline["per_kernel"] = per_kernel
+    roofline["hbm_peak_GBps"] = {"value": peak, "source": peak_src}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -556,6 +722,9 @@ def native_arm(args, rank, world, local_rank):
     batch = None
     if not args.no_batch and rank == 0 and world == 1:
         batch = batch_section(args, dev, max(1, args.steps // 3), 1)
+    serve = None
+    if not args.no_serve and rank == 0 and world == 1:
+        serve = serve_section(args, dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -574,7 +743,7 @@ def native_arm(args, rank, world, local_rank):
                                            / (ms_fp64 / 1000.0)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": KERNELS_PER_SOLVE_AUTO * nsys * args.steps,
-                "clocks": clocks, "systems": per, "eps1_sweep": sweep, "batch": batch,
+                "clocks": clocks, "systems": per, "eps1_sweep": sweep, "batch": batch, "serve": serve,
                 "sample": {"desc": sample_desc, "seconds_to_build": round(t_sample, 1),
                            "labels": np.bincount(cls, minlength=8)[2:].tolist()}}
         print(json.dumps(line), flush=True)

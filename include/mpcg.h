@@ -177,7 +177,7 @@ int32_t mpcg_solve(const mpcg_csr_t* A, const double* b, double* x, const mpcg_s
  * features, eps1 (Algorithm II when opts->eps1 <= 0, with `sample`) and
  * result record, with the same options (fp64_only: pure FP64 CG for every
  * system); stage1_only is not supported here (MPCG_ERR_UNIMPLEMENTED).  The grid is split into teams of
- * 1..16 blocks; each team takes systems from size-class queues (largest
+ * 1..128 blocks; each team takes systems from size-class queues (largest
  * first) and runs the whole method on each, so systems of uneven size run
  * concurrently.  Workspace: mpcg_batch_workspace_bytes (a descriptor table,
  * then one region per system).  The descriptor table is copied from host

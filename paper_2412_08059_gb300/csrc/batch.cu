@@ -1,8 +1,8 @@
 // batch.cu -- many independent systems in one persistent launch (a batching
 // pattern; the paper solves one system at a time).
 //
-// The grid (one block per SM, cooperative) is split into teams of 1, 2, 4, 8
-// or 16 blocks.  A host-side planner puts every system in the queue of a
+// The grid (one block per SM, cooperative) is split into teams of 1, 2, 4,
+// ..., 128 blocks.  A host-side planner puts every system in the queue of a
 // team-size class (larger systems, larger teams; largest first) and gives
 // each class a number of teams in proportion to its estimated work.  The
 // leader of a team takes the next system from its class queue, or, when
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
 // Host: the plan (teams and queues) and the launch.
 // ---------------------------------------------------------------------------------------
 // Plan of one launch: teams (blocks, sizes, classes) and the class queues.
-// Team-size class of a system: the smallest team (1, 2, 4, 8, 16 blocks)
+// Team-size class of a system: the smallest team (1, 2, 4, ..., 128 blocks)
 // with at most kRowsPerBlock rows per block.
 int size_class(int n) {
   int c = 0;

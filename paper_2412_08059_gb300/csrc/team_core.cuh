@@ -1,7 +1,7 @@
 // team_core.cuh -- the whole method for one system, run by a team of blocks
 // of a persistent launch (the batched solve and the serving steps).
 //
-// A team is 1, 2, 4, 8 or 16 blocks of one cooperative launch.  Teams
+// A team is 1, 2, 4, ..., 128 blocks of one cooperative launch.  Teams
 // synchronise with a bounded barrier over their own blocks (a block barrier
 // for one-block teams).  Scalars are computed from team-wide sums that every
 // block of the team forms in the same order, so all blocks take the same
@@ -21,7 +21,7 @@ namespace mpcg {
 
 constexpr int kBatchThreads = 512;
 constexpr int kBatchWarps = kBatchThreads / 32;
-constexpr int kTeamClasses = 5;                // team sizes 1, 2, 4, 8, 16
+constexpr int kTeamClasses = 8;                // team sizes 1, 2, 4, ..., 128 blocks
 constexpr int kRowsPerBlock = 16384;           // planner: target rows per block of a team
 constexpr int kNoBudget = 0x7fffffff;          // iteration budget of a run-to-completion call
 
