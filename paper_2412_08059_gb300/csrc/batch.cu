@@ -65,7 +65,8 @@ __device__ bool sys_solve(Team& t, const BatchSys& s, const BatchArgs& a) {
   } else if (sys_status(s) == 0) {
     if (a.auto_eps1) {
       // Algorithm II: l~ by 2BFS, v over the first k0 iterations, eps1 by kNN
-      BfsGraph g{ctl, s.A.row_ptr, s.A.col, s.n, s.w.fq0, s.w.fq1, s.w.label, s.w.ckey};
+      BfsGraph g{ctl, s.A.row_ptr, s.A.col, s.n, s.w.fq0, s.w.fq1, s.w.label, s.w.ckey,
+                 s.w.fq2, s.w.fq3};
       TeamSyncFn sync{&t};
       if (!pseudo_diameter_run(g, s.w.dist, s.w.dist2, team_tid(t), team_threads(t), sync))
         return false;

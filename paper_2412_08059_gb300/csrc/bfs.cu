@@ -6,7 +6,7 @@
 
 namespace mpcg {
 
-__global__ void __launch_bounds__(kCgThreads) k_pdiam(BfsGraph g, int32_t* d1, int32_t* d2,
+__global__ void __launch_bounds__(kCgThreads, 1) k_pdiam(BfsGraph g, int32_t* d1, int32_t* d2,
                                                       int slot) {
   if (volatile_status(g.ctl) != 0) return;
   GridSync sync{g.ctl, slot, 0ull};
@@ -14,7 +14,7 @@ __global__ void __launch_bounds__(kCgThreads) k_pdiam(BfsGraph g, int32_t* d1, i
   pseudo_diameter_run(g, d1, d2, tid, gridDim.x * blockDim.x, sync);
 }
 
-__global__ void __launch_bounds__(kCgThreads) k_bfs1(BfsGraph g, int32_t* dist, int src,
+__global__ void __launch_bounds__(kCgThreads, 1) k_bfs1(BfsGraph g, int32_t* dist, int src,
                                                      int slot) {
   if (volatile_status(g.ctl) != 0) return;
   GridSync sync{g.ctl, slot, 0ull};
@@ -36,6 +36,8 @@ BfsGraph bfs_graph(const Launch& L) {
   g.n = L.d.n;
   g.fq0 = L.ws.fq0;
   g.fq1 = L.ws.fq1;
+  g.fq2 = L.ws.fq2;
+  g.fq3 = L.ws.fq3;
   g.label = L.ws.label;
   g.ckey = L.ws.ckey;
   return g;

@@ -13,7 +13,8 @@
 //
 // 2BFS readings: s = vertex 0 (the smallest vertex of its component); the
 // farthest vertex t is the smallest index at maximal distance (atomicMax over
-// the key (dist, ~index)).  If the first BFS misses vertices, components are
+// the key (dist, ~index)).  The second search is started speculatively from
+// vertex n - 1 together with the first (see pseudo_diameter_run).  If the first BFS misses vertices, components are
 // labelled by their smallest vertex (label propagation with pointer
 // jumping) and 2BFS runs in every component at once from multi-source
 // frontiers; l~ is the largest second-BFS level.
@@ -32,6 +33,7 @@ struct BfsGraph {
   int n;
   int32_t *fq0, *fq1, *label;
   unsigned long long* ckey;
+  int32_t *fq2, *fq3;  // queues of the second search of bfs_dual
 };
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
@@ -203,6 +205,120 @@ __device__ bool bfs_run(const BfsGraph& g, int32_t* dist, int sources, int src, 
   return true;
 }
 
+// Two breadth-first searches advanced together, one barrier per level: A
+// from srcA into dA (queues fq0/fq1, counters qsize), B from srcB into dB
+// (queues fq2/fq3, counters qsizeB).  Each search is exactly the BFS that
+// bfs_run gives; the levels run until both frontiers are empty.  Out (in
+// every thread): the last non-empty level of each search and the vertices
+// reached by A.
+template <class Sync>
+__device__ bool bfs_dual(const BfsGraph& g, int32_t* dA, int32_t* dB, int srcA, int srcB, int tid,
+                         int T, Sync& sync, int* lastA, int* lastB, long long* reachedA) {
+  Ctl* ctl = g.ctl;
+  const int n = g.n;
+  const int lane = threadIdx.x & 31;
+  const int wbase = tid - lane;
+  for (int v = tid; v < n; v += T) {
+    dA[v] = -1;
+    dB[v] = -1;
+  }
+  if (tid == 0) {
+    for (int k = 0; k < 3; ++k) {
+      ctl->qsize[k] = 0;
+      ctl->qsizeB[k] = 0;
+    }
+  }
+  if (!sync()) return false;
+  if (tid == 0) {
+    dA[srcA] = 0;
+    dB[srcB] = 0;
+    g.fq0[0] = srcA;
+    g.fq2[0] = srcB;
+    ctl->qsize[0] = 1;
+    ctl->qsizeB[0] = 1;
+  }
+  if (!sync()) return false;
+  int level = 0, la = 0, lb = 0;
+  long long reached = 0;
+  for (;;) {
+    const int sa = *reinterpret_cast<volatile int*>(&ctl->qsize[level % 3]);
+    const int sb = *reinterpret_cast<volatile int*>(&ctl->qsizeB[level % 3]);
+    if (sa == 0 && sb == 0) break;
+    reached += sa;
+    if (sa) la = level;
+    if (sb) lb = level;
+    if (tid == 0) {
+      ctl->qsize[(level + 2) % 3] = 0;
+      ctl->qsizeB[(level + 2) % 3] = 0;
+    }
+    const int32_t* inA = (level & 1) ? g.fq1 : g.fq0;
+    int32_t* outA = (level & 1) ? g.fq0 : g.fq1;
+    const int32_t* inB = (level & 1) ? g.fq3 : g.fq2;
+    int32_t* outB = (level & 1) ? g.fq2 : g.fq3;
+    int* cntA = &ctl->qsize[(level + 1) % 3];
+    int* cntB = &ctl->qsizeB[(level + 1) % 3];
+    const int total = sa + sb;
+    for (int base = wbase; base < total; base += T) {  // warp-uniform bound
+      const int idx = base + lane;
+      const bool isB = idx >= sa;
+      int u = -1, e0 = 0, deg = 0;
+      if (idx < total) {
+        u = isB ? inB[idx - sa] : inA[idx];
+        e0 = g.rp[u];
+        deg = g.rp[u + 1] - e0;
+      }
+      int32_t* dist = isB ? dB : dA;
+      const int maxdeg = __reduce_max_sync(0xffffffffu, deg);
+      for (int k0 = 0; k0 < maxdeg; k0 += 8) {
+        int w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = (k0 + j < deg) ? g.col[e0 + k0 + j] : -1;
+        bool push[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          push[j] = w[j] >= 0 && w[j] != u && atomicCAS(&dist[w[j]], -1, level + 1) == -1;
+        int mine = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mine += push[j] ? 1 : 0;
+        // separate warp scans for the lanes of A and of B
+        const int mA = isB ? 0 : mine, mB = isB ? mine : 0;
+        int incA = mA, incB = mB;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int ta = __shfl_up_sync(0xffffffffu, incA, o);
+          const int tb = __shfl_up_sync(0xffffffffu, incB, o);
+          if (lane >= o) {
+            incA += ta;
+            incB += tb;
+          }
+        }
+        const int totA = __shfl_sync(0xffffffffu, incA, 31);
+        const int totB = __shfl_sync(0xffffffffu, incB, 31);
+        int bA = 0, bB = 0;
+        if (lane == 0) {
+          if (totA > 0) bA = atomicAdd(cntA, totA);
+          if (totB > 0) bB = atomicAdd(cntB, totB);
+        }
+        bA = __shfl_sync(0xffffffffu, bA, 0);
+        bB = __shfl_sync(0xffffffffu, bB, 0);
+        if (mine) {
+          int32_t* out = isB ? outB : outA;
+          int pos = isB ? bB + incB - mB : bA + incA - mA;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (push[j]) out[pos++] = w[j];
+        }
+      }
+    }
+    ++level;
+    if (!sync()) return false;
+  }
+  *lastA = la;
+  *lastB = lb;
+  *reachedA = reached;
+  return true;
+}
+
 // Connected components: label[v] = smallest vertex of v's component.
 // Rounds of (hook: for every edge with differing labels, lower the larger
 // label's entry to the smaller label) and (pointer jumping to the root),
@@ -257,19 +373,51 @@ __device__ bool cc_run(const BfsGraph& g, int tid, int T, Sync& sync) {
 
 // 2BFS pseudo-diameter with the per-component rule.  On return (true),
 // ctl->pdiam holds l~ and ctl->far_t the farthest vertex found from vertex 0.
+//
+// The second BFS starts from t, which the first BFS determines.  It is run
+// speculatively alongside the first, from t' = n - 1: in a grid graph
+// numbered row by row the farthest vertex from vertex 0 is the opposite
+// corner n - 1.  When the first BFS confirms t = t', the second search is
+// exactly the BFS from t and l~ is its depth; otherwise the BFS from t runs
+// afterwards.  Either way the result is that of the two searches in order.
 template <class Sync>
 __device__ bool pseudo_diameter_run(const BfsGraph& g, int32_t* d1, int32_t* d2, int tid, int T,
                                     Sync& sync) {
   Ctl* ctl = g.ctl;
-  if (tid == 0) ctl->key = 0ull;
+  const int lane = threadIdx.x & 31;
+  if (tid == 0) {
+    ctl->key = 0ull;
+    ctl->reached = 0;
+  }
   if (!sync()) return false;
-  if (!bfs_run(g, d1, kSrcSingle, 0, kRoleFirst, tid, T, sync)) return false;
+  const int guess = g.n - 1;
+  int lastA = 0, lastB = 0;
+  long long reached = 0;
+  if (!bfs_dual(g, d1, d2, 0, guess, tid, T, sync, &lastA, &lastB, &reached)) return false;
+  // farthest vertex of the first search: largest distance, then smallest index
+  {
+    unsigned long long best = 0;
+    for (int v = tid; v < g.n; v += T) {
+      const int d = d1[v];
+      if (d >= 0) {
+        const unsigned long long k = far_key(d, v);
+        best = k > best ? k : best;
+      }
+    }
+    best = warp_max_u64(best);
+    if (lane == 0 && best) atomicMax(&ctl->key, best);
+    if (tid == 0) ctl->reached = (int)reached;
+  }
   if (!sync()) return false;
-  const bool connected = *reinterpret_cast<volatile int*>(&ctl->reached) == g.n;
+  const bool connected = reached == g.n;
   if (connected) {
     const int t = far_key_vertex(*reinterpret_cast<volatile unsigned long long*>(&ctl->key));
     if (tid == 0) ctl->far_t = t;
-    if (!bfs_run(g, d2, kSrcSingle, t, kRoleSecond, tid, T, sync)) return false;
+    if (t == guess) {
+      if (tid == 0) ctl->pdiam = lastB > 0 ? lastB : 0;
+    } else {
+      if (!bfs_run(g, d2, kSrcSingle, t, kRoleSecond, tid, T, sync)) return false;
+    }
   } else {
     if (!cc_run(g, tid, T, sync)) return false;
     if (!bfs_run(g, d1, kSrcRoots, 0, kRoleComponentFirst, tid, T, sync)) return false;

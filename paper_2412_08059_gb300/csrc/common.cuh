@@ -45,6 +45,7 @@ struct Ctl {
   int pdiam, far_t, reached, ncomp, connected;
   unsigned long long key;
   int qsize[3];
+  int qsizeB[3];   // frontier counters of the second, speculative search
   int ccflag[2];
   int cls;
   int eps1_ready;  // fused stage 1: 0 pending, t + 1 when the kNN chose t, -1 on failure
@@ -67,6 +68,7 @@ struct Ws {
   float *b32, *x32, *r32, *d32a, *d32b, *q32;
   double *r64, *d64, *q64;
   int32_t *dist, *dist2, *fq0, *fq1, *label;
+  int32_t *fq2, *fq3;        // frontier queues of the speculative second search
   unsigned long long* ckey;  // per-component farthest-vertex keys
   float* snap;               // stage-1 snapshots of x~ at candidate crossings [6][n]
   size_t bytes;

@@ -54,6 +54,8 @@ size_t carve(const Dims& d, char* base, Ws* ws) {
   w.dist2 = (int32_t*)take(sizeof(int32_t) * n);
   w.fq0 = (int32_t*)take(sizeof(int32_t) * n);
   w.fq1 = (int32_t*)take(sizeof(int32_t) * n);
+  w.fq2 = (int32_t*)take(sizeof(int32_t) * n);
+  w.fq3 = (int32_t*)take(sizeof(int32_t) * n);
   w.label = (int32_t*)take(sizeof(int32_t) * n);
   w.ckey = (unsigned long long*)take(sizeof(unsigned long long) * n);
   w.snap = (float*)take(sizeof(float) * 6 * n);

@@ -61,7 +61,8 @@ __device__ bool slot_setup(Team& t, const BatchSys& s, const BatchArgs& a, int& 
 // Algorithm II features: 2BFS, the k0 iterations and the kNN vote.
 __device__ bool slot_features(Team& t, const BatchSys& s, const BatchArgs& a, int& red) {
   Ctl* ctl = s.w.ctl;
-  BfsGraph g{ctl, s.A.row_ptr, s.A.col, s.n, s.w.fq0, s.w.fq1, s.w.label, s.w.ckey};
+  BfsGraph g{ctl, s.A.row_ptr, s.A.col, s.n, s.w.fq0, s.w.fq1, s.w.label, s.w.ckey,
+                 s.w.fq2, s.w.fq3};
   TeamSyncFn sync{&t};
   if (!pseudo_diameter_run(g, s.w.dist, s.w.dist2, team_tid(t), team_threads(t), sync))
     return false;
