@@ -604,15 +604,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
   }
   const double eps = a.mode == kCgK0 ? ctl->eps2 : ctl->eps1;
   const int limit = a.mode == kCgK0 ? min(ctl->k0, ctl->max1) : ctl->max1;
+  const StopThr thr = stop_thr(eps, bnorm, rel);  // used by thread 0
   double vsum = 0.0;  // thread 0
   int k0done = 0, broke = 0;
 
   while (ok) {
     if (lead) {
-      const double m = stop_measure(rr, bnorm, rel);
       int dec = kGo;
-      if (isnan(m)) dec = kNan;
-      else if (m <= eps || it >= limit || (a.mode == kCgK0 && rr == 0.0)) dec = kStop;
+      if (isnan(rr)) dec = kNan;
+      else if (stop_pass(thr, rr) || it >= limit || (a.mode == kCgK0 && rr == 0.0)) dec = kStop;
       S.dec = dec;
       if (dec == kNan && lead0) set_status(ctl, MPCG_ERR_NAN);
     }
@@ -805,7 +805,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
   bool ok = true;
   int it = 0, restarts = 0;
   int failed = 0;                  // thread 0
-  double m = 0.0, true_rel = NAN;  // thread 0
+  double true_rel = NAN;  // thread 0
+  const StopThr thr2 = stop_thr(eps2, bnorm, rel);  // used by thread 0
   double rr = 0.0;                 // thread 0
 
   // Promote: x0 = float64(x~) (or 0).
@@ -919,12 +920,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
     }
     if (next == -1) {  // loop head: stop test on the recursive residual
       if (lead) {
-        m = stop_measure(rr, bnorm, rel);
         int nk = kIterate;
-        if (isnan(m)) {
+        if (isnan(rr)) {
           failed = MPCG_ERR_NAN;
           nk = kDone;
-        } else if (m <= eps2) {
+        } else if (stop_pass(thr2, rr)) {
           nk = kTrueRes;
         } else if (it >= max2) {
           failed = MPCG_ERR_NOT_CONVERGED;
@@ -944,7 +944,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
     ctl->n2 = it;
     ctl->restarts = restarts;
     if (restarts) ctl->warn_restart = 1;
-    ctl->res64 = m;
+    ctl->res64 = stop_measure(rr, bnorm, rel);
     ctl->true_rel = true_rel;
     ctl->rr = rr;
     ctl->t_fp64 = globaltimer();
@@ -1140,7 +1140,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
   float beta = 0.0f;
   int parity = 0, first = 1, it = 0;
   // thread 0 only:
-  double vsum = 0.0, m = 0.0;
+  double vsum = 0.0;
   int k0done = 0, in_k0 = 1, cls = -1, nslots = 0;
   int nt[16], snap_it[kSnapSlots];
   double res_at[16];
@@ -1150,16 +1150,26 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
   }
   enum { kGoOn = 0, kEnd = 1, kFailed = 2, kBrokeDown = 3 };
   int broke = 0;
+  // thread 0: stop thresholds of eps2 (slot 16) and of every candidate
+  // eps1 = 10^-t (slots 0..15), kept in shared memory
+  __shared__ double s_lo[17], s_hi[17];
+  if (lead) {
+    for (int t = 0; t <= 16; ++t) {
+      const StopThr c = stop_thr(t < 16 ? pow10_neg(t) : eps2, bnorm, rel);
+      s_lo[t] = c.lo;
+      s_hi[t] = c.hi;
+    }
+  }
 
   while (ok) {
     if (lead) {
-      m = stop_measure(rr, bnorm, rel);
       int dec = kGoOn, snap_slot = -1;
-      if (isnan(m)) {
+      if (isnan(rr)) {
         dec = kFailed;
         if (lead0) set_status(ctl, MPCG_ERR_NAN);
       } else {
-        if (in_k0 && (it >= min(k0, max1) || m <= eps2 || rr == 0.0)) {
+        if (in_k0 && (it >= min(k0, max1) || rr == 0.0 || rr <= s_lo[16] ||
+                      (rr <= s_hi[16] && stop_measure(rr, bnorm, rel) <= eps2))) {
           in_k0 = 0;  // end of the k0 phase: v of Eq. (13) for the kNN
           if (lead0) {
             ctl->k0_done = k0done;
@@ -1174,9 +1184,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
           bool fresh = false, all = true;
           for (int t = 0; t < 16; ++t) {
             if (!((cmask >> t) & 1u)) continue;
-            if (nt[t] < 0 && m <= pow10_neg(t)) {
+            if (nt[t] < 0 &&
+                (rr <= s_lo[t] ||
+                 (rr <= s_hi[t] && stop_measure(rr, bnorm, rel) <= pow10_neg(t)))) {
               nt[t] = it;
-              res_at[t] = m;
+              res_at[t] = stop_measure(rr, bnorm, rel);
               fresh = true;
             }
             if (nt[t] < 0) all = false;
@@ -1313,7 +1325,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
       // its iterate; otherwise (iteration cap, breakdown) at the current one.
       const double eps1 = pow10_neg(cls);
       int n1 = it, src = -1;
-      double res = m;
+      double res = stop_measure(rr, bnorm, rel);
       if (!in_k0 && nt[cls] >= 0 && nt[cls] < it) {
         n1 = nt[cls];
         res = res_at[cls];

@@ -100,6 +100,33 @@ __device__ __forceinline__ double stop_measure(double rr, double bnorm, int rel)
   return rel ? sqrt(rr) / bnorm : sqrt(rr);
 }
 
+// The stop test stop_measure(rr) <= eps without a square root and a division
+// per iteration.  stop_measure is non-decreasing in rr, so the test passes
+// exactly for rr up to some threshold near t = (eps ||b||)^2 (or eps^2).
+// rr <= lo passes and rr > hi fails for certain (the band of 1e-12 relative
+// covers the rounding of t and of the exact test); in the band the exact
+// test decides.  Where t is not a normal number the exact test always
+// decides.  The outcome is that of the exact test for every rr.
+struct StopThr {
+  double lo, hi, eps, bnorm;
+  int rel;
+};
+__device__ __forceinline__ StopThr stop_thr(double eps, double bnorm, int rel) {
+  const double s = rel ? eps * bnorm : eps;
+  const double t = s * s;
+  StopThr T{-1.0, INFINITY, eps, bnorm, rel};
+  if (t >= 1e-290 && t <= 1e290) {
+    T.lo = t * (1.0 - 1e-12);
+    T.hi = t * (1.0 + 1e-12);
+  }
+  return T;
+}
+__device__ __forceinline__ bool stop_pass(const StopThr& T, double rr) {
+  if (rr <= T.lo) return true;
+  if (rr > T.hi) return false;
+  return stop_measure(rr, T.bnorm, T.rel) <= T.eps;
+}
+
 __device__ __forceinline__ int volatile_status(const Ctl* c) {
   return *reinterpret_cast<const volatile int*>(&c->status);
 }

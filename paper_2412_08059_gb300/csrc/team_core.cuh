@@ -491,14 +491,14 @@ static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, 
   const double eps = mode == kCgK0 ? ctl->eps2 : ctl->eps1;
   const int limit = mode == kCgK0 ? min(ctl->k0, ctl->max1) : ctl->max1;
   const int it_start = it;
+  const StopThr thr = stop_thr(eps, bnorm, rel);  // used by thread 0
   double vsum = 0.0;  // thread 0
   int k0done = 0, broke = 0, suspended = 0;
   while (true) {
     int dec = kBGo;
     if (lead) {
-      const double m = stop_measure(rr, bnorm, rel);
-      if (isnan(m)) dec = kBNan;
-      else if (m <= eps || it >= limit || (mode == kCgK0 && rr == 0.0)) dec = kBStop;
+      if (isnan(rr)) dec = kBNan;
+      else if (stop_pass(thr, rr) || it >= limit || (mode == kCgK0 && rr == 0.0)) dec = kBStop;
       else if (mode != kCgK0 && it - it_start >= budget) dec = kBSuspend;
     }
     dec = bcast_dec(t, dec);
@@ -630,7 +630,8 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
   }
   int it = resume ? ctl->n2 : 0, restarts = resume ? ctl->restarts : 0, failed = 0;
   const int it_start = it;
-  double rr = resume ? ctl->rr : 0.0, m = 0.0, true_rel = NAN;
+  double rr = resume ? ctl->rr : 0.0, true_rel = NAN;
+  const StopThr thr2 = stop_thr(eps2, bnorm, rel);  // used by thread 0
   bool skip_restart = resume;
   for (;;) {
     // restart (CG line 1 from x): r = b - A x, d = r, r^T r
@@ -653,9 +654,8 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
     for (;;) {
       int dec = kBGo;
       if (lead) {
-        m = stop_measure(rr, bnorm, rel);
-        if (isnan(m)) dec = kBNan;
-        else if (m <= eps2) dec = kBStop;
+        if (isnan(rr)) dec = kBNan;
+        else if (stop_pass(thr2, rr)) dec = kBStop;
         else if (it >= max2) dec = kBCap;
         else if (it - it_start >= budget) dec = kBSuspend;
       }
@@ -766,7 +766,7 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
     ctl->n2 = it;
     ctl->restarts = restarts;
     if (restarts) ctl->warn_restart = 1;
-    ctl->res64 = m;
+    ctl->res64 = stop_measure(rr, bnorm, rel);
     ctl->true_rel = true_rel;
     ctl->rr = rr;
     ctl->t_fp64 = globaltimer();
