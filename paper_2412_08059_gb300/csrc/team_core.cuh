@@ -367,10 +367,11 @@ __device__ __forceinline__ int team_warps(const Team& t);
 // SpMV over the team's slices: warp gw owns slices gw, gw + W, ...; lane l
 // owns row 32 s + l.  Rw(i, acc) receives row i's sum in stored order (fused
 // multiply-adds from zero, padding rows included).  The metadata of 32 of
-// the warp's slices is loaded at once (one slice per lane) and two slices
-// are summed together so that their loads and gathers overlap.
+// the warp's slices is loaded at once (one slice per lane) and kU slices are
+// summed together so that their loads and gathers overlap.
 template <typename T, class Gather, class Row>
 __device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gather G, Row Rw) {
+  constexpr int kU = 4;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int gw = team_warp(t), W = team_warps(t);
@@ -385,29 +386,33 @@ __device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gath
       mp = s.w.slice_ptr[mine];
     }
     const int cnt = min(32, (s.nslices - base + W - 1) / W);
-    for (int j = 0; j < cnt; j += 2) {
-      const int j1 = min(j + 1, 31);
-      const bool h1 = j + 1 < cnt;
-      const uint32_t wf0 = __shfl_sync(full, mwf, j);
-      const uint32_t wf1 = __shfl_sync(full, mwf, j1);
-      const int p0 = __shfl_sync(full, mp, j) + lane;
-      const int p1 = __shfl_sync(full, mp, j1) + lane;
-      const int w0 = (int)(wf0 & ~kOverflowBit);
-      const int w1 = h1 ? (int)(wf1 & ~kOverflowBit) : 0;
-      const int i0 = (base + j * W) * kSlice + lane;
-      const int i1 = (base + (j + 1) * W) * kSlice + lane;
-      T a0 = (T)0, a1 = (T)0;
-      const int wm = max(w0, w1);
-#pragma unroll 4
-      for (int k = 0; k < wm; ++k) {
-        if (k < w0) a0 = fma(sv[p0 + kSlice * k], G(sc[p0 + kSlice * k]), a0);
-        if (k < w1) a1 = fma(sv[p1 + kSlice * k], G(sc[p1 + kSlice * k]), a1);
+    for (int j = 0; j < cnt; j += kU) {
+      int w[kU], p[kU], i[kU];
+      uint32_t wf[kU];
+      T a[kU];
+      int wm = 0;
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int ju = min(j + u, 31);
+        wf[u] = __shfl_sync(full, mwf, ju);
+        p[u] = __shfl_sync(full, mp, ju) + lane;
+        w[u] = j + u < cnt ? (int)(wf[u] & ~kOverflowBit) : 0;
+        i[u] = (base + (j + u) * W) * kSlice + lane;
+        a[u] = (T)0;
+        wm = max(wm, w[u]);
       }
-      if ((wf0 & kOverflowBit) && i0 < s.n) a0 = btail<T>(s, i0, w0, a0, G);
-      Rw(i0, a0);
-      if (h1) {
-        if ((wf1 & kOverflowBit) && i1 < s.n) a1 = btail<T>(s, i1, w1, a1, G);
-        Rw(i1, a1);
+#pragma unroll 2
+      for (int k = 0; k < wm; ++k) {
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+          if (k < w[u]) a[u] = fma(sv[p[u] + kSlice * k], G(sc[p[u] + kSlice * k]), a[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        if (j + u < cnt) {
+          if ((wf[u] & kOverflowBit) && i[u] < s.n) a[u] = btail<T>(s, i[u], w[u], a[u], G);
+          Rw(i[u], a[u]);
+        }
       }
     }
   }
