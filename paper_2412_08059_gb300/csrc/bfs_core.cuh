@@ -258,30 +258,53 @@ __device__ bool bfs_dual(const BfsGraph& g, int32_t* dA, int32_t* dB, int srcA, 
     int* cntA = &ctl->qsize[(level + 1) % 3];
     int* cntB = &ctl->qsizeB[(level + 1) % 3];
     const int total = sa + sb;
-    for (int base = wbase; base < total; base += T) {  // warp-uniform bound
-      const int idx = base + lane;
-      const bool isB = idx >= sa;
-      int u = -1, e0 = 0, deg = 0;
-      if (idx < total) {
-        u = isB ? inB[idx - sa] : inA[idx];
-        e0 = g.rp[u];
-        deg = g.rp[u + 1] - e0;
+    // Each lane takes two frontier vertices per round (items base + lane and
+    // base + T + lane), so that their loads and claims are in flight together.
+    for (int base = wbase; base < total; base += 2 * T) {  // warp-uniform bound
+      int u[2], e0[2], deg[2];
+      bool isB[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int idx = base + h * T + lane;
+        isB[h] = idx >= sa;
+        u[h] = -1;
+        if (idx < total) u[h] = isB[h] ? inB[idx - sa] : inA[idx];
       }
-      int32_t* dist = isB ? dB : dA;
-      const int maxdeg = __reduce_max_sync(0xffffffffu, deg);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        e0[h] = 0;
+        deg[h] = 0;
+        if (u[h] >= 0) {
+          e0[h] = g.rp[u[h]];
+          deg[h] = g.rp[u[h] + 1] - e0[h];
+        }
+      }
+      const int maxdeg = __reduce_max_sync(0xffffffffu, max(deg[0], deg[1]));
       for (int k0 = 0; k0 < maxdeg; k0 += 8) {
-        int w[8];
+        int w[2][8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) w[j] = (k0 + j < deg) ? g.col[e0 + k0 + j] : -1;
-        bool push[8];
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          push[j] = w[j] >= 0 && w[j] != u && atomicCAS(&dist[w[j]], -1, level + 1) == -1;
-        int mine = 0;
+          for (int j = 0; j < 8; ++j) w[h][j] = (k0 + j < deg[h]) ? g.col[e0[h] + k0 + j] : -1;
+        bool push[2][8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) mine += push[j] ? 1 : 0;
-        // separate warp scans for the lanes of A and of B
-        const int mA = isB ? 0 : mine, mB = isB ? mine : 0;
+        for (int h = 0; h < 2; ++h) {
+          int32_t* dist = isB[h] ? dB : dA;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            push[h][j] =
+                w[h][j] >= 0 && w[h][j] != u[h] && atomicCAS(&dist[w[h][j]], -1, level + 1) == -1;
+        }
+        int mA = 0, mB = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int mine = 0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) mine += push[h][j] ? 1 : 0;
+          if (isB[h]) mB += mine;
+          else mA += mine;
+        }
+        // separate warp scans for the pushes into A's and into B's queue
         int incA = mA, incB = mB;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -301,12 +324,16 @@ __device__ bool bfs_dual(const BfsGraph& g, int32_t* dA, int32_t* dB, int srcA, 
         }
         bA = __shfl_sync(0xffffffffu, bA, 0);
         bB = __shfl_sync(0xffffffffu, bB, 0);
-        if (mine) {
-          int32_t* out = isB ? outB : outA;
-          int pos = isB ? bB + incB - mB : bA + incA - mA;
+        int posA = bA + incA - mA, posB = bB + incB - mB;
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (push[j]) out[pos++] = w[j];
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (push[h][j]) {
+              if (isB[h]) outB[posB++] = w[h][j];
+              else outA[posA++] = w[h][j];
+            }
+          }
         }
       }
     }

@@ -1268,12 +1268,16 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
     const float alpha = S.alpha;
 
     // ---- P2: x += alpha d_k, r -= alpha q, r^T r; the label rides along ----
+    // Block 0 reads the label flag before its updates, so that the read's
+    // latency overlaps them; once the label is known it is no longer read.
+    int label_now = 0;
+    if (lead0) label_now = cls >= 0 ? cls + 1 : *reinterpret_cast<volatile int*>(&ctl->eps1_ready);
     FF prr{0.f, 0.f};
     p2_32(a, R0, R1, lane, dnew, alpha, prr);
     {
       double* buf = a.partials + (red & 1) * kMaxGrid;
       const double bp = block_ff(prr, S);
-      if (lead0) buf[gridDim.x] = (double)*reinterpret_cast<volatile int*>(&ctl->eps1_ready);
+      if (lead0) buf[gridDim.x] = (double)label_now;
       const double rrn = cgrid_total(bp, a.partials, red, ctl, a.slot, round, S, ok);
       if (lead) {
         const int label = (int)buf[gridDim.x];
