@@ -74,6 +74,22 @@ def workload_config(size):
                 (12 * nnz + 4 * (n + 1)) / 1e6)}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of x over all ranks (x itself on one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    tt = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(world: int, steps: int, systems_per_step: int, seconds: float) -> float:
+    """Solves per second of the whole job: every rank solves its own replica of
+    the step's systems (weak scaling), timed by the slowest rank."""
+    return world * steps * systems_per_step / seconds
+
+
 def algorithmic_bytes(n, nnz, p):
     """Per CG iteration: the matrix once, row offsets, x, r, d read and written once."""
     return nnz * (p + 4) + 4 * (n + 1) + 6 * p * n
@@ -530,10 +546,7 @@ def native_arm(args, rank, world, local_rank):
         barrier()
         ms = e0.elapsed_time(e1)
         clk = ck.stop() if ck else None
-        if world > 1:
-            tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(ms, world, dev)
         return ms, mpcg.read_results(res, nsys), clk
 
     ms_auto, r_auto, clocks = timed(o_auto, args.steps, args.warmup, clocks=True)
@@ -541,8 +554,8 @@ def native_arm(args, rank, world, local_rank):
     for r in r_auto + r_fp64:
         if r["status"] < 0:
             raise RuntimeError(f"solve failed: {r}")
-    value = world * args.steps * nsys / (ms_auto / 1000.0)
-    value_fp64 = world * args.steps * nsys / (ms_fp64 / 1000.0)
+    value = whole_job_rate(world, args.steps, nsys, ms_auto / 1000.0)
+    value_fp64 = whole_job_rate(world, args.steps, nsys, ms_fp64 / 1000.0)
 
     # ---- per system: time to solution, equivalent FP64 iterations, E (Eqs. 4, 12) ----
     B32 = algorithmic_bytes(n, nnz, 4)
@@ -698,11 +711,8 @@ def native_arm(args, rank, world, local_rank):
         torch.cuda.synchronize()
         barrier()
         wall = time.perf_counter() - t
-        if world > 1:
-            tt = torch.tensor([wall], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            wall = float(tt.item())
-        e2e = {"value": world * args.steps * nsys / wall, "unit": UNIT,
+        wall = max_over_ranks(wall, world, dev)
+        e2e = {"value": whole_job_rate(world, args.steps, nsys, wall), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "timing": "host wall clock around K steps incl. pinned H2D of CSR+b and D2H of x+result"}
 
