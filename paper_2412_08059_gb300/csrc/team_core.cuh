@@ -365,12 +365,14 @@ __device__ __forceinline__ int team_warp(const Team& t);
 __device__ __forceinline__ int team_warps(const Team& t);
 
 // SpMV over the team's slices: warp gw owns slices gw, gw + W, ...; lane l
-// owns row 32 s + l.  Rw(i, acc) receives row i's sum in stored order (fused
-// multiply-adds from zero, padding rows included).  The metadata of 32 of
+// owns row 32 s + l.  Rw(i, acc, own) receives row i's sum in stored order
+// (fused multiply-adds from zero, padding rows included) and the row's own
+// values that P(i) loaded before the gathers (P gets i >= n for absent rows).  The metadata of 32 of
 // the warp's slices is loaded at once (one slice per lane) and kU slices are
 // summed together so that their loads and gathers overlap.
-template <typename T, class Gather, class Row>
-__device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gather G, Row Rw) {
+template <typename T, class Gather, class Pre, class Row>
+__device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gather G, Pre P,
+                                          Row Rw) {
   constexpr int kU = 4;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -401,6 +403,11 @@ __device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gath
         a[u] = (T)0;
         wm = max(wm, w[u]);
       }
+      // the rows' own values, loaded before the gathers (the row callbacks
+      // store, and later loads could not be moved above those stores)
+      decltype(P(0)) own[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) own[u] = P(j + u < cnt ? i[u] : s.n);
 #pragma unroll 2
       for (int k = 0; k < wm; ++k) {
 #pragma unroll
@@ -411,7 +418,7 @@ __device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gath
       for (int u = 0; u < kU; ++u) {
         if (j + u < cnt) {
           if ((wf[u] & kOverflowBit) && i[u] < s.n) a[u] = btail<T>(s, i[u], w[u], a[u], G);
-          Rw(i[u], a[u]);
+          Rw(i[u], a[u], own[u]);
         }
       }
     }
@@ -420,6 +427,29 @@ __device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gath
 
 __device__ __forceinline__ int team_warp(const Team& t) { return t.rank * kBatchWarps + (threadIdx.x >> 5); }
 __device__ __forceinline__ int team_warps(const Team& t) { return t.size * kBatchWarps; }
+
+// Row phases over the team's rows, kR slices per step: Ld(i) loads a row's
+// operands, then Op(i, v) computes and stores.  All the step's loads are
+// issued before any of its stores (the stores may alias the arrays the next
+// loads read, so the compiler could not reorder them itself).
+template <class Ld, class Op>
+__device__ __forceinline__ void team_rows(const Team& t, const BatchSys& s, Ld L, Op O) {
+  const int lane = threadIdx.x & 31;
+  const int gw = team_warp(t), W = team_warps(t);
+  constexpr int kR = 4;
+  for (int sl = gw; sl < s.nslices; sl += kR * W) {
+    int i[kR];
+    decltype(L(0)) v[kR];
+#pragma unroll
+    for (int u = 0; u < kR; ++u) {
+      i[u] = (sl + u * W) * kSlice + lane;
+      v[u] = (sl + u * W < s.nslices && i[u] < s.n) ? L(i[u]) : decltype(L(0)){};
+    }
+#pragma unroll
+    for (int u = 0; u < kR; ++u)
+      if (sl + u * W < s.nslices && i[u] < s.n) O(i[u], v[u]);
+  }
+}
 
 // Broadcast of thread 0's decision (and scalars) to the block.
 __device__ __forceinline__ int bcast_dec(Team& t, int dec) {
@@ -522,9 +552,10 @@ static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, 
     FF pdq{0.f, 0.f};
     team_spmv<float>(
         t, s, [&](int c) -> float { return __fmaf_rn(bt, dold[c], r[c]); },
-        [&](int i, float acc) {
+        [&](int i) -> float2 { return i < n ? make_float2(dold[i], r[i]) : make_float2(0.f, 0.f); },
+        [&](int i, float acc, float2 own) {
           if (i < n) {
-            const float di = __fmaf_rn(bt, dold[i], r[i]);
+            const float di = __fmaf_rn(bt, own.x, own.y);
             dnew[i] = di;
             q[i] = acc;
             ff_add_prod(pdq, di, acc);
@@ -550,15 +581,14 @@ static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, 
     const float alpha = t.S->fval[0];
     // P2: x += alpha d_k, r -= alpha q, r^T r
     FF prr{0.f, 0.f};
-    for (int sl = gw; sl < s.nslices; sl += W) {
-      const int i = sl * kSlice + lane;
-      if (i < n) {
-        x[i] = __fmaf_rn(alpha, dnew[i], x[i]);
-        const float ri = __fmaf_rn(-alpha, q[i], r[i]);
-        r[i] = ri;
-        ff_add_prod(prr, ri, ri);
-      }
-    }
+    team_rows(
+        t, s, [&](int i) -> float4 { return make_float4(dnew[i], x[i], q[i], r[i]); },
+        [&](int i, float4 v) {
+          x[i] = __fmaf_rn(alpha, v.x, v.y);
+          const float ri = __fmaf_rn(-alpha, v.z, v.w);
+          r[i] = ri;
+          ff_add_prod(prr, ri, ri);
+        });
     double rrn;
     if (!team_sum_ff(t, prr, s.w.partials, red, rrn)) return false;
     dec = kBGo;
@@ -644,9 +674,10 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
     double p = 0.0;
     team_spmv<double>(
         t, s, [&](int c) -> double { return x[c]; },
-        [&](int i, double acc) {
+        [&](int i) -> double { return i < n ? b[i] : 0.0; },
+        [&](int i, double acc, double bi) {
           if (i < n) {
-            const double ri = b[i] - acc;
+            const double ri = bi - acc;
             r[i] = ri;
             d[i] = ri;
             p = __fma_rn(ri, ri, p);
@@ -690,10 +721,11 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
       double pq = 0.0;
       team_spmv<double>(
           t, s, [&](int c) -> double { return d[c]; },
-          [&](int i, double acc) {
+          [&](int i) -> double { return i < n ? d[i] : 0.0; },
+          [&](int i, double acc, double di) {
             if (i < n) {
               q[i] = acc;
-              pq = __fma_rn(d[i], acc, pq);
+              pq = __fma_rn(di, acc, pq);
             }
           });
       double dq;
@@ -712,15 +744,14 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
       const double alpha = t.S->val[2];
       // P2: x += alpha d, r -= alpha q, r^T r
       double pr = 0.0;
-      for (int sl = gw; sl < s.nslices; sl += W) {
-        const int i = sl * kSlice + lane;
-        if (i < n) {
-          x[i] = __fma_rn(alpha, d[i], x[i]);
-          const double ri = __fma_rn(-alpha, q[i], r[i]);
-          r[i] = ri;
-          pr = __fma_rn(ri, ri, pr);
-        }
-      }
+      team_rows(
+          t, s, [&](int i) -> double4 { return make_double4(d[i], x[i], q[i], r[i]); },
+          [&](int i, double4 v) {
+            x[i] = __fma_rn(alpha, v.x, v.y);
+            const double ri = __fma_rn(-alpha, v.z, v.w);
+            r[i] = ri;
+            pr = __fma_rn(ri, ri, pr);
+          });
       double rrn;
       if (!team_sum_d(t, pr, s.w.partials, red, rrn)) return false;
       dec = kBGo;
@@ -736,10 +767,9 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
       const double beta = t.S->val[3];
       rr = rrn;
       // P3: d = r + beta d
-      for (int sl = gw; sl < s.nslices; sl += W) {
-        const int i = sl * kSlice + lane;
-        if (i < n) d[i] = __fma_rn(beta, d[i], r[i]);
-      }
+      team_rows(
+          t, s, [&](int i) -> double2 { return make_double2(d[i], r[i]); },
+          [&](int i, double2 v) { d[i] = __fma_rn(beta, v.x, v.y); });
       if (!team_sync(t)) return false;
       ++it;
     }
@@ -748,9 +778,10 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
     double pt = 0.0;
     team_spmv<double>(
         t, s, [&](int c) -> double { return x[c]; },
-        [&](int i, double acc) {
+        [&](int i) -> double { return i < n ? b[i] : 0.0; },
+        [&](int i, double acc, double bi) {
           if (i < n) {
-            const double ri = b[i] - acc;
+            const double ri = bi - acc;
             pt = __fma_rn(ri, ri, pt);
           }
         });
