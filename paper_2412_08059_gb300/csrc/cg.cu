@@ -481,10 +481,9 @@ __device__ __forceinline__ void warp_rows(int S0, int S1, int n, int& R0, int& R
 
 // x += alpha d, r -= alpha q, r^T r over rows [R0, R1): four rows per lane,
 // two groups of four in flight.
-__device__ __forceinline__ void upd32(const CgArgs& a, int i, float4 d4, float4 q4, float alpha,
-                                      FF& prr) {
-  float4 x4 = *reinterpret_cast<const float4*>(a.x32 + i);
-  float4 r4 = *reinterpret_cast<const float4*>(a.r32 + i);
+// x += alpha d, r -= alpha q, r^T r for four rows whose operands are loaded.
+__device__ __forceinline__ void upd32(const CgArgs& a, int i, float4 d4, float4 q4, float4 x4,
+                                      float4 r4, float alpha, FF& prr) {
   x4.x = __fmaf_rn(alpha, d4.x, x4.x);
   x4.y = __fmaf_rn(alpha, d4.y, x4.y);
   x4.z = __fmaf_rn(alpha, d4.z, x4.z);
@@ -501,22 +500,26 @@ __device__ __forceinline__ void upd32(const CgArgs& a, int i, float4 d4, float4 
   ff_add_prod(prr, r4.w, r4.w);
 }
 
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// Rows [R0, R1): four rows per lane, two groups of four; every operand of
+// both groups is loaded before the first store (stores to x and r could
+// alias later loads, so the compiler would not reorder them).
 __device__ __forceinline__ void p2_32(const CgArgs& a, int R0, int R1, int lane, const float* d,
                                       float alpha, FF& prr) {
   for (int base = R0 + 4 * lane; base < R1; base += 8 * kSlice) {
     const int b2 = base + 4 * kSlice;
     if (b2 + 4 <= R1) {
-      const float4 d4 = *reinterpret_cast<const float4*>(d + base);
-      const float4 q4 = *reinterpret_cast<const float4*>(a.q32 + base);
-      const float4 e4 = *reinterpret_cast<const float4*>(d + b2);
-      const float4 s4 = *reinterpret_cast<const float4*>(a.q32 + b2);
-      upd32(a, base, d4, q4, alpha, prr);
-      upd32(a, b2, e4, s4, alpha, prr);
+      const float4 d4 = ld4(d + base), q4 = ld4(a.q32 + base);
+      const float4 x4 = ld4(a.x32 + base), r4 = ld4(a.r32 + base);
+      const float4 e4 = ld4(d + b2), s4 = ld4(a.q32 + b2);
+      const float4 y4 = ld4(a.x32 + b2), t4 = ld4(a.r32 + b2);
+      upd32(a, base, d4, q4, x4, r4, alpha, prr);
+      upd32(a, b2, e4, s4, y4, t4, alpha, prr);
     } else {
       for (int g = base; g < R1 && g <= b2; g += 4 * kSlice) {
         if (g + 4 <= R1) {
-          upd32(a, g, *reinterpret_cast<const float4*>(d + g),
-                *reinterpret_cast<const float4*>(a.q32 + g), alpha, prr);
+          upd32(a, g, ld4(d + g), ld4(a.q32 + g), ld4(a.x32 + g), ld4(a.r32 + g), alpha, prr);
         } else {
           for (int i = g; i < R1; ++i) {
             a.x32[i] = __fmaf_rn(alpha, d[i], a.x32[i]);
@@ -713,19 +716,46 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
 // Double-precision stage (restart of Algorithm I/II, or pure FP64 CG).
 // ---------------------------------------------------------------------------------------
 
+__device__ __forceinline__ double2 ld2(const double* p) {
+  return *reinterpret_cast<const double2*>(p);
+}
+
 // x += alpha d, r -= alpha q over rows [R0, R1): two rows per lane, two
-// pairs in flight; returns this thread's part of r^T r.
+// pairs per step with every operand loaded before the first store; returns
+// this thread's part of r^T r.
 __device__ __forceinline__ double p2_64(const CgArgs& a, int R0, int R1, int lane, double alpha) {
   double prr = 0.0;
   for (int base = R0 + 2 * lane; base < R1; base += 4 * kSlice) {
+    const int g1 = base + 2 * kSlice;
+    if (g1 + 2 <= R1) {
+      const double2 d0 = ld2(a.d64 + base), q0 = ld2(a.q64 + base);
+      const double2 d1 = ld2(a.d64 + g1), q1 = ld2(a.q64 + g1);
+      double2 x0 = ld2(a.x64 + base), r0 = ld2(a.r64 + base);
+      double2 x1 = ld2(a.x64 + g1), r1 = ld2(a.r64 + g1);
+      x0.x = __fma_rn(alpha, d0.x, x0.x);
+      x0.y = __fma_rn(alpha, d0.y, x0.y);
+      r0.x = __fma_rn(-alpha, q0.x, r0.x);
+      r0.y = __fma_rn(-alpha, q0.y, r0.y);
+      x1.x = __fma_rn(alpha, d1.x, x1.x);
+      x1.y = __fma_rn(alpha, d1.y, x1.y);
+      r1.x = __fma_rn(-alpha, q1.x, r1.x);
+      r1.y = __fma_rn(-alpha, q1.y, r1.y);
+      *reinterpret_cast<double2*>(a.x64 + base) = x0;
+      *reinterpret_cast<double2*>(a.r64 + base) = r0;
+      *reinterpret_cast<double2*>(a.x64 + g1) = x1;
+      *reinterpret_cast<double2*>(a.r64 + g1) = r1;
+      prr = __fma_rn(r0.x, r0.x, prr);
+      prr = __fma_rn(r0.y, r0.y, prr);
+      prr = __fma_rn(r1.x, r1.x, prr);
+      prr = __fma_rn(r1.y, r1.y, prr);
+      continue;
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int g = base + h * 2 * kSlice;
       if (g + 2 <= R1) {
-        const double2 d2 = *reinterpret_cast<const double2*>(a.d64 + g);
-        const double2 q2 = *reinterpret_cast<const double2*>(a.q64 + g);
-        double2 x2 = *reinterpret_cast<const double2*>(a.x64 + g);
-        double2 r2 = *reinterpret_cast<const double2*>(a.r64 + g);
+        const double2 d2 = ld2(a.d64 + g), q2 = ld2(a.q64 + g);
+        double2 x2 = ld2(a.x64 + g), r2 = ld2(a.r64 + g);
         x2.x = __fma_rn(alpha, d2.x, x2.x);
         x2.y = __fma_rn(alpha, d2.y, x2.y);
         r2.x = __fma_rn(-alpha, q2.x, r2.x);
@@ -745,15 +775,27 @@ __device__ __forceinline__ double p2_64(const CgArgs& a, int R0, int R1, int lan
   return prr;
 }
 
-// d = r + beta d over rows [R0, R1).
+// d = r + beta d over rows [R0, R1), both pairs of a step loaded first.
 __device__ __forceinline__ void p3_64(const CgArgs& a, int R0, int R1, int lane, double beta) {
   for (int base = R0 + 2 * lane; base < R1; base += 4 * kSlice) {
+    const int g1 = base + 2 * kSlice;
+    if (g1 + 2 <= R1) {
+      double2 d0 = ld2(a.d64 + base), d1 = ld2(a.d64 + g1);
+      const double2 r0 = ld2(a.r64 + base), r1 = ld2(a.r64 + g1);
+      d0.x = __fma_rn(beta, d0.x, r0.x);
+      d0.y = __fma_rn(beta, d0.y, r0.y);
+      d1.x = __fma_rn(beta, d1.x, r1.x);
+      d1.y = __fma_rn(beta, d1.y, r1.y);
+      *reinterpret_cast<double2*>(a.d64 + base) = d0;
+      *reinterpret_cast<double2*>(a.d64 + g1) = d1;
+      continue;
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int g = base + h * 2 * kSlice;
       if (g + 2 <= R1) {
-        double2 d2 = *reinterpret_cast<const double2*>(a.d64 + g);
-        const double2 r2 = *reinterpret_cast<const double2*>(a.r64 + g);
+        double2 d2 = ld2(a.d64 + g);
+        const double2 r2 = ld2(a.r64 + g);
         d2.x = __fma_rn(beta, d2.x, r2.x);
         d2.y = __fma_rn(beta, d2.y, r2.y);
         *reinterpret_cast<double2*>(a.d64 + g) = d2;
