@@ -165,7 +165,11 @@ int32_t mpcg_choose_eps1(const mpcg_features_t* f, const mpcg_sample_t* sample,
 /* The method (Algorithm II, or Algorithm I when opts->eps1 > 0, or pure FP64
  * CG when opts->fp64_only): x (device, float64[n]) receives the solution;
  * its input value is ignored (x0 = 0).  sample: required by Algorithm II,
- * ignored otherwise.  res: device-writable result record. */
+ * ignored otherwise.  res: device-writable result record.  In Algorithm II
+ * the 2BFS and the kNN run alongside the single-precision iterations, which
+ * keep going past k0 and keep the iterate at every candidate eps1; N1 and x~
+ * are those of the paper's sequential order (k0 iterations, features, kNN,
+ * CG from iterate k0 to eps1). */
 int32_t mpcg_solve(const mpcg_csr_t* A, const double* b, double* x, const mpcg_sample_t* sample,
                    const mpcg_options_t* opts, void* ws, size_t ws_bytes, mpcg_result_t* res,
                    mpcg_stream_t stream);
@@ -176,8 +180,9 @@ int32_t mpcg_solve(const mpcg_csr_t* A, const double* b, double* x, const mpcg_s
  * pointers; res: device array of nsys records.  Every system gets its own
  * features, eps1 (Algorithm II when opts->eps1 <= 0, with `sample`) and
  * result record, with the same options (fp64_only: pure FP64 CG for every
- * system); stage1_only is not supported here (MPCG_ERR_UNIMPLEMENTED).  The grid is split into teams of
- * 1..128 blocks; each team takes systems from size-class queues (largest
+ * system; stage1_only is refused with MPCG_ERR_UNIMPLEMENTED).  The grid is
+ * split into teams of 1..128 blocks; each team takes systems from size-class
+ * queues (largest
  * first) and runs the whole method on each, so systems of uneven size run
  * concurrently.  Workspace: mpcg_batch_workspace_bytes (a descriptor table,
  * then one region per system).  The descriptor table is copied from host

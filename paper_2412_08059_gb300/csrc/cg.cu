@@ -32,6 +32,11 @@
 // Double-precision stage: d is stored explicitly (forming it on the fly would
 // cost one FP64 FMA per stored entry), so the iteration has a third phase
 //   P3  d = r + beta d  followed by a grid barrier.
+//
+// Kernels: k_cg32 (single-precision stage of Algorithm I, and the k0 phase
+// for mpcg_features), k_stage1 (the single-precision stage of Algorithm II
+// with the 2BFS and the kNN running alongside; described at the kernel),
+// k_cg64 (double-precision stage), k_promote and k_spmv.
 #include <math.h>
 
 #include "internal.h"
