@@ -1463,17 +1463,22 @@ static CgArgs make_args(const Launch& L, int slot, int mode) {
 
 // Blocks of the stage kernels: one per SM (fewer when asked).  0 on failure.
 int cg_grid(int requested) {
-  static int cached = 0;
-  if (!cached) {
+  // Per device: the shared-memory attribute and the occupancy are properties
+  // of the device the kernels run on.  A benign race between host threads
+  // computes the same values twice.
+  constexpr int kMaxDevices = 64;
+  static int cached[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+  if (!cached[dev]) {
     struct K {
       const void* f;
       size_t smem;
     } ks[3] = {{(const void*)k_cg32, ring_smem_bytes<float>()},
                {(const void*)k_cg64, ring_smem_bytes<double>()},
                {(const void*)k_stage1, ring_smem_bytes<float>()}};
-    int dev = 0, sms = 0, per = 1 << 30;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    int sms = 0, per = 1 << 30;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return 0;
     for (const K& k : ks) {
       int g = 0;
@@ -1484,11 +1489,13 @@ int cg_grid(int requested) {
         return 0;
       if (g < per) per = g;
     }
-    cached = per > 0 ? sms * per : -1;
-    if (cached > kMaxGrid - 1) cached = kMaxGrid - 1;  // one reduction slot stays free
+    int c = per > 0 ? sms * per : -1;
+    if (c > kMaxGrid - 1) c = kMaxGrid - 1;  // one reduction slot stays free
+    cached[dev] = c;
   }
-  if (cached <= 0) return 0;
-  return (requested > 0 && requested < cached) ? requested : cached;
+  const int c = cached[dev];
+  if (c <= 0) return 0;
+  return (requested > 0 && requested < c) ? requested : c;
 }
 
 const void* cg32_kernel() { return (const void*)k_cg32; }
