@@ -282,3 +282,20 @@ def test_full_size_128cubed_properties(mp):
         res = b - synth.spmv_input(A, xn)
         assert np.linalg.norm(res) / np.linalg.norm(b) <= 1e-10 * 1.01
         assert np.linalg.norm(xn - xs) / np.linalg.norm(xs) <= 6744 * 1e-10
+
+
+@pytest.mark.parametrize("classes", [(0, 1, 9), (1, 9), (9,)])
+def test_algorithm_ii_classes_outside_two_to_seven(mp, classes):
+    """Labels whose eps1 = 10^-t is met at once (t = 0, 1) or never in single
+    precision (t = 9: the stage stops at its cap with a warning), as the
+    oracle does."""
+    A = synth.laplacian_2d(37, 29)
+    xs, b = synth.rhs(A, seed=12)
+    feat, cls = synth.random_sample(200, seed=4, classes=classes)
+    feat[:, 0] = np.linspace(0.5, 2.0, 200) * A.n
+    feat[:, 1] = np.linspace(0.5, 2.0, 200)[::-1] * A.nnz
+    S = mp.DeviceSample(feat, cls)
+    x, r = mp.solve(mp.DeviceCSR.from_host(A), torch.from_numpy(b).cuda(), S)
+    xo, ro = oracle.solve(A, b, S=(feat, cls))
+    assert r["cls"] == ro["cls"] and r["eps1"] == ro["eps1"] and r["pdiam"] == ro["pdiam"]
+    parity(r, ro, x.cpu().numpy(), xo)
