@@ -260,8 +260,10 @@ def batch_section(args, dev, steps, warmup):
     nsys = len(mats)
     ws = torch.empty(mpcg.batch_workspace_bytes(dmats), dtype=torch.uint8, device=dev)
     res = mpcg.result_buffer(nsys, dev)
-    o_mixed = mpcg.options()
-    o_fp64 = mpcg.options(fp64_only=1)
+    # autotune the team granularity once, outside the timed region
+    team_rows, tune_ms = mpcg.batch_tune(dmats, dbs, xs, mpcg.options(), ws, res, S)
+    o_mixed = mpcg.options(team_rows=team_rows)
+    o_fp64 = mpcg.options(fp64_only=1, team_rows=team_rows)
 
     def timed(fn, k, w):
         for _ in range(w):
@@ -322,6 +324,8 @@ def batch_section(args, dev, steps, warmup):
         "fp64_TFLOPs_batch_fp64": flops64 / (ms_fp64 / 1e3) / 1e12,
         "failed_statuses": bad, "sample_seconds": round(t_sample, 1),
         "kernels_per_batch": 1,
+        "autotuned_team_rows": team_rows,
+        "tuning_ms": dict(zip(("8192", "16384", "32768", "65536"), [round(x, 1) for x in tune_ms])),
     }
 
 
@@ -371,6 +375,12 @@ def serve_section(args, dev):
     ress = [mpcg.result_buffer(1, dev) for _ in range(R)]
     pool = int(sum(sorted((mpcg.workspace_bytes(A.n, A.nnz) for A in mats), reverse=True)[:24]))
     max_iters = 40
+    # team granularity: autotuned on one batch of the resident matrices
+    tws = torch.empty(mpcg.batch_workspace_bytes(dmats), dtype=torch.uint8, device=dev)
+    txs = [torch.empty(A.n, dtype=torch.float64, device=dev) for A in mats]
+    team_rows, _ = mpcg.batch_tune(dmats, [r[0] for r in rhs], txs, mpcg.options(), tws,
+                                   mpcg.result_buffer(len(mats), dev), S)
+    del tws, txs
 
     def run_server(opts, arrivals):
         srv = mpcg.Server(256, pool, opts, S, dev)
@@ -423,7 +433,8 @@ def serve_section(args, dev):
             done_t[i] = time.perf_counter() - t0
         return done_t, time.perf_counter() - t0
 
-    o_mixed, o_fp64 = mpcg.options(), mpcg.options(fp64_only=1)
+    o_mixed = mpcg.options(team_rows=team_rows)
+    o_fp64 = mpcg.options(fp64_only=1, team_rows=team_rows)
     run_server(o_mixed, np.zeros(R))  # warm-up
     _, _, burst, _, _ = run_server(o_fp64, np.zeros(R))
     capacity = R / burst  # saturated pure-FP64 serving throughput
@@ -455,6 +466,7 @@ def serve_section(args, dev):
                         f"({rate:.0f}/s), 32 resident matrices n lognormal [1e3, 2e6] "
                         "(2D/3D/aniso/shifted Laplacians), eps2 in {1e-8, 1e-10}",
             "sum_n_resident": int(sum(A.n for A in mats)), "max_iters_per_step": max_iters,
+            "autotuned_team_rows": team_rows,
             "saturated_fp64_solves_per_s": capacity,
             "continuous_batching_mixed": mixed, "continuous_batching_fp64": fp64,
             "one_at_a_time_mixed": fifo}

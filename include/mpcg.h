@@ -114,7 +114,9 @@ typedef struct {
   int32_t grid_blocks;       /* persistent grid size; 0 = one full wave of the device */
   int32_t timeout_ms;        /* limit of every device-side wait (default 20000) */
   int32_t stage1_only;       /* 1: stop after the single-precision stage; x = float64(x~) */
-  int32_t reserved[4];
+  int32_t team_rows;         /* batch and server: target rows per block of a team, which sets
+                                the team size of each system (<= 0: 16384) */
+  int32_t reserved[3];
 } mpcg_options_t;
 
 /* Result record, written by the device at the end of the call's work into
@@ -196,6 +198,22 @@ int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const double* const*
                          double* const* x, const mpcg_sample_t* sample,
                          const mpcg_options_t* opts, void* ws, size_t ws_bytes,
                          mpcg_result_t* res, mpcg_stream_t stream);
+
+/* Autotuner of the batched solve (not in the paper): times mpcg_solve_batch
+ * with the given arguments at each of MPCG_TUNE_CANDIDATES team granularities
+ * (opts->team_rows = 8192, 16384, 32768, 65536 rows per block; a system's
+ * team is the smallest with at most that many rows per block) and writes the
+ * fastest to *team_rows_out (host), and each candidate's milliseconds to
+ * ms_out (host float[MPCG_TUNE_CANDIDATES], nullable).  Pass the result in
+ * opts->team_rows to later batch calls or to a server.  Unlike the other
+ * entry points this call synchronises the host with `stream` (one event wait
+ * per candidate).  x and res hold the last candidate's results. */
+#define MPCG_TUNE_CANDIDATES 4
+int32_t mpcg_batch_tune(int32_t nsys, const mpcg_csr_t* A, const double* const* b,
+                        double* const* x, const mpcg_sample_t* sample,
+                        const mpcg_options_t* opts, void* ws, size_t ws_bytes,
+                        mpcg_result_t* res, mpcg_stream_t stream, int32_t* team_rows_out,
+                        float* ms_out);
 
 /* ---- serving: continuous batching over a slot table (not in the paper) ----
  *

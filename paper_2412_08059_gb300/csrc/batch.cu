@@ -129,10 +129,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
 // ---------------------------------------------------------------------------------------
 // Plan of one launch: teams (blocks, sizes, classes) and the class queues.
 // Team-size class of a system: the smallest team (1, 2, 4, ..., 128 blocks)
-// with at most kRowsPerBlock rows per block.
-int size_class(int n) {
+// with at most rows_per_block rows per block.
+int size_class(int n, int rows_per_block) {
   int c = 0;
-  while (c < kTeamClasses - 1 && (long long)n > (long long)kRowsPerBlock << c) ++c;
+  while (c < kTeamClasses - 1 && (long long)n > (long long)rows_per_block << c) ++c;
   return c;
 }
 
@@ -140,14 +140,15 @@ int size_class(int n) {
 // iteration count that grows like sqrt(n) (CG on discretised operators).
 double work_of(int n, int nnz) { return ((double)nnz + 6.0 * n) * sqrt((double)n); }
 
-Plan make_plan(int nsys, const int* n, const double* work, int grid) {
+Plan make_plan(int nsys, const int* n, const double* work, int grid, int rows_per_block) {
+  if (rows_per_block <= 0) rows_per_block = kRowsPerBlock;
   Plan P;
   std::vector<int> cls(nsys);
   std::vector<double> w(nsys);
   double cw[kTeamClasses] = {0};
   int cnt[kTeamClasses] = {0};
   for (int i = 0; i < nsys; ++i) {
-    cls[i] = size_class(n[i]);
+    cls[i] = size_class(n[i], rows_per_block);
     w[i] = work[i];
   }
   // Demote the largest classes while one team of every non-empty class does
@@ -286,7 +287,7 @@ extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const dou
   if (grid <= 0) return MPCG_ERR_CUDA;
   std::vector<double> work(nsys);
   for (int32_t i = 0; i < nsys; ++i) work[i] = work_of(nv[i], mv[i]);
-  const Plan P = make_plan(nsys, nv.data(), work.data(), grid);
+  const Plan P = make_plan(nsys, nv.data(), work.data(), grid, opts->team_rows);
 
   // Header blob: [BatchHdr | BatchSys[nsys] | order | team_of_block |
   // rank_of_block | team_size | team_class], then the systems' regions.
@@ -350,4 +351,47 @@ extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const dou
   const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_batch, dim3(grid),
                                                     dim3(kBatchThreads), args, 0, st);
   return e == cudaSuccess ? MPCG_OK : MPCG_ERR_CUDA;
+}
+
+extern "C" int32_t mpcg_batch_tune(int32_t nsys, const mpcg_csr_t* A, const double* const* b,
+                                   double* const* x, const mpcg_sample_t* sample,
+                                   const mpcg_options_t* opts, void* ws, size_t ws_bytes,
+                                   mpcg_result_t* res, mpcg_stream_t stream,
+                                   int32_t* team_rows_out, float* ms_out) {
+  if (!opts || !team_rows_out) return MPCG_ERR_INVALID_ARG;
+  static const int kCand[MPCG_TUNE_CANDIDATES] = {8192, 16384, 32768, 65536};
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return MPCG_ERR_CUDA;
+  }
+  int32_t status = MPCG_OK;
+  int best = -1;
+  float best_ms = 0.0f;
+  for (int k = 0; k < MPCG_TUNE_CANDIDATES && status == MPCG_OK; ++k) {
+    mpcg_options_t o = *opts;
+    o.team_rows = kCand[k];
+    float ms = -1.0f;
+    if (cudaEventRecord(e0, st) != cudaSuccess) {
+      status = MPCG_ERR_CUDA;
+      break;
+    }
+    status = mpcg_solve_batch(nsys, A, b, x, sample, &o, ws, ws_bytes, res, st);
+    if (status != MPCG_OK) break;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      status = MPCG_ERR_CUDA;
+      break;
+    }
+    if (ms_out) ms_out[k] = ms;
+    if (best < 0 || ms < best_ms) {
+      best = k;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status == MPCG_OK) *team_rows_out = kCand[best];
+  return status;
 }

@@ -327,7 +327,7 @@ extern "C" int32_t mpcg_batch_step(mpcg_server_t* s, int32_t max_iters, int32_t*
       s->fresh[i] = 0;
     }
   if (!ids.empty()) {
-    const Plan P = make_plan((int)ids.size(), nv.data(), work.data(), s->grid);
+    const Plan P = make_plan((int)ids.size(), nv.data(), work.data(), s->grid, s->o.team_rows);
     char* m = s->mirror.data();
     BatchHdr* H = (BatchHdr*)m;
     memset(H, 0, sizeof(BatchHdr));

@@ -22,7 +22,7 @@ namespace mpcg {
 constexpr int kBatchThreads = 512;
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kTeamClasses = 8;                // team sizes 1, 2, 4, ..., 128 blocks
-constexpr int kRowsPerBlock = 16384;           // planner: target rows per block of a team
+constexpr int kRowsPerBlock = 16384;           // planner default: target rows per block of a team
 constexpr int kNoBudget = 0x7fffffff;          // iteration budget of a run-to-completion call
 
 // One system of the batch (device copy written by the host).
@@ -863,7 +863,8 @@ struct Plan {
   int qbase[kTeamClasses], qlen[kTeamClasses];
 };
 // Teams for a grid of `grid` blocks and the class queues of nsys systems of
-// n rows with estimated work `work` (largest first within a class).
-Plan make_plan(int nsys, const int* n, const double* work, int grid);
+// n rows with estimated work `work` (largest first within a class); a system
+// goes to the smallest team with at most rows_per_block rows per block.
+Plan make_plan(int nsys, const int* n, const double* work, int grid, int rows_per_block);
 
 }  // namespace mpcg

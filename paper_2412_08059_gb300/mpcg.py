@@ -54,7 +54,8 @@ class Options(C.Structure):
                 ("max_it_fp32", C.c_int32), ("max_it_fp64", C.c_int32),
                 ("max_true_restarts", C.c_int32), ("feat_mask", C.c_uint32),
                 ("fp64_only", C.c_int32), ("grid_blocks", C.c_int32), ("timeout_ms", C.c_int32),
-                ("stage1_only", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("stage1_only", C.c_int32), ("team_rows", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class Result(C.Structure):
@@ -84,7 +85,7 @@ SYMBOLS = ("mpcg_options_default", "mpcg_status_string", "mpcg_workspace_bytes",
            "mpcg_choose_eps1", "mpcg_solve", "mpcg_batch_workspace_bytes", "mpcg_solve_batch",
            "mpcg_spmv", "mpcg_bfs", "mpcg_pseudo_diameter", "mpcg_solve_static",
            "mpcg_server_workspace_bytes", "mpcg_server_create", "mpcg_server_destroy",
-           "mpcg_server_admit", "mpcg_batch_step", "mpcg_server_retire")
+           "mpcg_server_admit", "mpcg_batch_step", "mpcg_server_retire", "mpcg_batch_tune")
 
 
 def load(path: str = LIB_PATH):
@@ -122,6 +123,9 @@ def load(path: str = LIB_PATH):
         L.mpcg_bfs.argtypes = [C.POINTER(CsrDesc), I32, P, P, SZ, P]
         L.mpcg_pseudo_diameter.restype = I32
         L.mpcg_pseudo_diameter.argtypes = [C.POINTER(CsrDesc), P, P, SZ, P]
+        L.mpcg_batch_tune.restype = I32
+        L.mpcg_batch_tune.argtypes = [I32, P, P, P, C.POINTER(SampleDesc), C.POINTER(Options),
+                                      P, SZ, P, P, C.POINTER(I32), P]
         L.mpcg_server_workspace_bytes.restype = SZ
         L.mpcg_server_workspace_bytes.argtypes = [I32, SZ]
         L.mpcg_server_create.restype = I32
@@ -317,6 +321,26 @@ def solve_batch_async(mats: list[DeviceCSR], bs: list, xs: list, opts: Options,
                                  C.byref(sample.desc) if sample is not None else None,
                                  C.byref(opts), _ptr(ws), ws.numel(), _ptr(res), _stream(stream))
     _check(st, "mpcg_solve_batch")
+
+
+TUNE_CANDIDATES = 4
+
+
+def batch_tune(mats: list[DeviceCSR], bs: list, xs: list, opts: Options, ws: torch.Tensor,
+               res: torch.Tensor, sample: DeviceSample | None = None, stream=None):
+    """mpcg_batch_tune: (fastest team_rows, milliseconds per candidate).  Synchronises."""
+    n = len(mats)
+    descs = (CsrDesc * n)(*[m.desc for m in mats])
+    bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    best = C.c_int32(0)
+    ms = (C.c_float * TUNE_CANDIDATES)()
+    st = load().mpcg_batch_tune(n, descs, bp, xp,
+                                C.byref(sample.desc) if sample is not None else None,
+                                C.byref(opts), _ptr(ws), ws.numel(), _ptr(res), _stream(stream),
+                                C.byref(best), ms)
+    _check(st, "mpcg_batch_tune")
+    return best.value, list(ms)
 
 
 def batch_workspace_bytes(mats: list[DeviceCSR]) -> int:

@@ -170,3 +170,23 @@ def test_batch_many_small_systems_steal(mp):
         parity(rs[k], ro, xs[k], xo)
     assert all(r["status"] in (0, 1) for r in rs)
     assert all(r["true_rel_resid"] <= 1e-10 for r in rs)
+
+
+def test_batch_tune_picks_a_candidate_and_results_hold(mp):
+    mats = mixed_systems()
+    bs = [synth.rhs(A, seed=120 + i)[1] for i, A in enumerate(mats)]
+    dmats = [mp.DeviceCSR.from_host(A) for A in mats]
+    dbs = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in bs]
+    xs = [torch.empty(A.n, dtype=torch.float64, device="cuda") for A in mats]
+    ws = torch.empty(mp.batch_workspace_bytes(dmats), dtype=torch.uint8, device="cuda")
+    res = mp.result_buffer(len(mats))
+    opts = mp.options(eps1=1e-4)
+    best, ms = mp.batch_tune(dmats, dbs, xs, opts, ws, res, None)
+    assert best in (8192, 16384, 32768, 65536)
+    assert len(ms) == 4 and all(t > 0 for t in ms)
+    assert ms[(8192, 16384, 32768, 65536).index(best)] == min(ms)
+    # a batch with the chosen granularity still matches the oracle
+    xs2, rs = run_batch(mp, mats, bs, None, eps1=1e-4, team_rows=best)
+    for A, b, x, r in zip(mats, bs, xs2, rs):
+        xo, ro = oracle.solve(A, b, eps1=1e-4)
+        parity(r, ro, x, xo)
