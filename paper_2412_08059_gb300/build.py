@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmpcg.so")
 SOURCES = ("prep.cu", "cg.cu", "bfs.cu", "knn.cu", "api.cu", "noalloc.cu", "batch.cu", "serve.cu")
-HEADERS = ("common.cuh", "internal.h", "bfs_core.cuh", "knn_core.cuh", "team_core.cuh")
+HEADERS = ("common.cuh", "internal.h", "bfs_core.cuh", "bfs_block.cuh", "knn_core.cuh", "team_core.cuh")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

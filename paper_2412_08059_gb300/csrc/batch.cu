@@ -65,11 +65,7 @@ __device__ bool sys_solve(Team& t, const BatchSys& s, const BatchArgs& a) {
   } else if (sys_status(s) == 0) {
     if (a.auto_eps1) {
       // Algorithm II: l~ by 2BFS, v over the first k0 iterations, eps1 by kNN
-      BfsGraph g{ctl, s.A.row_ptr, s.A.col, s.n, s.w.fq0, s.w.fq1, s.w.label, s.w.ckey,
-                 s.w.fq2, s.w.fq3};
-      TeamSyncFn sync{&t};
-      if (!pseudo_diameter_run(g, s.w.dist, s.w.dist2, team_tid(t), team_threads(t), sync))
-        return false;
+      if (!team_pseudo_diameter(t, s, a.smem_bytes)) return false;
       if (!team_sync(t)) return false;
       bool done;
       if (!sys_cg32(t, s, kCgK0, red, kNoBudget, &done)) return false;
@@ -139,6 +135,14 @@ int size_class(int n, int rows_per_block) {
 // Work estimate of a system: entries touched per iteration times an
 // iteration count that grows like sqrt(n) (CG on discretised operators).
 double work_of(int n, int nnz) { return ((double)nnz + 6.0 * n) * sqrt((double)n); }
+
+int team_smem(const void* kernel, int auto_eps1) {
+  if (!auto_eps1) return 0;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTeamBfsSmem) !=
+      cudaSuccess)
+    return -1;
+  return kTeamBfsSmem;
+}
 
 Plan make_plan(int nsys, const int* n, const double* work, int grid, int rows_per_block) {
   if (rows_per_block <= 0) rows_per_block = kRowsPerBlock;
@@ -244,7 +248,9 @@ size_t batch_header_bytes(int nsys) {
          a256(sizeof(int) * (size_t)nsys) + 4 * a256(sizeof(int) * kMaxGrid);
 }
 
-int batch_grid(int requested) { return persistent_grid((const void*)k_batch, kBatchThreads, requested); }
+int batch_grid(int requested, int smem) {
+  return persistent_grid((const void*)k_batch, kBatchThreads, requested, (size_t)smem);
+}
 
 }  // namespace
 
@@ -283,7 +289,9 @@ extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const dou
   }
   if (mpcg_batch_workspace_bytes(nsys, nv.data(), mv.data(), opts) > ws_bytes)
     return MPCG_ERR_WORKSPACE;
-  const int grid = batch_grid(opts->grid_blocks);
+  const int smem = team_smem((const void*)k_batch, auto_eps1);
+  if (smem < 0) return MPCG_ERR_CUDA;
+  const int grid = batch_grid(opts->grid_blocks, smem);
   if (grid <= 0) return MPCG_ERR_CUDA;
   std::vector<double> work(nsys);
   for (int32_t i = 0; i < nsys; ++i) work[i] = work_of(nv[i], mv[i]);
@@ -346,10 +354,11 @@ extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const dou
   a.team_class = tcl_d;
   a.o = *opts;
   a.auto_eps1 = auto_eps1;
+  a.smem_bytes = smem;
   if (auto_eps1) a.knn = knn_spec(*sample, *opts);
   void* args[] = {&a};
   const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_batch, dim3(grid),
-                                                    dim3(kBatchThreads), args, 0, st);
+                                                    dim3(kBatchThreads), args, (size_t)smem, st);
   return e == cudaSuccess ? MPCG_OK : MPCG_ERR_CUDA;
 }
 

@@ -28,7 +28,7 @@ struct Launch {
   int grid_req;  // requested grid (0 = one full wave)
 };
 
-int persistent_grid(const void* kernel, int threads, int requested);
+int persistent_grid(const void* kernel, int threads, int requested, size_t dyn_smem = 0);
 
 // api.cu: host checks shared by the entry points
 bool options_ok(const mpcg_options_t* o);

@@ -64,11 +64,12 @@ size_t carve(const Dims& d, char* base, Ws* ws) {
   return off;
 }
 
-int persistent_grid(const void* kernel, int threads, int requested) {
+int persistent_grid(const void* kernel, int threads, int requested, size_t dyn_smem) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, dyn_smem) !=
+      cudaSuccess)
     return 0;
   if (per_sm > 1) per_sm = 1;  // fewer barrier arrivals: one block per SM
   int full = sms * per_sm;

@@ -61,11 +61,7 @@ __device__ bool slot_setup(Team& t, const BatchSys& s, const BatchArgs& a, int& 
 // Algorithm II features: 2BFS, the k0 iterations and the kNN vote.
 __device__ bool slot_features(Team& t, const BatchSys& s, const BatchArgs& a, int& red) {
   Ctl* ctl = s.w.ctl;
-  BfsGraph g{ctl, s.A.row_ptr, s.A.col, s.n, s.w.fq0, s.w.fq1, s.w.label, s.w.ckey,
-                 s.w.fq2, s.w.fq3};
-  TeamSyncFn sync{&t};
-  if (!pseudo_diameter_run(g, s.w.dist, s.w.dist2, team_tid(t), team_threads(t), sync))
-    return false;
+  if (!team_pseudo_diameter(t, s, a.smem_bytes)) return false;
   if (!team_sync(t)) return false;
   bool done;
   if (!sys_cg32(t, s, kCgK0, red, kNoBudget, &done)) return false;
@@ -191,6 +187,7 @@ struct mpcg_server {
   KnnSpec knn;
   int auto_eps1;
   int grid;
+  int smem;  // dynamic shared memory of each step launch
 };
 
 namespace {
@@ -239,7 +236,10 @@ extern "C" int32_t mpcg_server_create(void* ws, size_t ws_bytes, int32_t max_slo
   const int auto_eps1 = !opts->fp64_only && !(opts->eps1 > 0.0);
   if (auto_eps1 && !sample_ok(sample)) return MPCG_ERR_INVALID_ARG;
   if (!ws || ((uintptr_t)ws & 255u) || ws_bytes <= fixed_bytes(max_slots)) return MPCG_ERR_WORKSPACE;
-  const int grid = persistent_grid((const void*)k_serve, kBatchThreads, opts->grid_blocks);
+  const int smem = team_smem((const void*)k_serve, auto_eps1);
+  if (smem < 0) return MPCG_ERR_CUDA;
+  const int grid = persistent_grid((const void*)k_serve, kBatchThreads, opts->grid_blocks,
+                                   (size_t)smem);
   if (grid <= 0) return MPCG_ERR_CUDA;
   mpcg_server* s = new mpcg_server();
   s->dev = (char*)ws;
@@ -258,6 +258,7 @@ extern "C" int32_t mpcg_server_create(void* ws, size_t ws_bytes, int32_t max_slo
   s->auto_eps1 = auto_eps1;
   if (auto_eps1) s->knn = knn_spec(*sample, *opts);
   s->grid = grid;
+  s->smem = smem;
   *out = s;
   return MPCG_OK;
 }
@@ -355,6 +356,7 @@ extern "C" int32_t mpcg_batch_step(mpcg_server_t* s, int32_t max_iters, int32_t*
     a.team_class = put(P.team_class, kMaxGrid);
     a.o = s->o;
     a.auto_eps1 = s->auto_eps1;
+    a.smem_bytes = s->smem;
     a.knn = s->knn;
     if (cudaMemcpyAsync(s->dev, m, s->mirror.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
       return MPCG_ERR_CUDA;
@@ -364,7 +366,7 @@ extern "C" int32_t mpcg_batch_step(mpcg_server_t* s, int32_t max_iters, int32_t*
     sa.budget = max_iters;
     void* args[] = {&sa};
     if (cudaLaunchCooperativeKernel((const void*)k_serve, dim3(s->grid), dim3(kBatchThreads), args,
-                                    0, st) != cudaSuccess)
+                                    (size_t)s->smem, st) != cudaSuccess)
       return MPCG_ERR_CUDA;
   }
   if (slot_phase &&

@@ -15,6 +15,7 @@
 
 #include <vector>
 
+#include "bfs_block.cuh"
 #include "internal.h"
 
 namespace mpcg {
@@ -24,6 +25,8 @@ constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kTeamClasses = 8;                // team sizes 1, 2, 4, ..., 128 blocks
 constexpr int kRowsPerBlock = 16384;           // planner default: target rows per block of a team
 constexpr int kNoBudget = 0x7fffffff;          // iteration budget of a run-to-completion call
+constexpr int kTeamBfsSmem = 96 * 1024;        // dynamic shared memory of a launch that runs the 2BFS
+constexpr int kBlockBfsMaxN = 1 << 18;         // larger systems run the 2BFS over the whole team
 
 // One system of the batch (device copy written by the host).
 struct BatchSys {
@@ -57,6 +60,7 @@ struct BatchArgs {
   KnnSpec knn;
   mpcg_options_t o;
   int auto_eps1;
+  int smem_bytes;  // dynamic shared memory of the launch (0: none)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -79,6 +83,11 @@ struct Team {
   long long timeout_ns;
   TeamShared* S;
 };
+
+// The launch's dynamic shared memory (the block-local 2BFS); its size is
+// BatchArgs::smem_bytes.  Not kept in Team, so that it takes no register
+// for the length of the kernel.
+extern __shared__ __align__(16) unsigned char team_dyn[];
 
 // Bounded barrier over the team's blocks.  False (in every thread of the
 // block) on timeout or when another team has aborted the launch.
@@ -855,6 +864,49 @@ static __device__ int batch_take(BatchHdr* h, const int* order, int c) {
   return -1;
 }
 
+// Block-local 2BFS of one system (every thread of the calling block):
+// ctl->pdiam, far_t, reached and connected = 1 if the graph is connected,
+// else only connected = 0.  Not inlined: its code then leaves the register
+// allocation of the CG loops in the same kernel alone (measured: inlined, the
+// FP64 stage of a 512-system batch ran 12 % slower), and only the system's
+// pointer crosses the call, so the search itself keeps its state in
+// registers.
+static __device__ __noinline__ void block_bfs_system(const BatchSys* sp, int smem_bytes) {
+  const BatchSys& s = *sp;
+  Ctl* ctl = s.w.ctl;
+  int32_t* const gq[4] = {s.w.fq0, s.w.fq1, s.w.fq2, s.w.fq3};
+  const BlockBfs b = block_bfs_layout(s.A.row_ptr, s.A.col, s.n, team_dyn, smem_bytes,
+                                      reinterpret_cast<uint32_t*>(s.w.ckey), gq);
+  int pd = 0, tv = 0;
+  const bool ok = block_pseudo_diameter(b, &pd, &tv);
+  if (threadIdx.x == 0) {
+    if (ok) {
+      ctl->pdiam = pd;
+      ctl->far_t = tv;
+      ctl->reached = s.n;
+    }
+    ctl->connected = ok ? 1 : 0;
+  }
+}
+
+// 2BFS pseudo-diameter of the system (Sec. 6): ctl->pdiam and ctl->far_t.
+// Connected systems of up to kBlockBfsMaxN rows: the team's first block runs
+// both searches alone in shared memory (bfs_block.cuh) while the others wait
+// at the barrier.  Larger or disconnected systems (and launches without the
+// shared buffer): the team version over all of the team's blocks.
+static __device__ bool team_pseudo_diameter(Team& t, const BatchSys& s, int smem_bytes) {
+  Ctl* ctl = s.w.ctl;
+  if (s.n >= 1 && s.n <= kBlockBfsMaxN && smem_bytes > 0) {
+    if (t.rank == 0) block_bfs_system(&s, smem_bytes);
+    if (!team_sync(t)) return false;
+    if (*reinterpret_cast<volatile int*>(&ctl->connected)) return true;
+  }
+  BfsGraph g{ctl, s.A.row_ptr, s.A.col, s.n, s.w.fq0, s.w.fq1, s.w.label, s.w.ckey,
+             s.w.fq2, s.w.fq3};
+  TeamSyncFn sync{&t};
+  return pseudo_diameter_run(g, s.w.dist, s.w.dist2, team_tid(t), team_threads(t), sync);
+}
+
 // ---------------------------------------------------------------------------------------
 // Host: plan of a team launch (batch.cu).
 // ---------------------------------------------------------------------------------------
@@ -866,5 +918,9 @@ struct Plan {
 // n rows with estimated work `work` (largest first within a class); a system
 // goes to the smallest team with at most rows_per_block rows per block.
 Plan make_plan(int nsys, const int* n, const double* work, int grid, int rows_per_block);
+// Dynamic shared memory of a team launch of `kernel`: the block-local 2BFS
+// buffer when the launch computes features (auto_eps1), else none.  Raises
+// the kernel's limit on the current device; -1 on a CUDA error.
+int team_smem(const void* kernel, int auto_eps1);
 
 }  // namespace mpcg

@@ -1,0 +1,110 @@
+"""GPU: the 2BFS pseudo-diameter of batched systems against the oracle's BFS
+(Sec. 6), over the storage cases of the block-local search (bitmaps in
+shared or global memory, frontiers past the shared queue capacity), the
+speculative second search (t = n - 1, t != n - 1 with the second search
+dropped), the team-wide search for disconnected and for larger systems, and
+n = 1.  Every system is also solved to eps2 (Algorithm II)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_08059_gb300 import build, mpcg
+    build.build()
+    mpcg.load()
+    return mpcg
+
+
+def permuted(A, seed):
+    """P A P^T for a random permutation P: the same graph, renumbered."""
+    rng = np.random.default_rng(seed)
+    p = rng.permutation(A.n)           # new index of old vertex i is p[i]
+    inv = np.argsort(p)                # old vertex of new index k
+    rows, cols, vals = [], [], []
+    for k in range(A.n):
+        i = inv[k]
+        lo, hi = A.row_ptr[i], A.row_ptr[i + 1]
+        c = p[A.col[lo:hi]]
+        order = np.argsort(c, kind="stable")
+        cols.append(c[order])
+        vals.append(A.val[lo:hi][order])
+        rows.append(hi - lo)
+    rp = np.zeros(A.n + 1, np.int64)
+    rp[1:] = np.cumsum(rows)
+    return synth.CSR(rp.astype(np.int32), np.concatenate(cols).astype(np.int32),
+                     np.concatenate(vals))
+
+
+def union(*mats):
+    rp, cols, vals, off, base = [np.zeros(1, np.int64)], [], [], 0, 0
+    for A in mats:
+        rp.append(A.row_ptr[1:].astype(np.int64) + base)
+        cols.append(A.col.astype(np.int64) + off)
+        vals.append(A.val)
+        off += A.n
+        base += A.nnz
+    return synth.CSR(np.concatenate(rp).astype(np.int32), np.concatenate(cols).astype(np.int32),
+                     np.concatenate(vals))
+
+
+def systems():
+    return [
+        synth.laplacian_2d(180, 150),                      # t = n - 1, shared bitmaps
+        permuted(synth.laplacian_2d(60, 45), seed=1),      # t != n - 1: second search dropped
+        synth.random_regular_laplacian(30000, 8, 1e-3, seed=5),  # frontiers past the shared queues
+        synth.star(3001, 1.1),                             # t = 1, l~ = 2
+        synth.path(2500),                                  # 2499 levels
+        synth.from_edges(1, [], [], np.zeros(0), np.full(1, 2.0)),  # n = 1
+        union(synth.path(40), synth.laplacian_2d(12, 9)),  # disconnected: team-wide search
+        synth.laplacian_3d(60, eps=1e-2),                  # n = 216000: bitmaps in global memory
+        synth.laplacian_2d(512, 512),                      # n = 2^18: largest block-local case
+        synth.laplacian_2d(513, 512),                      # n > 2^18: team-wide search
+    ]
+
+
+def sample_over(mats, seed=2, count=200):
+    feat, cls = synth.random_sample(count, seed=seed)
+    ns = np.array([A.n for A in mats], float)
+    feat[:, 0] = np.exp(np.linspace(np.log(0.5 * ns.min()), np.log(2 * ns.max()), count))
+    feat[:, 1] = feat[:, 0] * np.linspace(3.0, 9.0, count)[::-1]
+    return feat, cls
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("team_rows", [16384, 65536])
+def test_batch_pseudo_diameter_matches_oracle(mp, team_rows):
+    mats = systems()
+    bs = [synth.rhs(A, seed=300 + i)[1] for i, A in enumerate(mats)]
+    feat, cls = sample_over(mats)
+    S = mp.DeviceSample(feat, cls)
+    dmats = [mp.DeviceCSR.from_host(A) for A in mats]
+    dbs = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in bs]
+    xs = [torch.empty(A.n, dtype=torch.float64, device="cuda") for A in mats]
+    ws = torch.empty(mp.batch_workspace_bytes(dmats), dtype=torch.uint8, device="cuda")
+    res = mp.result_buffer(len(mats))
+    mp.solve_batch_async(dmats, dbs, xs, mp.options(team_rows=team_rows), ws, res, S)
+    torch.cuda.synchronize()
+    rs = mp.read_results(res, len(mats))
+    for A, r in zip(mats, rs):
+        assert r["pdiam"] == oracle.pseudo_diameter(A), (A.n, r["pdiam"])
+        assert r["cls"] == oracle.knn([A.n, A.nnz, r["pdiam"], r["v"]], (feat, cls))
+        assert r["status"] >= 0, (A.n, r["status"])
+        assert r["true_rel_resid"] <= 1e-10
+
+
+def test_pinned_diameters():
+    """The pins the GPU test relies on, from the oracle alone (CPU)."""
+    assert oracle.pseudo_diameter(synth.path(2500)) == 2499
+    assert oracle.pseudo_diameter(synth.star(3001, 1.1)) == 2
+    assert oracle.pseudo_diameter(synth.laplacian_2d(180, 150)) == 179 + 149
+    A = permuted(synth.laplacian_2d(60, 45), seed=1)
+    ell, t = oracle.pseudo_diameter(A, return_t=True)
+    assert ell == 59 + 44 and t != A.n - 1
