@@ -20,6 +20,7 @@
 // SpMV rows summed in stored order with fused multiply-adds, float-float
 // dot products in single precision, alpha and beta rounded once to float.
 #include <math.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <algorithm>
@@ -29,11 +30,92 @@
 
 namespace mpcg {
 
-// Returns false if the launch aborted.
-__device__ bool sys_solve(Team& t, const BatchSys& s, const BatchArgs& a) {
+// Set-up of a system: CSR check, b~ = float32(b), sliced layout, ||b||; x = 0
+// when b = 0.  Returns false if the launch aborted.
+static __device__ bool sys_prep(Team& t, const BatchSys& s, const BatchArgs& a, int& red) {
+  Ctl* ctl = s.w.ctl;
+  const bool lead0 = t.rank == 0 && threadIdx.x == 0;
+  sys_init(t, s, a);
+  if (!team_sync(t)) return false;
+  sys_rows(t, s);
+  if (!team_sync(t)) return false;
+  if (sys_status(s) == 0) {
+    if (t.rank == 0) block_scan_slices(s.w.slice_w, s.w.slice_ptr, s.nslices);
+    if (!team_sync(t)) return false;
+    sys_fill(t, s);
+    // ||b||_2 in double
+    double p = 0.0;
+    for (int i = team_tid(t); i < s.n; i += team_threads(t)) p = __fma_rn(s.b[i], s.b[i], p);
+    double bb;
+    if (!team_sum_d(t, p, s.w.partials, red, bb)) return false;  // includes the fill barrier
+    if (lead0) {
+      const double bn = sqrt(bb);
+      ctl->t_prep = globaltimer();
+      ctl->bnorm64 = bn;
+      if (!isfinite(bn)) set_status(ctl, MPCG_ERR_NAN);
+      else if (bn == 0.0) ctl->trivial = 1;
+    }
+    if (!team_sync(t)) return false;
+  }
+  if (sys_status(s) == 0 && *reinterpret_cast<volatile int*>(&ctl->trivial)) {
+    for (int i = team_tid(t); i < s.n; i += team_threads(t)) s.x[i] = 0.0;  // b = 0: x = 0
+  }
+  return team_sync(t);
+}
+
+// First launch of a mixed-precision batch: set-up, then Algorithm II's
+// features (2BFS, the k0 iterations and v, the kNN label) or the fixed eps1
+// of Algorithm I, and the single-precision stage.  Returns false if the
+// launch aborted.
+static __device__ bool sys_stage1(Team& t, const BatchSys& s, const BatchArgs& a) {
+  Ctl* ctl = s.w.ctl;
+  int red = 0;
+  if (!sys_prep(t, s, a, red)) return false;
+  if (sys_status(s) != 0 || ctl->trivial) return true;
+  bool done;
+  if (a.auto_eps1) {
+    if (!team_pseudo_diameter(t, s, a.smem_bytes)) return false;
+    if (!team_sync(t)) return false;
+    if (!sys_cg32<true>(t, s, kCgK0, red, kNoBudget, &done)) return false;
+    if (!team_sync(t)) return false;
+    if (sys_status(s) == 0 && t.rank == 0 && threadIdx.x < 32) {
+      const double chi[4] = {(double)s.n, (double)s.nnz, (double)ctl->pdiam, ctl->v};
+      const int cls = knn_warp(a.knn, chi);
+      if (threadIdx.x == 0) {
+        if (cls < 0) {
+          set_status(ctl, MPCG_ERR_INVALID_ARG);
+        } else {
+          ctl->cls = cls;
+          ctl->eps1 = pow10_neg(cls);
+        }
+        ctl->t_features = globaltimer();
+      }
+    }
+    if (!team_sync(t)) return false;
+    if (sys_status(s) == 0 && !sys_cg32<true>(t, s, kCgContinue, red, kNoBudget, &done)) return false;
+  } else {
+    if (!sys_cg32<true>(t, s, kCgToEps1, red, kNoBudget, &done)) return false;
+  }
+  return team_sync(t);
+}
+
+// The whole method for one system in one launch (set-up, features or the
+// fixed eps1, both stages, the result record), single-precision SpMV from
+// global memory; with a.part == 2 only the double-precision stage after
+// sys_stage1 and the result record.  Returns false if the launch aborted.
+static __device__ bool sys_solve(Team& t, const BatchSys& s, const BatchArgs& a) {
   Ctl* ctl = s.w.ctl;
   const bool lead0 = t.rank == 0 && threadIdx.x == 0;
   int red = 0;
+  if (a.part == 2) {
+    bool done;
+    if (sys_status(s) == 0 && !*reinterpret_cast<volatile int*>(&ctl->trivial) &&
+        !sys_cg64(t, s, 0, red, kNoBudget, false, &done))
+      return false;
+    if (!team_sync(t)) return false;
+    sys_finalize(t, s);
+    return true;
+  }
   sys_init(t, s, a);
   if (!team_sync(t)) return false;
   sys_rows(t, s);
@@ -68,7 +150,7 @@ __device__ bool sys_solve(Team& t, const BatchSys& s, const BatchArgs& a) {
       if (!team_pseudo_diameter(t, s, a.smem_bytes)) return false;
       if (!team_sync(t)) return false;
       bool done;
-      if (!sys_cg32(t, s, kCgK0, red, kNoBudget, &done)) return false;
+      if (!sys_cg32<false>(t, s, kCgK0, red, kNoBudget, &done)) return false;
       if (!team_sync(t)) return false;
       if (sys_status(s) == 0 && t.rank == 0 && threadIdx.x < 32) {
         const double chi[4] = {(double)s.n, (double)s.nnz, (double)ctl->pdiam, ctl->v};
@@ -84,10 +166,10 @@ __device__ bool sys_solve(Team& t, const BatchSys& s, const BatchArgs& a) {
         }
       }
       if (!team_sync(t)) return false;
-      if (sys_status(s) == 0 && !sys_cg32(t, s, kCgContinue, red, kNoBudget, &done)) return false;
+      if (sys_status(s) == 0 && !sys_cg32<false>(t, s, kCgContinue, red, kNoBudget, &done)) return false;
     } else {
       bool done;
-      if (!sys_cg32(t, s, kCgToEps1, red, kNoBudget, &done)) return false;
+      if (!sys_cg32<false>(t, s, kCgToEps1, red, kNoBudget, &done)) return false;
     }
     if (!team_sync(t)) return false;
     bool done;
@@ -98,6 +180,12 @@ __device__ bool sys_solve(Team& t, const BatchSys& s, const BatchArgs& a) {
   return true;
 }
 
+// The persistent team loop of one launch: kPart 1 runs sys_stage1 on every
+// system, kPart 2 sys_solve.  Two kernels, so that the code of one stage
+// does not change the register allocation of the other's loops (measured:
+// with both stages in one kernel, whatever else the kernel held moved the
+// FP64 stage by up to 50 %).
+template <int kPart>
 __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
   __shared__ TeamShared S;
   Team t;
@@ -115,7 +203,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
     if (!team_sync(t)) return;
     const int idx = *reinterpret_cast<volatile int*>(&a.h->next[t.team]);
     if (idx < 0) return;
-    if (!sys_solve(t, a.sys[idx], a)) return;
+    if constexpr (kPart == 1) {
+      if (!sys_stage1(t, a.sys[idx], a)) return;
+    } else {
+      if (!sys_solve(t, a.sys[idx], a)) return;
+    }
     if (!team_sync(t)) return;  // every block has read next[team]
   }
 }
@@ -136,12 +228,11 @@ int size_class(int n, int rows_per_block) {
 // iteration count that grows like sqrt(n) (CG on discretised operators).
 double work_of(int n, int nnz) { return ((double)nnz + 6.0 * n) * sqrt((double)n); }
 
-int team_smem(const void* kernel, int auto_eps1) {
-  if (!auto_eps1) return 0;
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTeamBfsSmem) !=
+int team_smem(const void* kernel, int stage1) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTeamSmem) !=
       cudaSuccess)
     return -1;
-  return kTeamBfsSmem;
+  return stage1 ? kTeamSmem : kScanSmem;
 }
 
 Plan make_plan(int nsys, const int* n, const double* work, int grid, int rows_per_block) {
@@ -249,7 +340,7 @@ size_t batch_header_bytes(int nsys) {
 }
 
 int batch_grid(int requested, int smem) {
-  return persistent_grid((const void*)k_batch, kBatchThreads, requested, (size_t)smem);
+  return persistent_grid((const void*)k_batch<1>, kBatchThreads, requested, (size_t)smem);
 }
 
 }  // namespace
@@ -289,8 +380,9 @@ extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const dou
   }
   if (mpcg_batch_workspace_bytes(nsys, nv.data(), mv.data(), opts) > ws_bytes)
     return MPCG_ERR_WORKSPACE;
-  const int smem = team_smem((const void*)k_batch, auto_eps1);
-  if (smem < 0) return MPCG_ERR_CUDA;
+  const int smem = team_smem((const void*)k_batch<1>, 1);
+  const int smem2 = team_smem((const void*)k_batch<2>, 0);
+  if (smem < 0 || smem2 < 0) return MPCG_ERR_CUDA;
   const int grid = batch_grid(opts->grid_blocks, smem);
   if (grid <= 0) return MPCG_ERR_CUDA;
   std::vector<double> work(nsys);
@@ -354,11 +446,20 @@ extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const dou
   a.team_class = tcl_d;
   a.o = *opts;
   a.auto_eps1 = auto_eps1;
-  a.smem_bytes = smem;
   if (auto_eps1) a.knn = knn_spec(*sample, *opts);
   void* args[] = {&a};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_batch, dim3(grid),
-                                                    dim3(kBatchThreads), args, (size_t)smem, st);
+  if (!opts->fp64_only) {  // set-up, features and the single-precision stage
+    a.smem_bytes = smem;
+    if (cudaLaunchCooperativeKernel((const void*)k_batch<1>, dim3(grid), dim3(kBatchThreads), args,
+                                    (size_t)smem, st) != cudaSuccess)
+      return MPCG_ERR_CUDA;
+    // fresh barriers and queues for the second launch; an abort stays set
+    if (cudaMemsetAsync(Hd, 0, offsetof(BatchHdr, qbase), st) != cudaSuccess) return MPCG_ERR_CUDA;
+  }
+  a.smem_bytes = smem2;
+  a.part = opts->fp64_only ? 0 : 2;
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_batch<2>, dim3(grid),
+                                                    dim3(kBatchThreads), args, (size_t)smem2, st);
   return e == cudaSuccess ? MPCG_OK : MPCG_ERR_CUDA;
 }
 

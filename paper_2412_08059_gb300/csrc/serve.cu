@@ -64,7 +64,7 @@ __device__ bool slot_features(Team& t, const BatchSys& s, const BatchArgs& a, in
   if (!team_pseudo_diameter(t, s, a.smem_bytes)) return false;
   if (!team_sync(t)) return false;
   bool done;
-  if (!sys_cg32(t, s, kCgK0, red, kNoBudget, &done)) return false;
+  if (!sys_cg32<false>(t, s, kCgK0, red, kNoBudget, &done)) return false;
   if (!team_sync(t)) return false;
   if (sys_status(s) == 0 && t.rank == 0 && threadIdx.x < 32) {
     const double chi[4] = {(double)s.n, (double)s.nnz, (double)ctl->pdiam, ctl->v};
@@ -103,12 +103,12 @@ __device__ bool slot_advance(Team& t, const BatchSys& s, int* phase_p, const Bat
       if (!slot_features(t, s, a, red)) return false;
       ph = sys_status(s) != 0 ? kPhDone : kPhStage1;
     } else {
-      if (!sys_cg32(t, s, kCgToEps1, red, budget, &done)) return false;
+      if (!sys_cg32<false>(t, s, kCgToEps1, red, budget, &done)) return false;
       if (!team_sync(t)) return false;
       ph = sys_status(s) != 0 ? kPhDone : (done ? kPhStage2Start : kPhStage1);
     }
   } else if (ph == kPhStage1) {
-    if (!sys_cg32(t, s, kCgContinue, red, budget, &done)) return false;
+    if (!sys_cg32<false>(t, s, kCgContinue, red, budget, &done)) return false;
     if (!team_sync(t)) return false;
     ph = sys_status(s) != 0 ? kPhDone : (done ? kPhStage2Start : kPhStage1);
   }
@@ -236,7 +236,7 @@ extern "C" int32_t mpcg_server_create(void* ws, size_t ws_bytes, int32_t max_slo
   const int auto_eps1 = !opts->fp64_only && !(opts->eps1 > 0.0);
   if (auto_eps1 && !sample_ok(sample)) return MPCG_ERR_INVALID_ARG;
   if (!ws || ((uintptr_t)ws & 255u) || ws_bytes <= fixed_bytes(max_slots)) return MPCG_ERR_WORKSPACE;
-  const int smem = team_smem((const void*)k_serve, auto_eps1);
+  const int smem = team_smem((const void*)k_serve, !opts->fp64_only);
   if (smem < 0) return MPCG_ERR_CUDA;
   const int grid = persistent_grid((const void*)k_serve, kBatchThreads, opts->grid_blocks,
                                    (size_t)smem);

@@ -25,7 +25,18 @@ constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kTeamClasses = 8;                // team sizes 1, 2, 4, ..., 128 blocks
 constexpr int kRowsPerBlock = 16384;           // planner default: target rows per block of a team
 constexpr int kNoBudget = 0x7fffffff;          // iteration budget of a run-to-completion call
-constexpr int kTeamBfsSmem = 96 * 1024;        // dynamic shared memory of a launch that runs the 2BFS
+constexpr int kTeamFastW = 8;                  // widest slice whose pairs the SpMV stages
+constexpr int kSpmvStep = 2;                   // slices per SpMV step (their gathers overlap)
+constexpr int kStageWarpBytes = 2 * kSpmvStep * kSlice * kTeamFastW * (4 + 4);  // two float stages
+constexpr int kBScanPer = 8;                   // slice widths per thread in the block scan
+constexpr int kBScanTile = kBatchThreads * kBScanPer;
+constexpr int kScanSmem = kBScanTile * 4 + kBatchThreads * 8;  // the scan's tile and partials
+// Dynamic shared memory of a team launch: the scan at set-up; with a
+// single-precision stage also the SpMV stages and the block-local 2BFS.
+// 128 KB plus the static part keeps the 132 KB shared-memory carve-out, so
+// the L1 cache keeps 124 KB of the 256 KB.
+constexpr int kTeamSmem = kBatchWarps * kStageWarpBytes;
+static_assert(kTeamSmem >= kScanSmem, "scan buffer");
 constexpr int kBlockBfsMaxN = 1 << 18;         // larger systems run the 2BFS over the whole team
 
 // One system of the batch (device copy written by the host).
@@ -61,6 +72,7 @@ struct BatchArgs {
   mpcg_options_t o;
   int auto_eps1;
   int smem_bytes;  // dynamic shared memory of the launch (0: none)
+  int part;        // batch launches: 1 = set-up to the single-precision stage, 2 = the rest
 };
 
 // ---------------------------------------------------------------------------------------
@@ -276,12 +288,11 @@ static __device__ void sys_rows(const Team& t, const BatchSys& s) {
   }
 }
 
-// Exclusive scan of 32 * width over the slices, by one block.
-constexpr int kBScanPer = 8;
-constexpr int kBScanTile = kBatchThreads * kBScanPer;
+// Exclusive scan of 32 * width over the slices, by one block (tile and
+// partials in the launch's dynamic shared memory).
 static __device__ void block_scan_slices(const uint32_t* slice_w, int32_t* slice_ptr, int nslices) {
-  __shared__ int32_t tile[kBScanTile];
-  __shared__ long long part[kBatchThreads];
+  int32_t* tile = reinterpret_cast<int32_t*>(team_dyn);
+  long long* part = reinterpret_cast<long long*>(team_dyn + kBScanTile * 4);
   __shared__ long long carry_s;
   const int t = threadIdx.x;
   if (t == 0) carry_s = 0;
@@ -373,15 +384,140 @@ __device__ __forceinline__ T btail(const BatchSys& s, int i, int w, T acc, Gathe
 __device__ __forceinline__ int team_warp(const Team& t);
 __device__ __forceinline__ int team_warps(const Team& t);
 
-// SpMV over the team's slices: warp gw owns slices gw, gw + W, ...; lane l
+// Asynchronous 16-byte global -> shared copies (cached in L2 only), in
+// per-thread groups: a thread waits for its own groups, then a __syncwarp
+// makes every lane's copies visible to the warp.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copy one slice's (column, value) pairs -- 32 w contiguous elements from
+// element p0 (a multiple of 32, so every 16-byte copy is aligned) -- into a
+// warp's stage.
+template <typename T>
+__device__ __forceinline__ void stage_slice(int32_t* cdst, T* vdst, const int32_t* sc, const T* sv,
+                                            int p0, int w, int lane) {
+  const int E = kSlice * w;
+  for (int q = lane; q < E / 4; q += 32) cp_async16(cdst + 4 * q, sc + p0 + 4 * q);
+  constexpr int per = 16 / (int)sizeof(T);
+  for (int q = lane; q < E / per; q += 32) cp_async16(vdst + per * q, sv + p0 + per * q);
+}
+
+// SpMV over the team's slices, pairs staged in shared memory (the single-
+// precision stage): warp gw owns slices gw, gw + W, ...; lane l owns row
+// 32 s + l.  Rw(i, acc, own) receives row i's sum in stored order (fused
+// multiply-adds from zero, padding rows included) and the row's own values
+// that P(i) loaded before the gathers (P gets i >= n for absent rows).
+//
+// The slices are taken kS at a time (a step).  The (column, value) pairs of
+// the next step's slices are copied into the warp's shared-memory stage
+// (two stages per warp in the launch's dynamic shared memory) while the
+// current step runs, so a step costs one round trip for its gathers: the
+// pairs come from shared memory and every gather of a row is issued at once.
+// Slices wider than kTeamFastW, or with an overflow tail, read their pairs
+// from global memory instead.  The metadata of 32 of the warp's slices is
+// loaded at once (one slice per lane).
+template <typename T, class Gather, class Pre, class Row>
+__device__ __forceinline__ void team_spmv_staged(const Team& t, const BatchSys& s, Gather G, Pre P,
+                                                 Row Rw) {
+  static_assert(sizeof(T) == 4, "the stages hold 4-byte values");
+  constexpr int kS = kSpmvStep;
+  constexpr int kE = kSlice * kTeamFastW;      // elements of a staged slice
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = team_warp(t), W = team_warps(t);
+  const T* sv = bvals<T>(s);
+  const int32_t* sc = s.w.scol;
+  int32_t* cbuf = reinterpret_cast<int32_t*>(team_dyn + warp * kStageWarpBytes);  // [2][kS][kE]
+  T* vbuf = reinterpret_cast<T*>(cbuf + 2 * kS * kE);                             // [2][kS][kE]
+  for (int base = gw; base < s.nslices; base += 32 * W) {
+    const int mine = base + lane * W;
+    uint32_t mwf = 0u;
+    int mp = 0;
+    if (mine < s.nslices) {
+      mwf = s.w.slice_w[mine];
+      mp = s.w.slice_ptr[mine];
+    }
+    const int cnt = min(32, (s.nslices - base + W - 1) / W);
+    const int nsteps = (cnt + kS - 1) / kS;
+    auto issue = [&](int step) {  // the copies of a step, into stage step & 1
+#pragma unroll
+      for (int u = 0; u < kS; ++u) {
+        const int jj = step * kS + u;
+        if (jj < cnt) {  // warp-uniform
+          const uint32_t wf = __shfl_sync(full, mwf, jj);
+          const int pp = __shfl_sync(full, mp, jj);
+          const int w = (int)(wf & ~kOverflowBit);
+          if (!(wf & kOverflowBit) && w <= kTeamFastW) {
+            const int slot = ((step & 1) * kS + u) * kE;
+            stage_slice<T>(cbuf + slot, vbuf + slot, sc, sv, pp, w, lane);
+          }
+        }
+      }
+      cp_async_commit();
+    };
+    issue(0);
+    for (int step = 0; step < nsteps; ++step) {
+      if (step + 1 < nsteps) issue(step + 1);
+      else cp_async_commit();  // an empty group keeps the count: wait<1> below covers `step`
+      int w[kS], p[kS], i[kS];
+      uint32_t wf[kS];
+      T a[kS];
+      decltype(P(0)) own[kS];
+#pragma unroll
+      for (int u = 0; u < kS; ++u) {
+        const int jj = step * kS + u;
+        const int ju = min(jj, 31);
+        wf[u] = __shfl_sync(full, mwf, ju);
+        p[u] = __shfl_sync(full, mp, ju) + lane;
+        w[u] = jj < cnt ? (int)(wf[u] & ~kOverflowBit) : 0;
+        i[u] = (base + jj * W) * kSlice + lane;
+        a[u] = (T)0;
+        // the rows' own values, loaded before the gathers (the row callbacks
+        // store, and later loads could not be moved above those stores)
+        own[u] = P(jj < cnt ? i[u] : s.n);
+      }
+      cp_async_wait<1>();
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < kS; ++u) {
+        if (!(wf[u] & kOverflowBit) && w[u] <= kTeamFastW) {
+          const int slot = ((step & 1) * kS + u) * kE + lane;
+          const int32_t* cs = cbuf + slot;
+          const T* vs = vbuf + slot;
+#pragma unroll
+          for (int k = 0; k < kTeamFastW; ++k)
+            if (k < w[u]) a[u] = fma(vs[kSlice * k], G(cs[kSlice * k]), a[u]);
+        } else if (step * kS + u < cnt) {
+          for (int k = 0; k < w[u]; ++k) a[u] = fma(sv[p[u] + kSlice * k], G(sc[p[u] + kSlice * k]), a[u]);
+          if (i[u] < s.n) a[u] = btail<T>(s, i[u], w[u], a[u], G);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kS; ++u)
+        if (step * kS + u < cnt) Rw(i[u], a[u], own[u]);
+      __syncwarp();  // the stage is read before step + 2 copies into it
+    }
+    cp_async_wait<0>();
+  }
+}
+
+// SpMV over the team's slices, operands from global memory (the double-
+// precision stage): warp gw owns slices gw, gw + W, ...; lane l
 // owns row 32 s + l.  Rw(i, acc, own) receives row i's sum in stored order
 // (fused multiply-adds from zero, padding rows included) and the row's own
 // values that P(i) loaded before the gathers (P gets i >= n for absent rows).  The metadata of 32 of
 // the warp's slices is loaded at once (one slice per lane) and kU slices are
 // summed together so that their loads and gathers overlap.
 template <typename T, class Gather, class Pre, class Row>
-__device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gather G, Pre P,
-                                          Row Rw) {
+__device__ __forceinline__ void team_spmv_regs(const Team& t, const BatchSys& s, Gather G, Pre P,
+                                               Row Rw) {
   constexpr int kU = 4;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -434,6 +570,19 @@ __device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gath
   }
 }
 
+// The SpMV of the team kernels.  The single-precision stage stages its
+// pairs in shared memory; the double-precision stage loads them from global
+// memory: staged double pairs would need 12 bytes an element, and the shared
+// memory they take comes out of the L1 cache that the stage's gathers use
+// (measured on the 512-system batch: the FP64 stage lost more to the
+// smaller L1 than it gained from the staging).
+template <typename T, bool kStage, class Gather, class Pre, class Row>
+__device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gather G, Pre P,
+                                          Row Rw) {
+  if constexpr (kStage && sizeof(T) == 4) team_spmv_staged<T>(t, s, G, P, Rw);
+  else team_spmv_regs<T>(t, s, G, P, Rw);
+}
+
 __device__ __forceinline__ int team_warp(const Team& t) { return t.rank * kBatchWarps + (threadIdx.x >> 5); }
 __device__ __forceinline__ int team_warps(const Team& t) { return t.size * kBatchWarps; }
 
@@ -476,6 +625,7 @@ enum BDec { kBGo = 0, kBStop = 1, kBNan = 2, kBBroke = 3, kBBreakdown = 4, kBCap
 // control block.  Outside the k0 phase at most `budget` iterations run;
 // *done is false when the budget ended the call before the stage ended.
 // Returns false if the launch aborted.
+template <bool kStage>
 static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, int budget, bool* done) {
   *done = true;
   Ctl* ctl = s.w.ctl;
@@ -559,7 +709,7 @@ static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, 
     float* dnew = parity ? s.w.d32a : s.w.d32b;
     const float bt = first ? 0.0f : beta;
     FF pdq{0.f, 0.f};
-    team_spmv<float>(
+    team_spmv<float, kStage>(
         t, s, [&](int c) -> float { return __fmaf_rn(bt, dold[c], r[c]); },
         [&](int i) -> float2 { return i < n ? make_float2(dold[i], r[i]) : make_float2(0.f, 0.f); },
         [&](int i, float acc, float2 own) {
@@ -681,7 +831,7 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
     // restart (CG line 1 from x): r = b - A x, d = r, r^T r
     if (!skip_restart) {
     double p = 0.0;
-    team_spmv<double>(
+    team_spmv<double, false>(
         t, s, [&](int c) -> double { return x[c]; },
         [&](int i) -> double { return i < n ? b[i] : 0.0; },
         [&](int i, double acc, double bi) {
@@ -728,7 +878,7 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
       }
       // P1: q = A d, d^T q
       double pq = 0.0;
-      team_spmv<double>(
+      team_spmv<double, false>(
           t, s, [&](int c) -> double { return d[c]; },
           [&](int i) -> double { return i < n ? d[i] : 0.0; },
           [&](int i, double acc, double di) {
@@ -785,7 +935,7 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
     if (failed && failed != MPCG_ERR_NOT_CONVERGED) break;
     // true residual ||b - A x|| (also after the iteration cap)
     double pt = 0.0;
-    team_spmv<double>(
+    team_spmv<double, false>(
         t, s, [&](int c) -> double { return x[c]; },
         [&](int i) -> double { return i < n ? b[i] : 0.0; },
         [&](int i, double acc, double bi) {
@@ -918,9 +1068,9 @@ struct Plan {
 // n rows with estimated work `work` (largest first within a class); a system
 // goes to the smallest team with at most rows_per_block rows per block.
 Plan make_plan(int nsys, const int* n, const double* work, int grid, int rows_per_block);
-// Dynamic shared memory of a team launch of `kernel`: the block-local 2BFS
-// buffer when the launch computes features (auto_eps1), else none.  Raises
-// the kernel's limit on the current device; -1 on a CUDA error.
-int team_smem(const void* kernel, int auto_eps1);
+// Dynamic shared memory of a team launch of `kernel`: kTeamSmem when it runs
+// a single-precision stage (stage1 != 0), else only the scan's kScanSmem.
+// Raises the kernel's limit on the current device; -1 on a CUDA error.
+int team_smem(const void* kernel, int stage1);
 
 }  // namespace mpcg
