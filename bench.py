@@ -323,7 +323,7 @@ def batch_section(args, dev, steps, warmup):
                              "batch_fp64": bytes_fp64 / (ms_fp64 / 1e3) / 1e9},
         "fp64_TFLOPs_batch_fp64": flops64 / (ms_fp64 / 1e3) / 1e12,
         "failed_statuses": bad, "sample_seconds": round(t_sample, 1),
-        "kernels_per_batch": 1,
+        "kernels_per_batch": {"batch_mixed": 2, "batch_fp64": 1},
         "autotuned_team_rows": team_rows,
         "tuning_ms": dict(zip(("8192", "16384", "32768", "65536"), [round(x, 1) for x in tune_ms])),
     }

@@ -685,17 +685,16 @@ static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, 
   const double eps = mode == kCgK0 ? ctl->eps2 : ctl->eps1;
   const int limit = mode == kCgK0 ? min(ctl->k0, ctl->max1) : ctl->max1;
   const int it_start = it;
-  const StopThr thr = stop_thr(eps, bnorm, rel);  // used by thread 0
+  // Every thread holds the team sums (identical in every block), so every
+  // thread takes the loop's decisions itself, with no broadcast barrier.
+  const StopThr thr = stop_thr(eps, bnorm, rel);
   double vsum = 0.0;  // thread 0
   int k0done = 0, broke = 0, suspended = 0;
   while (true) {
     int dec = kBGo;
-    if (lead) {
-      if (isnan(rr)) dec = kBNan;
-      else if (stop_pass(thr, rr) || it >= limit || (mode == kCgK0 && rr == 0.0)) dec = kBStop;
-      else if (mode != kCgK0 && it - it_start >= budget) dec = kBSuspend;
-    }
-    dec = bcast_dec(t, dec);
+    if (isnan(rr)) dec = kBNan;
+    else if (stop_pass(thr, rr) || it >= limit || (mode == kCgK0 && rr == 0.0)) dec = kBStop;
+    else if (mode != kCgK0 && it - it_start >= budget) dec = kBSuspend;
     if (dec == kBSuspend) {
       suspended = 1;
       break;
@@ -723,12 +722,8 @@ static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, 
     double dq;
     if (!team_sum_ff(t, pdq, s.w.partials, red, dq)) return false;
     dec = kBGo;
-    if (lead) {
-      if (!isfinite(dq)) dec = kBNan;
-      else if (!(dq > 0.0)) dec = kBBroke;
-      else t.S->fval[0] = (float)(rr / dq);
-    }
-    dec = bcast_dec(t, dec);
+    if (!isfinite(dq)) dec = kBNan;
+    else if (!(dq > 0.0)) dec = kBBroke;
     if (dec == kBNan) {
       if (lead0) set_status(ctl, MPCG_ERR_NAN);
       break;
@@ -737,7 +732,7 @@ static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, 
       broke = 1;
       break;
     }
-    const float alpha = t.S->fval[0];
+    const float alpha = (float)(rr / dq);
     // P2: x += alpha d_k, r -= alpha q, r^T r
     FF prr{0.f, 0.f};
     team_rows(
@@ -750,21 +745,12 @@ static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, 
         });
     double rrn;
     if (!team_sum_ff(t, prr, s.w.partials, red, rrn)) return false;
-    dec = kBGo;
-    if (lead) {
-      if (!isfinite(rrn)) {
-        dec = kBNan;
-      } else {
-        if (mode == kCgK0) vsum += sqrt(rrn) / sqrt(rr);  // Eq. (13) ratio
-        t.S->fval[1] = (float)(rrn / rr);
-      }
-    }
-    dec = bcast_dec(t, dec);
-    if (dec == kBNan) {
+    if (!isfinite(rrn)) {
       if (lead0) set_status(ctl, MPCG_ERR_NAN);
       break;
     }
-    beta = t.S->fval[1];
+    if (lead && mode == kCgK0) vsum += sqrt(rrn) / sqrt(rr);  // Eq. (13) ratio
+    beta = (float)(rrn / rr);
     rr = rrn;
     if (mode == kCgK0) ++k0done;
     parity ^= 1;
