@@ -116,7 +116,10 @@ typedef struct {
   int32_t stage1_only;       /* 1: stop after the single-precision stage; x = float64(x~) */
   int32_t team_rows;         /* batch and server: target rows per block of a team, which sets
                                 the team size of each system (<= 0: 16384) */
-  int32_t reserved[3];
+  int32_t serve_split;       /* server, mixed precision: 1 = two launches per step (set-up,
+                                features and the single-precision stage with its SpMV staged in
+                                shared memory; then the FP64 stage); 0 = one launch (default) */
+  int32_t reserved[2];
 } mpcg_options_t;
 
 /* Result record, written by the device at the end of the call's work into

@@ -14,6 +14,7 @@
 // side by side, and requests admitted between steps join the next one.  The
 // host retires finished systems (freeing their slot and pool block) and
 // admits new ones between steps.
+#include <stddef.h>
 #include <string.h>
 
 #include <algorithm>
@@ -30,6 +31,7 @@ struct ServeArgs {
   BatchArgs b;
   int* phase;  // [max_slots]
   int budget;
+  int part;    // phases this launch advances (slot_advance)
 };
 
 // Set-up of a new system (as in the batched solve).  Returns false if the
@@ -59,12 +61,13 @@ __device__ bool slot_setup(Team& t, const BatchSys& s, const BatchArgs& a, int& 
 }
 
 // Algorithm II features: 2BFS, the k0 iterations and the kNN vote.
+template <bool kStage>
 __device__ bool slot_features(Team& t, const BatchSys& s, const BatchArgs& a, int& red) {
   Ctl* ctl = s.w.ctl;
   if (!team_pseudo_diameter(t, s, a.smem_bytes)) return false;
   if (!team_sync(t)) return false;
   bool done;
-  if (!sys_cg32<false>(t, s, kCgK0, red, kNoBudget, &done)) return false;
+  if (!sys_cg32<kStage>(t, s, kCgK0, red, kNoBudget, &done)) return false;
   if (!team_sync(t)) return false;
   if (sys_status(s) == 0 && t.rank == 0 && threadIdx.x < 32) {
     const double chi[4] = {(double)s.n, (double)s.nnz, (double)ctl->pdiam, ctl->v};
@@ -82,12 +85,19 @@ __device__ bool slot_features(Team& t, const BatchSys& s, const BatchArgs& a, in
   return team_sync(t);
 }
 
-// Advance one system by one step.  Returns false if the launch aborted.
+// Advance one system by one step.  part 0: every phase; part 1: set-up,
+// features and the single-precision stage only (a system that ends the stage
+// stops at kPhStage2Start); part 2: the double-precision stage only (the two
+// launches of a step with the serve_split option).
+// kStage: the single-precision SpMV staged in shared memory.  Returns false
+// if the launch aborted.
+template <bool kStage>
 __device__ bool slot_advance(Team& t, const BatchSys& s, int* phase_p, const BatchArgs& a,
-                             int budget) {
+                             int budget, int part) {
   Ctl* ctl = s.w.ctl;
   int ph = *reinterpret_cast<volatile int*>(phase_p);
   if (ph == kPhDone || ph < 0 || ph > kPhDone) return true;
+  if ((part == 1 && ph >= kPhStage2Start) || (part == 2 && ph < kPhStage2Start)) return true;
   int red = 0;
   bool done = true;
   if (ph == kPhNew) {
@@ -100,19 +110,19 @@ __device__ bool slot_advance(Team& t, const BatchSys& s, int* phase_p, const Bat
     } else if (a.o.fp64_only) {
       ph = kPhStage2Start;
     } else if (a.auto_eps1) {
-      if (!slot_features(t, s, a, red)) return false;
+      if (!slot_features<kStage>(t, s, a, red)) return false;
       ph = sys_status(s) != 0 ? kPhDone : kPhStage1;
     } else {
-      if (!sys_cg32<false>(t, s, kCgToEps1, red, budget, &done)) return false;
+      if (!sys_cg32<kStage>(t, s, kCgToEps1, red, budget, &done)) return false;
       if (!team_sync(t)) return false;
       ph = sys_status(s) != 0 ? kPhDone : (done ? kPhStage2Start : kPhStage1);
     }
   } else if (ph == kPhStage1) {
-    if (!sys_cg32<false>(t, s, kCgContinue, red, budget, &done)) return false;
+    if (!sys_cg32<kStage>(t, s, kCgContinue, red, budget, &done)) return false;
     if (!team_sync(t)) return false;
     ph = sys_status(s) != 0 ? kPhDone : (done ? kPhStage2Start : kPhStage1);
   }
-  if (ph == kPhStage2Start || ph == kPhStage2) {
+  if ((ph == kPhStage2Start || ph == kPhStage2) && part != 1) {
     const bool resume = ph == kPhStage2;
     if (!sys_cg64(t, s, a.o.fp64_only ? 1 : 0, red, budget, resume, &done)) return false;
     if (!team_sync(t)) return false;
@@ -124,6 +134,16 @@ __device__ bool slot_advance(Team& t, const BatchSys& s, int* phase_p, const Bat
   return true;
 }
 
+// One step over the admitted systems.  By default one launch of k_serve<2>
+// with part 0 advances every phase.  With the serve_split option a
+// mixed-precision server runs two launches per step:
+//   * k_serve<1>: set-up, features and the single-precision stage, with the
+//     SpMV staged in shared memory;
+//   * k_serve<2> with part 2: the double-precision stage.
+// Measured on the serving mix at 300 requests/s, the split has cheaper FP32
+// iterations, but a step then costs both launches in sequence. The median
+// latency rose from 19 to 30 ms, so the split is off by default.
+template <int kPart>
 __global__ void __launch_bounds__(kBatchThreads, 1) k_serve(ServeArgs sa) {
   __shared__ TeamShared S;
   const BatchArgs& a = sa.b;
@@ -142,7 +162,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_serve(ServeArgs sa) {
     if (!team_sync(t)) return;
     const int idx = *reinterpret_cast<volatile int*>(&a.h->next[t.team]);
     if (idx < 0) return;
-    if (!slot_advance(t, a.sys[idx], sa.phase + idx, a, sa.budget)) return;
+    if (!slot_advance<kPart == 1>(t, a.sys[idx], sa.phase + idx, a, sa.budget, sa.part)) return;
     if (!team_sync(t)) return;
   }
 }
@@ -187,7 +207,7 @@ struct mpcg_server {
   KnnSpec knn;
   int auto_eps1;
   int grid;
-  int smem;  // dynamic shared memory of each step launch
+  int smem, smem2;  // dynamic shared memory of the two launches of a step
 };
 
 namespace {
@@ -236,9 +256,10 @@ extern "C" int32_t mpcg_server_create(void* ws, size_t ws_bytes, int32_t max_slo
   const int auto_eps1 = !opts->fp64_only && !(opts->eps1 > 0.0);
   if (auto_eps1 && !sample_ok(sample)) return MPCG_ERR_INVALID_ARG;
   if (!ws || ((uintptr_t)ws & 255u) || ws_bytes <= fixed_bytes(max_slots)) return MPCG_ERR_WORKSPACE;
-  const int smem = team_smem((const void*)k_serve, !opts->fp64_only);
-  if (smem < 0) return MPCG_ERR_CUDA;
-  const int grid = persistent_grid((const void*)k_serve, kBatchThreads, opts->grid_blocks,
+  const int smem = team_smem((const void*)k_serve<1>, 1);
+  const int smem2 = team_smem((const void*)k_serve<2>, 1);
+  if (smem < 0 || smem2 < 0) return MPCG_ERR_CUDA;
+  const int grid = persistent_grid((const void*)k_serve<1>, kBatchThreads, opts->grid_blocks,
                                    (size_t)smem);
   if (grid <= 0) return MPCG_ERR_CUDA;
   mpcg_server* s = new mpcg_server();
@@ -259,6 +280,7 @@ extern "C" int32_t mpcg_server_create(void* ws, size_t ws_bytes, int32_t max_slo
   if (auto_eps1) s->knn = knn_spec(*sample, *opts);
   s->grid = grid;
   s->smem = smem;
+  s->smem2 = smem2;
   *out = s;
   return MPCG_OK;
 }
@@ -356,17 +378,30 @@ extern "C" int32_t mpcg_batch_step(mpcg_server_t* s, int32_t max_iters, int32_t*
     a.team_class = put(P.team_class, kMaxGrid);
     a.o = s->o;
     a.auto_eps1 = s->auto_eps1;
-    a.smem_bytes = s->smem;
     a.knn = s->knn;
     if (cudaMemcpyAsync(s->dev, m, s->mirror.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
       return MPCG_ERR_CUDA;
     ServeArgs sa{};
-    sa.b = a;
     sa.phase = s->phase_d;
     sa.budget = max_iters;
     void* args[] = {&sa};
-    if (cudaLaunchCooperativeKernel((const void*)k_serve, dim3(s->grid), dim3(kBatchThreads), args,
-                                    (size_t)s->smem, st) != cudaSuccess)
+    const bool split = s->o.serve_split && !s->o.fp64_only;
+    if (split) {  // set-up, features, single-precision stage
+      a.smem_bytes = s->smem;
+      sa.b = a;
+      sa.part = 1;
+      if (cudaLaunchCooperativeKernel((const void*)k_serve<1>, dim3(s->grid), dim3(kBatchThreads),
+                                      args, (size_t)s->smem, st) != cudaSuccess)
+        return MPCG_ERR_CUDA;
+      // fresh barriers and queues for the second launch; an abort stays set
+      if (cudaMemsetAsync(s->dev, 0, offsetof(BatchHdr, qbase), st) != cudaSuccess)
+        return MPCG_ERR_CUDA;
+    }
+    a.smem_bytes = s->smem2;
+    sa.b = a;
+    sa.part = split ? 2 : 0;
+    if (cudaLaunchCooperativeKernel((const void*)k_serve<2>, dim3(s->grid), dim3(kBatchThreads),
+                                    args, (size_t)s->smem2, st) != cudaSuccess)
       return MPCG_ERR_CUDA;
   }
   if (slot_phase &&

@@ -82,7 +82,9 @@ def serve(mp, srv, reqs, waves, max_iters, max_steps=100000):
     raise AssertionError("requests did not finish")
 
 
-@pytest.mark.parametrize("kw", [dict(), dict(eps1=1e-4)], ids=["alg2", "alg1"])
+@pytest.mark.parametrize("kw", [dict(), dict(eps1=1e-4), dict(serve_split=1),
+                                dict(eps1=1e-4, serve_split=1)],
+                         ids=["alg2", "alg1", "alg2-split", "alg1-split"])
 def test_serve_same_alone_and_in_mix(mp, kw):
     reqs_mix = requests(mp)
     reqs_alone = requests(mp)
@@ -106,8 +108,8 @@ def test_serve_same_alone_and_in_mix(mp, kw):
         assert close_count(a["n1"], m["n1"]) and close_count(a["n2"], m["n2"])
         assert np.linalg.norm(xa - xm) <= 1e-6 * np.linalg.norm(xa)
         # and the oracle
-        if kw:
-            xo, ro = oracle.solve(rm.A, rm.b, **kw)
+        if "eps1" in kw:
+            xo, ro = oracle.solve(rm.A, rm.b, eps1=kw["eps1"])
         else:
             xo, ro = oracle.solve(rm.A, rm.b, S=(feat, cls))
             assert m["cls"] == ro["cls"] and m["pdiam"] == ro["pdiam"]
