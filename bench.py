@@ -450,7 +450,7 @@ def serve_section(args, dev):
             out["queue_wait_ms_mean"] = float(((adm_t - arrivals) * 1e3).mean())
         if steps is not None:
             out["steps"] = steps
-            out["gpu_launches"] = steps
+            out["gpu_launches"] = 2 * steps  # the step kernel and the abort check after it
         if res is not None:
             out["failed"] = int(sum(r["status"] < 0 for r in res))
             out["max_true_rel_resid_over_eps2"] = float(max(r["true_rel_resid"] / e for r, e in zip(res, req_e)))

@@ -199,7 +199,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
   t.S = &S;
   const int cls = a.team_class[t.team];
   for (;;) {
-    if (t.rank == 0 && threadIdx.x == 0) a.h->next[t.team] = batch_take(a.h, a.order, cls);
+    // A team barrier sees the abort flag only when it has to wait, so the
+    // leader also checks it before taking the next system.
+    if (t.rank == 0 && threadIdx.x == 0)
+      a.h->next[t.team] =
+          *reinterpret_cast<volatile int*>(&a.h->abort) ? -1 : batch_take(a.h, a.order, cls);
     if (!team_sync(t)) return;
     const int idx = *reinterpret_cast<volatile int*>(&a.h->next[t.team]);
     if (idx < 0) return;
@@ -435,6 +439,18 @@ extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const dou
   }
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemcpyAsync(dev, blob.data(), hdr, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return MPCG_ERR_CUDA;
+  // Every record starts as MPCG_ERR_TIMEOUT: a system that the launch leaves
+  // unfinished after a team barrier timed out (the launch aborts) reports
+  // that instead of the record's earlier contents.
+  std::vector<mpcg_result_t> pre((size_t)nsys);
+  memset(pre.data(), 0, sizeof(mpcg_result_t) * (size_t)nsys);
+  for (auto& r : pre) {
+    r.status = MPCG_ERR_TIMEOUT;
+    r.cls = -1;
+  }
+  if (cudaMemcpyAsync(res, pre.data(), sizeof(mpcg_result_t) * (size_t)nsys, cudaMemcpyDefault,
+                      st) != cudaSuccess)
     return MPCG_ERR_CUDA;
   BatchArgs a{};
   a.h = Hd;

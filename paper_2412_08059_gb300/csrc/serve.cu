@@ -167,6 +167,26 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_serve(ServeArgs sa) {
   }
 }
 
+// After a step (same stream): if the step aborted (a team barrier timed out),
+// every system of the step that is not done ends as timed out, with its
+// result record written.  A team that aborted may have left a system's
+// vectors part-way through an update that its saved state does not
+// describe, and which teams did is not recorded, so every unfinished system
+// of the step fails.  A kernel of its own, so that the step kernel's code is
+// not changed by it (its schedule moved by 5-8 % with such code inside).
+__global__ void k_serve_abort(const BatchHdr* h, const BatchSys* sys, const int* order, int count,
+                              int* phase) {
+  if (threadIdx.x != 0 || !*reinterpret_cast<const volatile int*>(&h->abort)) return;
+  Team t0{};  // rank 0: sys_finalize writes from thread 0 of rank 0
+  for (int j = 0; j < count; ++j) {
+    const int i = order[j];
+    if (phase[i] == kPhDone) continue;
+    set_status(sys[i].w.ctl, MPCG_ERR_TIMEOUT);
+    sys_finalize(t0, sys[i]);
+    phase[i] = kPhDone;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Host: the server (slot table, device pool, per-step plan and launch).
 // ---------------------------------------------------------------------------------------
@@ -403,6 +423,8 @@ extern "C" int32_t mpcg_batch_step(mpcg_server_t* s, int32_t max_iters, int32_t*
     if (cudaLaunchCooperativeKernel((const void*)k_serve<2>, dim3(s->grid), dim3(kBatchThreads),
                                     args, (size_t)s->smem2, st) != cudaSuccess)
       return MPCG_ERR_CUDA;
+    k_serve_abort<<<1, 32, 0, st>>>(a.h, a.sys, a.order, (int)ids.size(), s->phase_d);
+    if (cudaGetLastError() != cudaSuccess) return MPCG_ERR_CUDA;
   }
   if (slot_phase &&
       cudaMemcpyAsync(slot_phase, s->phase_d, sizeof(int) * (size_t)s->max_slots,

@@ -190,3 +190,39 @@ def test_batch_tune_picks_a_candidate_and_results_hold(mp):
     for A, b, x, r in zip(mats, bs, xs2, rs):
         xo, ro = oracle.solve(A, b, eps1=1e-4)
         parity(r, ro, x, xo)
+
+
+def test_batch_abort_reports_timeout_not_stale_records(mp):
+    """A team barrier that times out aborts the launch.  The 2e5-vertex path
+    is solved by a team of 32 blocks (8192 rows per block); its first block
+    runs the block-local 2BFS (2e5 levels, tens of ms) while the other 31
+    wait at the team barrier, past a 5 ms limit (the other systems are
+    one-block teams, whose barriers cannot time out).  The records were first filled by a
+    successful run, so a stale record would read as a success: every record
+    must read either MPCG_ERR_TIMEOUT or a solve that matches the oracle.  The
+    context stays usable."""
+    mats = [synth.path(200000)] + [synth.laplacian_2d(30 + 3 * i, 20) for i in range(6)]
+    bs = [synth.rhs(A, seed=140 + i)[1] for i, A in enumerate(mats)]
+    feat, cls = sample_over(mats, seed=5)
+    S = mp.DeviceSample(feat, cls)
+    dmats = [mp.DeviceCSR.from_host(A) for A in mats]
+    dbs = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in bs]
+    xs = [torch.empty(A.n, dtype=torch.float64, device="cuda") for A in mats]
+    ws = torch.empty(mp.batch_workspace_bytes(dmats), dtype=torch.uint8, device="cuda")
+    res = mp.result_buffer(len(mats))
+
+    def run(**kw):
+        mp.solve_batch_async(dmats, dbs, xs, mp.options(team_rows=8192, **kw), ws, res, S)
+        torch.cuda.synchronize()
+        return mp.read_results(res, len(mats))
+
+    assert all(r["status"] >= 0 for r in run())
+    rs = run(timeout_ms=5)
+    assert rs[0]["status"] == mp.ERR_TIMEOUT
+    for A, b, x, r in zip(mats, bs, xs, rs):
+        assert r["status"] in (mp.ERR_TIMEOUT, mp.OK, mp.WARN_EPS1_NOT_REACHED), r["status"]
+        if r["status"] >= 0:
+            xo, ro = oracle.solve(A, b, S=(feat, cls))
+            parity(r, ro, x.cpu().numpy(), xo)
+    rs = run()  # same workspace, default limit
+    assert all(r["status"] >= 0 and r["true_rel_resid"] <= 1e-10 for r in rs)

@@ -170,3 +170,30 @@ def test_serve_per_request_eps2_and_fp64(mp):
         assert m["true_rel_resid"] <= r.eps2
         assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
     assert reqs[0].result(mp)[1]["n2"] < reqs[1].result(mp)[1]["n2"]
+
+
+def test_serve_abort_ends_the_system_as_timed_out(mp):
+    """A step that aborts (a team barrier timed out) ends the system its team
+    was working on as MPCG_ERR_TIMEOUT, phase done, result written.  The
+    2e5-vertex path goes to a team of 32 blocks (8192 rows per block); its
+    first block runs the block-local 2BFS (2e5 levels, tens of ms) while the
+    other 31 wait at the team barrier past a 5 ms limit.  Requests admitted
+    after that step (one-block teams, whose barriers cannot time out) are
+    served normally and match the oracle."""
+    P = synth.path(200000)
+    path = Request(mp, P, synth.rhs(P, seed=401)[1])
+    later = requests(mp)[:4]
+    feat, cls = sample_over([r.A for r in later] + [path.A])
+    S = mp.DeviceSample(feat, cls)
+    pool = 4 * sum(mp.workspace_bytes(r.A.n, r.A.nnz) for r in later + [path])
+    srv = mp.Server(16, pool, mp.options(team_rows=8192, timeout_ms=5), S)
+    serve(mp, srv, [path] + later, [[path], later], max_iters=13)
+    srv.close()
+    _, rp = path.result(mp)
+    assert rp["status"] == mp.ERR_TIMEOUT
+    for r in later:
+        x, m = r.result(mp)
+        xo, ro = oracle.solve(r.A, r.b, S=(feat, cls))
+        assert m["status"] == ro["status"] and m["cls"] == ro["cls"]
+        assert close_count(m["n1"], ro["n1"]) and close_count(m["n2"], ro["n2"])
+        assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
