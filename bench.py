@@ -61,7 +61,27 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving section")
     ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--paper-eval", type=float, default=0.0,
+                    help="run the paper's evaluation protocol (Sec. 12) at this fraction of its "
+                         "general-sample sizes (0: skip)")
+    ap.add_argument("--paper-eval-splits", type=int, default=100)
+    ap.add_argument("--paper-eval-only", action="store_true",
+                    help="run only the evaluation protocol")
     return ap.parse_args()
+
+
+def paper_eval_section(args):
+    """The evaluation protocol of Sec. 12 (paper_2412_08059_gb300/evaluate.py) on
+    regenerated general samples of the three matrix families of Appendix A:
+    labels from the GPU eps1 sweep, N_S from Eq. (26), random splits, kNN
+    accuracy, localization and the efficiencies of Eq. (27)."""
+    from paper_2412_08059_gb300 import evaluate
+    t = time.time()
+    res = evaluate.run(scale=args.paper_eval, splits=args.paper_eval_splits,
+                       log=lambda m: print(m, file=sys.stderr, flush=True))
+    return {"scale_of_paper_sample_sizes": args.paper_eval, "splits": args.paper_eval_splits,
+            "features": "(m, l~, v), weighted kNN", "seconds": round(time.time() - t, 1),
+            "samples": res}
 
 
 def workload_config(size):
@@ -498,6 +518,11 @@ def native_arm(args, rank, world, local_rank):
         if rank == 0:
             print(json.dumps({"serve": serve_section(args, dev)}), flush=True)
         return
+    if args.paper_eval_only:
+        if rank == 0:
+            args.paper_eval = args.paper_eval or 0.1
+            print(json.dumps({"paper_eval": paper_eval_section(args)}), flush=True)
+        return
 
     def barrier():
         if world > 1:
@@ -770,6 +795,9 @@ def native_arm(args, rank, world, local_rank):
     serve = None
     if not args.no_serve and rank == 0 and world == 1:
         serve = serve_section(args, dev)
+    paper = None
+    if args.paper_eval > 0 and rank == 0 and world == 1:
+        paper = paper_eval_section(args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -789,6 +817,7 @@ def native_arm(args, rank, world, local_rank):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": KERNELS_PER_SOLVE_AUTO * nsys * args.steps,
                 "clocks": clocks, "systems": per, "eps1_sweep": sweep, "batch": batch, "serve": serve,
+                "paper_eval": paper,
                 "sample": {"desc": sample_desc, "seconds_to_build": round(t_sample, 1),
                            "labels": np.bincount(cls, minlength=8)[2:].tolist()}}
         print(json.dumps(line), flush=True)

@@ -167,6 +167,20 @@ int32_t mpcg_choose_eps1(const mpcg_features_t* f, const mpcg_sample_t* sample,
                          const mpcg_options_t* opts, double* eps1_out, int32_t* cls_out,
                          mpcg_stream_t stream);
 
+/* The same kNN vote for many queries in one launch (classifying the test set
+ * of the evaluation protocol of Sec. 12), one warp per query.  chi: device,
+ * double[count][4], raw feature vectors (n, m, l~, v) as mpcg_features_t
+ * gives them; cls_out: device int32[count], class t of each query, or -1 for
+ * an invalid query (a non-finite selected feature).  nbr_out: device
+ * int32[count][opts->knn_k], nullable: the indices of the query's nearest
+ * sample points in selection order ((squared distance, index) ascending),
+ * -1 past the sample's size -- what the localization measure of Sec. 11.4
+ * counts.  count = 0 launches nothing.  MPCG_ERR_INVALID_ARG on a bad sample,
+ * options or pointer. */
+int32_t mpcg_knn_batch(const mpcg_sample_t* sample, const double* chi, int32_t count,
+                       const mpcg_options_t* opts, int32_t* cls_out, int32_t* nbr_out,
+                       mpcg_stream_t stream);
+
 /* The method (Algorithm II, or Algorithm I when opts->eps1 > 0, or pure FP64
  * CG when opts->fp64_only): x (device, float64[n]) receives the solution;
  * its input value is ignored (x0 = 0).  sample: required by Algorithm II,

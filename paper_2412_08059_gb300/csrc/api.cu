@@ -135,6 +135,15 @@ int32_t mpcg_choose_eps1(const mpcg_features_t* f, const mpcg_sample_t* sample,
                                 eps1_out, cls_out));
 }
 
+int32_t mpcg_knn_batch(const mpcg_sample_t* sample, const double* chi, int32_t count,
+                       const mpcg_options_t* opts, int32_t* cls_out, int32_t* nbr_out,
+                       mpcg_stream_t stream) {
+  if (count < 0 || (count > 0 && (!chi || !cls_out)) || !options_ok(opts) || !sample_ok(sample))
+    return MPCG_ERR_INVALID_ARG;
+  return cuda_status(launch_knn_batch((cudaStream_t)stream, *sample, *opts, chi, count, cls_out,
+                                      nbr_out));
+}
+
 int32_t mpcg_solve(const mpcg_csr_t* A, const double* b, double* x, const mpcg_sample_t* sample,
                    const mpcg_options_t* opts, void* ws, size_t ws_bytes, mpcg_result_t* res,
                    mpcg_stream_t stream) {

@@ -64,5 +64,7 @@ const void* bfs_kernel();
 KnnSpec knn_spec(const mpcg_sample_t& S, const mpcg_options_t& o);
 cudaError_t launch_knn(cudaStream_t st, const double* feat4, const mpcg_sample_t& S,
                        const mpcg_options_t& o, Ctl* ctl, double* eps1_out, int32_t* cls_out);
+cudaError_t launch_knn_batch(cudaStream_t st, const mpcg_sample_t& S, const mpcg_options_t& o,
+                             const double* chi4, int count, int32_t* cls, int32_t* nbr);
 
 }  // namespace mpcg

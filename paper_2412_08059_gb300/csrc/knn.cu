@@ -51,6 +51,36 @@ KnnSpec knn_spec(const mpcg_sample_t& S, const mpcg_options_t& o) {
   return s;
 }
 
+// Many queries (the classification of a test set, Sec. 12): one warp per
+// query, grid-stride.  chi: [count][4]; cls: [count]; nbr: [count][k] or null.
+__global__ void k_knn_batch(KnnSpec s, const double* chi4, int count, int32_t* cls,
+                            int32_t* nbr) {
+  const int warps = (int)(gridDim.x * blockDim.x) >> 5;
+  const int w0 = (int)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int qi = w0; qi < count; qi += warps) {  // warp-uniform
+    double chi[4];
+    for (int c = 0; c < 4; ++c) chi[c] = chi4[4 * (size_t)qi + c];
+    const int t = knn_warp(s, chi);
+    if ((threadIdx.x & 31) == 0) cls[qi] = t;
+    if (nbr && !knn_neighbours_warp(s, chi, nbr + (size_t)qi * s.k) && (threadIdx.x & 31) == 0)
+      for (int j = 0; j < s.k; ++j) nbr[(size_t)qi * s.k + j] = -1;
+  }
+}
+
+cudaError_t launch_knn_batch(cudaStream_t st, const mpcg_sample_t& S, const mpcg_options_t& o,
+                             const double* chi4, int count, int32_t* cls, int32_t* nbr) {
+  if (count <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorUnknown;
+  const int threads = 256;                                   // 8 queries per block at a time
+  const int need = (count + threads / 32 - 1) / (threads / 32);
+  const int grid = need < 8 * sms ? need : 8 * sms;
+  k_knn_batch<<<grid, threads, 0, st>>>(knn_spec(S, o), chi4, count, cls, nbr);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_knn(cudaStream_t st, const double* feat4, const mpcg_sample_t& S,
                        const mpcg_options_t& o, Ctl* ctl, double* eps1_out, int32_t* cls_out) {
   k_knn<<<1, 32, 0, st>>>(knn_spec(S, o), ctl, feat4, eps1_out, cls_out);

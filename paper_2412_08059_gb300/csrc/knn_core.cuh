@@ -146,6 +146,55 @@ __device__ inline int knn_warp(const KnnSpec& s, const double chi[4]) {
   return result;
 }
 
+// The k nearest sample points of a query (the same selection as knn_warp:
+// the k smallest pairs (d2, index), in order), written to nbr[0..k) by lane
+// 0, with -1 past min(k, count).  Used to report the neighbours of a query
+// (the localization measure of Sec. 11.4); kept apart from knn_warp so that
+// the solve kernels that vote carry no code for it.  Returns false in every
+// lane if the query or the sample is invalid (nothing written).
+__device__ inline bool knn_neighbours_warp(const KnnSpec& s, const double chi[4], int* nbr) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  double q[4];
+  int bad = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (((s.mask >> c) & 1u) && !isfinite(chi[c])) bad = 1;
+    q[c] = knn_scale(chi[c], s.fmin[c], s.fmax[c]);
+  }
+  if (s.count <= 0 || s.k <= 0 || s.k > MPCG_KNN_MAX_K) bad = 1;
+  if (__any_sync(full, bad)) return false;
+  const int k = s.k < s.count ? s.k : s.count;
+  double last_d = -INFINITY;
+  int last_i = -1;
+  for (int j = 0; j < k; ++j) {
+    double bd = INFINITY;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < s.count; i += 32) {
+      const double d = knn_d2(s, q, i);
+      if (knn_pair_less(last_d, last_i, d, i) && knn_pair_less(d, i, bd, bi)) {
+        bd = d;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double od = __shfl_xor_sync(full, bd, o);
+      const int oi = __shfl_xor_sync(full, bi, o);
+      if (knn_pair_less(od, oi, bd, bi)) {
+        bd = od;
+        bi = oi;
+      }
+    }
+    if (lane == 0) nbr[j] = bi;
+    last_d = bd;
+    last_i = bi;
+  }
+  if (lane == 0)
+    for (int j = k; j < s.k; ++j) nbr[j] = -1;
+  return true;
+}
+
 // eps1 = 10^-t as the correctly rounded decimal literal.
 __device__ __forceinline__ double pow10_neg(int t) {
   switch (t) {

@@ -85,7 +85,8 @@ SYMBOLS = ("mpcg_options_default", "mpcg_status_string", "mpcg_workspace_bytes",
            "mpcg_choose_eps1", "mpcg_solve", "mpcg_batch_workspace_bytes", "mpcg_solve_batch",
            "mpcg_spmv", "mpcg_bfs", "mpcg_pseudo_diameter", "mpcg_solve_static",
            "mpcg_server_workspace_bytes", "mpcg_server_create", "mpcg_server_destroy",
-           "mpcg_server_admit", "mpcg_batch_step", "mpcg_server_retire", "mpcg_batch_tune")
+           "mpcg_server_admit", "mpcg_batch_step", "mpcg_server_retire", "mpcg_batch_tune",
+           "mpcg_knn_batch")
 
 
 def load(path: str = LIB_PATH):
@@ -109,6 +110,8 @@ def load(path: str = LIB_PATH):
         L.mpcg_features.argtypes = [C.POINTER(CsrDesc), P, C.POINTER(Options), P, SZ, P, P]
         L.mpcg_choose_eps1.restype = I32
         L.mpcg_choose_eps1.argtypes = [P, C.POINTER(SampleDesc), C.POINTER(Options), P, P, P]
+        L.mpcg_knn_batch.restype = I32
+        L.mpcg_knn_batch.argtypes = [C.POINTER(SampleDesc), P, I32, C.POINTER(Options), P, P, P]
         L.mpcg_solve.restype = I32
         L.mpcg_solve.argtypes = [C.POINTER(CsrDesc), P, P, C.POINTER(SampleDesc),
                                  C.POINTER(Options), P, SZ, P, P]
@@ -281,6 +284,22 @@ def choose_eps1(feat4, sample: DeviceSample, **kw):
                                  _ptr(eps), _ptr(cls), _stream())
     _check(st, "mpcg_choose_eps1")
     return float(eps.item()), int(cls.item())
+
+
+def knn_batch(chi, sample: DeviceSample, neighbours: bool = False, stream=None, **kw):
+    """mpcg_knn_batch: the kNN vote for every row of chi ([count, 4] raw
+    features).  Returns the classes (int32 tensor, -1 for an invalid query)
+    and, with neighbours, the [count, knn_k] neighbour indices (-1 padded)."""
+    o = options(**kw)
+    q = torch.as_tensor(chi, dtype=torch.float64).reshape(-1, 4).to(sample.feat.device).contiguous()
+    count = q.shape[0]
+    cls = torch.empty(count, dtype=torch.int32, device=q.device)
+    nbr = (torch.empty((count, o.knn_k), dtype=torch.int32, device=q.device)
+           if neighbours else None)
+    st = load().mpcg_knn_batch(C.byref(sample.desc), _ptr(q), count, C.byref(o), _ptr(cls),
+                               _ptr(nbr), _stream(stream))
+    _check(st, "mpcg_knn_batch")
+    return (cls, nbr) if neighbours else cls
 
 
 def spmv(A: DeviceCSR, x: torch.Tensor, ws=None) -> torch.Tensor:
