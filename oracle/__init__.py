@@ -60,7 +60,8 @@ class Opts(C.Structure):
     _fields_ = [("eps1", C.c_double), ("eps2", C.c_double), ("k0", C.c_int32),
                 ("knn_k", C.c_int32), ("weighted", C.c_int32), ("tol_relative", C.c_int32),
                 ("max_it_fp32", C.c_int32), ("max_it_fp64", C.c_int32),
-                ("max_true_restarts", C.c_int32), ("feat_mask", C.c_uint32)]
+                ("max_true_restarts", C.c_int32), ("feat_mask", C.c_uint32),
+                ("bfs_starts", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -96,6 +97,8 @@ def lib():
             L.orc_bfs.restype = C.c_int32
             L.orc_pseudo_diameter.argtypes = [C.POINTER(Csr), C.POINTER(C.c_int32)]
             L.orc_pseudo_diameter.restype = C.c_int32
+            L.orc_pseudo_diameter_rep.argtypes = [C.POINTER(Csr), C.c_int32, C.POINTER(C.c_int32)]
+            L.orc_pseudo_diameter_rep.restype = C.c_int32
             L.orc_components.argtypes = [C.POINTER(Csr), P]
             L.orc_components.restype = C.c_int32
             L.orc_knn.argtypes = [P, C.POINTER(Sample), C.c_int32, C.c_int32, C.c_uint32, P, P]
@@ -231,10 +234,12 @@ def bfs(A, src):
     return dist, reached
 
 
-def pseudo_diameter(A, return_t=False):
+def pseudo_diameter(A, return_t=False, starts=1):
+    """2BFS pseudo-diameter (Sec. 6); starts > 1: the repeated 2BFS of the
+    remark there (the largest value over `starts` runs)."""
     h = csr(A)
     t = C.c_int32(-1)
-    ell = lib().orc_pseudo_diameter(C.byref(h.s), C.byref(t))
+    ell = lib().orc_pseudo_diameter_rep(C.byref(h.s), int(starts), C.byref(t))
     return (ell, t.value) if return_t else ell
 
 

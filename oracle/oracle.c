@@ -331,6 +331,33 @@ int32_t orc_pseudo_diameter(const orc_csr* A, int32_t* t_out) {
   return ell;
 }
 
+/* Repeated 2BFS (the remark of Sec. 6: running 2BFS from several start
+ * vertices and keeping the largest pseudo-diameter).  Reading: run 0 is
+ * orc_pseudo_diameter above; run r = 1 .. R-1 starts from s_r = floor(r n /
+ * R) and is one 2BFS inside the component of s_r (BFS from s_r, t_r = the
+ * smallest vertex at maximal distance, BFS from t_r, its largest distance).
+ * l~ is the largest value of the R runs.  R <= 1 is the single run. */
+int32_t orc_pseudo_diameter_rep(const orc_csr* A, int32_t R, int32_t* t_out) {
+  int32_t ell = orc_pseudo_diameter(A, t_out);
+  if (ell < 0 || R <= 1) return ell;
+  const int32_t n = A->n;
+  int32_t* d1 = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* d2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  if (!d1 || !d2) { free(d1); free(d2); return -1; }
+  for (int32_t r = 1; r < R; ++r) {
+    const int32_t s = (int32_t)(((int64_t)r * n) / R);
+    orc_bfs(A, s, d1);
+    int32_t far = -1, t = s;
+    for (int32_t v = 0; v < n; ++v)
+      if (d1[v] > far) { far = d1[v]; t = v; }
+    orc_bfs(A, t, d2);
+    for (int32_t v = 0; v < n; ++v)
+      if (d2[v] > ell) ell = d2[v];
+  }
+  free(d1); free(d2);
+  return ell;
+}
+
 /* ------------------------------------------------------------------------ */
 /* kNN classification (Sec. 11).                                             */
 /* ------------------------------------------------------------------------ */
@@ -421,6 +448,7 @@ orc_opts orc_opts_default(void) {
   o.max_it_fp64 = 0;
   o.max_true_restarts = 2;
   o.feat_mask = 0xFu;
+  o.bfs_starts = 1;
   return o;
 }
 
@@ -490,7 +518,7 @@ int32_t orc_features(const orc_csr* A, const double* b, const orc_opts* o,
     *k0_done = 0;
   feat[0] = (double)n;
   feat[1] = (double)A->nnz;
-  feat[2] = (double)orc_pseudo_diameter(A, NULL);
+  feat[2] = (double)orc_pseudo_diameter_rep(A, o->bfs_starts, NULL);
   feat[3] = v;
   cg32_free(&s);
   free(v32);
@@ -543,7 +571,7 @@ int32_t orc_solve(const orc_csr* A, const double* b, double* x,
     if (status != ORC_OK) goto done32;
     res->k0_done = k0_done;
     res->v = v;
-    res->pdiam = (double)orc_pseudo_diameter(A, NULL);
+    res->pdiam = (double)orc_pseudo_diameter_rep(A, o->bfs_starts, NULL);
     res->feat[0] = (double)n;
     res->feat[1] = (double)A->nnz;
     res->feat[2] = res->pdiam;

@@ -63,6 +63,7 @@ typedef struct {
   int32_t max_it_fp64;  /* cap on N2 (<= 0: 10 n) */
   int32_t max_true_restarts; /* extra FP64 restarts when the true residual misses eps2 */
   uint32_t feat_mask;   /* bit c set: feature c used in the distance */
+  int32_t bfs_starts;   /* 2BFS runs for l~ (Sec. 6 remark; <= 1: the single run) */
 } orc_opts;
 
 typedef struct {
@@ -103,6 +104,7 @@ int32_t orc_cg32(const orc_csr* A, const double* b, float* x, double eps,
 /* ---- sparsity-graph features (Sec. 6) ---- */
 int32_t orc_bfs(const orc_csr* A, int32_t src, int32_t* dist);  /* returns #reached */
 int32_t orc_pseudo_diameter(const orc_csr* A, int32_t* t_out);    /* 2BFS, per component */
+int32_t orc_pseudo_diameter_rep(const orc_csr* A, int32_t R, int32_t* t_out); /* R runs, max */
 int32_t orc_components(const orc_csr* A, int32_t* label);         /* label = min vertex; returns #components */
 
 /* ---- kNN (Sec. 11) ----

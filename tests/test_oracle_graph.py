@@ -1,4 +1,6 @@
 """Pins of the oracle's BFS, components and 2BFS pseudo-diameter (Sec. 6)."""
+from collections import deque
+
 import numpy as np
 import pytest
 from scipy.sparse import csr_matrix
@@ -111,3 +113,101 @@ def test_banded_components():
 def test_single_vertex():
     A = synth.from_edges(1, [], [], np.zeros(0), np.ones(1))
     assert oracle.pseudo_diameter(A) == 0
+
+
+# ---- repeated 2BFS (remark of Sec. 6) ------------------------------------------------------
+
+def _adj(A):
+    return [[int(c) for c in A.col[A.row_ptr[i]:A.row_ptr[i + 1]] if c != i] for i in range(A.n)]
+
+
+def _bfs_py(adj, s):
+    d = [-1] * len(adj)
+    d[s] = 0
+    q = deque([s])
+    while q:
+        u = q.popleft()
+        for w in adj[u]:
+            if d[w] < 0:
+                d[w] = d[u] + 1
+                q.append(w)
+    return d
+
+
+def _two_bfs_py(adj, s):
+    d = _bfs_py(adj, s)
+    far = max(d)
+    t = d.index(far)                      # smallest vertex at the largest distance
+    return max(_bfs_py(adj, t))
+
+
+def _repeated_py(A, R):
+    """Run 0: per component from its smallest vertex; run r: 2BFS from floor(r n / R)."""
+    adj = _adj(A)
+    n = A.n
+    ell, seen = 0, [False] * n
+    for s in range(n):
+        if not seen[s]:
+            for v, dv in enumerate(_bfs_py(adj, s)):
+                if dv >= 0:
+                    seen[v] = True
+            ell = max(ell, _two_bfs_py(adj, s))
+    for r in range(1, R):
+        ell = max(ell, _two_bfs_py(adj, (r * n) // R))
+    return ell
+
+
+def _diameter_py(A):
+    adj = _adj(A)
+    return max(max(_bfs_py(adj, s)) for s in range(A.n))
+
+
+def _random_graph(n, m, seed):
+    rng = np.random.default_rng(seed)
+    pairs = set()
+    while len(pairs) < m:
+        a, b = rng.integers(0, n, 2)
+        if a != b:
+            pairs.add((int(min(a, b)), int(max(a, b))))
+    i = np.array([p for p, _ in pairs])
+    j = np.array([q for _, q in pairs])
+    return synth.from_edges(n, i, j, -np.ones(i.size), np.full(n, 10.0))
+
+
+def test_repeated_2bfs_matches_independent_bfs_and_bounds():
+    for seed in range(40):
+        n = 8 + seed % 9
+        A = _random_graph(n, n + seed % 5, seed)        # often disconnected, often cyclic
+        exact = _diameter_py(A)
+        one = oracle.pseudo_diameter(A)
+        prev, prev_R = one, 1
+        for R in (1, 2, 3, 5, n):
+            got = oracle.pseudo_diameter(A, starts=R)
+            assert got == _repeated_py(A, R), (seed, R)
+            assert one <= got <= exact
+            assert got >= prev if R > 1 and R % prev_R == 0 else True
+            prev, prev_R = got, R
+        assert oracle.pseudo_diameter(A, starts=1) == one
+
+
+def test_repeated_2bfs_can_beat_a_single_run():
+    """Among small random connected graphs, some have a single-start 2BFS below the
+    diameter; every start (R = n) then reaches at least as far, and strictly further on
+    some of them."""
+    better = 0
+    for seed in range(300):
+        n = 10 + seed % 7
+        A = _random_graph(n, n + 2 + seed % 4, 1000 + seed)
+        if oracle.components(A)[1] != 1:
+            continue
+        one, every = oracle.pseudo_diameter(A), oracle.pseudo_diameter(A, starts=n)
+        assert one <= every <= _diameter_py(A)
+        better += every > one
+    assert better > 0
+
+
+def test_repeated_2bfs_on_grids_and_paths_keeps_the_exact_value():
+    for A, ell in ((synth.laplacian_2d(13, 7), 18), (synth.path(50), 49),
+                   (synth.laplacian_3d(5), 12)):
+        for R in (1, 4, 9):
+            assert oracle.pseudo_diameter(A, starts=R) == ell
