@@ -119,7 +119,12 @@ typedef struct {
   int32_t serve_split;       /* server, mixed precision: 1 = two launches per step (set-up,
                                 features and the single-precision stage with its SpMV staged in
                                 shared memory; then the FP64 stage); 0 = one launch (default) */
-  int32_t reserved[2];
+  int32_t bfs_starts;        /* 2BFS runs for l~ (the repeated 2BFS of Sec. 6: run r >= 1 starts
+                                from floor(r n / R); l~ = the largest); <= 1: one run (default).
+                                mpcg_solve and mpcg_features only: the batched solve and the
+                                server refuse Algorithm II with bfs_starts > 1
+                                (MPCG_ERR_UNIMPLEMENTED) */
+  int32_t reserved[1];
 } mpcg_options_t;
 
 /* Result record, written by the device at the end of the call's work into

@@ -23,6 +23,7 @@ bool options_ok(const mpcg_options_t* o) {
   if (!(o->eps2 >= 0.0)) return false;
   if (o->k0 < 0 || o->knn_k < 1 || o->knn_k > MPCG_KNN_MAX_K) return false;
   if (o->grid_blocks < 0 || o->timeout_ms < 0) return false;
+  if (o->bfs_starts < 0) return false;
   return true;
 }
 
@@ -84,6 +85,7 @@ mpcg_options_t mpcg_options_default(void) {
   o.fp64_only = 0;
   o.grid_blocks = 0;
   o.timeout_ms = 20000;
+  o.bfs_starts = 1;
   return o;
 }
 

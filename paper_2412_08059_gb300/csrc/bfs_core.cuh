@@ -398,6 +398,35 @@ __device__ bool cc_run(const BfsGraph& g, int tid, int T, Sync& sync) {
   return true;
 }
 
+// Runs r = 1 .. R-1 of the repeated 2BFS (the remark of Sec. 6; R =
+// ctl->bfs_starts): one 2BFS from s_r = floor(r n / R) inside its component
+// each (BFS from s_r, t_r = the smallest vertex at the largest distance, BFS
+// from t_r); ctl->pdiam becomes the largest of all runs.  Not inlined: the
+// kernels that compute features carry it as a call.
+template <class Sync>
+__device__ __noinline__ bool pseudo_diameter_repeats(const BfsGraph& g, int32_t* d1, int32_t* d2,
+                                                     int tid, int T, Sync& sync) {
+  Ctl* ctl = g.ctl;
+  const int R = ctl->bfs_starts;
+  for (int r = 1; r < R; ++r) {
+    const int s = (int)(((long long)r * g.n) / R);
+    if (tid == 0) ctl->key = 0ull;
+    if (!sync()) return false;
+    const int prev = *reinterpret_cast<volatile int*>(&ctl->pdiam);
+    if (!bfs_run(g, d1, kSrcSingle, s, kRoleFirst, tid, T, sync)) return false;
+    if (!sync()) return false;
+    const int t = far_key_vertex(*reinterpret_cast<volatile unsigned long long*>(&ctl->key));
+    if (!bfs_run(g, d2, kSrcSingle, t, kRoleSecond, tid, T, sync)) return false;
+    if (!sync()) return false;
+    if (tid == 0) {
+      const int cur = *reinterpret_cast<volatile int*>(&ctl->pdiam);
+      ctl->pdiam = cur > prev ? cur : prev;
+    }
+    if (!sync()) return false;
+  }
+  return true;
+}
+
 // 2BFS pseudo-diameter with the per-component rule.  On return (true),
 // ctl->pdiam holds l~ and ctl->far_t the farthest vertex found from vertex 0.
 //
@@ -407,7 +436,9 @@ __device__ bool cc_run(const BfsGraph& g, int tid, int T, Sync& sync) {
 // corner n - 1.  When the first BFS confirms t = t', the second search is
 // exactly the BFS from t and l~ is its depth; otherwise the BFS from t runs
 // afterwards.  Either way the result is that of the two searches in order.
-template <class Sync>
+// kRepeats: run the repeated 2BFS when ctl->bfs_starts > 1 (the team kernels
+// instantiate it without, so that their code does not change).
+template <class Sync, bool kRepeats = true>
 __device__ bool pseudo_diameter_run(const BfsGraph& g, int32_t* d1, int32_t* d2, int tid, int T,
                                     Sync& sync) {
   Ctl* ctl = g.ctl;
@@ -453,6 +484,9 @@ __device__ bool pseudo_diameter_run(const BfsGraph& g, int32_t* d1, int32_t* d2,
     if (tid == 0) ctl->far_t = far_key_vertex(g.ckey[0]);
   }
   if (tid == 0) ctl->connected = connected ? 1 : 0;
+  if constexpr (kRepeats) {
+    if (ctl->bfs_starts > 1) return pseudo_diameter_repeats(g, d1, d2, tid, T, sync);
+  }
   return true;
 }
 

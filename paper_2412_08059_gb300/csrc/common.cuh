@@ -52,6 +52,7 @@ struct Ctl {
   int x32_src;     // stage-1 result: -1 = x32, s >= 0 = snapshot slot s
   // device clock marks (ns)
   unsigned long long t_start, t_prep, t_features, t_fp32, t_fp64, t_end;
+  int bfs_starts;  // 2BFS runs for l~ (the repeated 2BFS of Sec. 6; 1 = the single run)
 };
 
 // ---------------------------------------------------------------------------------------

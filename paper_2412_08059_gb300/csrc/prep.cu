@@ -97,6 +97,7 @@ __global__ void k_init(Ctl* c, int n, int nnz, int nslices, int wcap, mpcg_optio
   c->cls = -1;
   c->first = 1;
   c->x32_src = -1;
+  c->bfs_starts = o.bfs_starts > 1 ? o.bfs_starts : 1;
 }
 
 // One thread per row (padded to whole slices): checks the CSR rules, writes

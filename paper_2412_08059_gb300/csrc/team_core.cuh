@@ -1040,7 +1040,8 @@ static __device__ bool team_pseudo_diameter(Team& t, const BatchSys& s, int smem
   BfsGraph g{ctl, s.A.row_ptr, s.A.col, s.n, s.w.fq0, s.w.fq1, s.w.label, s.w.ckey,
              s.w.fq2, s.w.fq3};
   TeamSyncFn sync{&t};
-  return pseudo_diameter_run(g, s.w.dist, s.w.dist2, team_tid(t), team_threads(t), sync);
+  return pseudo_diameter_run<TeamSyncFn, false>(g, s.w.dist, s.w.dist2, team_tid(t),
+                                                team_threads(t), sync);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -55,7 +55,8 @@ class Options(C.Structure):
                 ("max_true_restarts", C.c_int32), ("feat_mask", C.c_uint32),
                 ("fp64_only", C.c_int32), ("grid_blocks", C.c_int32), ("timeout_ms", C.c_int32),
                 ("stage1_only", C.c_int32), ("team_rows", C.c_int32),
-                ("serve_split", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("serve_split", C.c_int32), ("bfs_starts", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class Result(C.Structure):

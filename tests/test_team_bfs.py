@@ -108,3 +108,59 @@ def test_pinned_diameters():
     A = permuted(synth.laplacian_2d(60, 45), seed=1)
     ell, t = oracle.pseudo_diameter(A, return_t=True)
     assert ell == 59 + 44 and t != A.n - 1
+
+
+def small_random_graph(n, m, seed):
+    rng = np.random.default_rng(seed)
+    pairs = set()
+    while len(pairs) < m:
+        a, b = rng.integers(0, n, 2)
+        if a != b:
+            pairs.add((int(min(a, b)), int(max(a, b))))
+    i = np.array([p for p, _ in pairs])
+    j = np.array([q for _, q in pairs])
+    return synth.from_edges(n, i, j, -np.ones(i.size), np.full(n, 12.0))
+
+
+def repeat_cases():
+    """Graphs on which more 2BFS starts find a larger l~ (found by the oracle), a
+    sparse random graph with cycles, a disconnected one and grids (exact anyway)."""
+    gains = []
+    for seed in range(400):
+        A = small_random_graph(10 + seed % 7, 12 + seed % 5, 2000 + seed)
+        if oracle.components(A)[1] == 1 and \
+                oracle.pseudo_diameter(A, starts=A.n) > oracle.pseudo_diameter(A):
+            gains.append(A)
+        if len(gains) == 4:
+            break
+    assert gains
+    return gains + [synth.random_regular_laplacian(3000, 3, 1e-2, seed=8),
+                    union(synth.path(40), small_random_graph(30, 34, 5)),
+                    synth.laplacian_2d(40, 30), synth.laplacian_2d(513, 512)]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("R", [3, 16])
+def test_repeated_2bfs_matches_oracle(mp, R):
+    """The repeated 2BFS of Sec. 6 in the fused stage-1 kernel (mpcg_solve) and
+    in the feature kernels (mpcg_features); the team kernels run one 2BFS and
+    refuse the option."""
+    mats = repeat_cases()
+    want = [oracle.pseudo_diameter(A, starts=R) for A in mats]
+    assert any(w > oracle.pseudo_diameter(A) for w, A in zip(want, mats))
+    bs = [synth.rhs(A, seed=500 + i)[1] for i, A in enumerate(mats)]
+    feat, cls = sample_over(mats, seed=6)
+    S = mp.DeviceSample(feat, cls)
+    dmats = [mp.DeviceCSR.from_host(A) for A in mats]
+    dbs = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in bs]
+    for A, b, w, dA, db in zip(mats, bs, want, dmats, dbs):
+        _, r = mp.solve(dA, db, S, bfs_starts=R)
+        assert r["pdiam"] == w, (A.n, r["pdiam"], w)
+        assert r["status"] >= 0
+        assert mp.features(dA, db, bfs_starts=R)["pdiam"] == w
+    assert mp.features(dmats[0], dbs[0])["pdiam"] == oracle.pseudo_diameter(mats[0])
+    xs = [torch.empty(A.n, dtype=torch.float64, device="cuda") for A in mats]
+    ws = torch.empty(mp.batch_workspace_bytes(dmats), dtype=torch.uint8, device="cuda")
+    with pytest.raises(RuntimeError, match="not implemented|unimplemented"):
+        mp.solve_batch_async(dmats, dbs, xs, mp.options(bfs_starts=R), ws,
+                             mp.result_buffer(len(mats)), S)
