@@ -72,34 +72,48 @@ typedef struct {
   const float* v32;
   float *x, *r, *d, *q;
   double rr; /* r^T r in double */
+  /* Jacobi preconditioning (the PCG form of Sec. 5; NULL: plain CG):
+   * dinv = 1 / diag(A~) in float, z = dinv r, rz = r^T z in double. */
+  const float* dinv;
+  float* z;
+  double rz;
 } cg32_t;
 
 enum { IT_OK = 0, IT_BREAKDOWN = 1, IT_NAN = 2 };
 
-static int cg32_alloc(cg32_t* s, const orc_csr* A, const float* v32) {
+static int cg32_alloc(cg32_t* s, const orc_csr* A, const float* v32, const float* dinv) {
   s->n = A->n;
   s->rp = A->row_ptr;
   s->ci = A->col;
   s->v32 = v32;
+  s->dinv = dinv;
+  s->rz = 0.0;
   size_t bytes = sizeof(float) * (size_t)(A->n > 0 ? A->n : 1);
   s->x = (float*)malloc(bytes);
   s->r = (float*)malloc(bytes);
   s->d = (float*)malloc(bytes);
   s->q = (float*)malloc(bytes);
-  if (s->x && s->r && s->d && s->q) return 1;
-  free(s->x); free(s->r); free(s->d); free(s->q);
+  s->z = (float*)malloc(bytes);
+  if (s->x && s->r && s->d && s->q && s->z) return 1;
+  free(s->x); free(s->r); free(s->d); free(s->q); free(s->z);
   return 0;
 }
 static void cg32_free(cg32_t* s) {
-  free(s->x); free(s->r); free(s->d); free(s->q);
+  free(s->x); free(s->r); free(s->d); free(s->q); free(s->z);
 }
 
-/* CG line 1: x0 = 0, r0 = b - A x0, d0 = r0. */
+/* CG line 1: x0 = 0, r0 = b - A x0, d0 = r0 (PCG: z0 = M^-1 r0, d0 = z0). */
 static void cg32_start(cg32_t* s, const float* b32) {
   for (int32_t i = 0; i < s->n; ++i) s->x[i] = 0.0f;
   orc_spmv32(s->n, s->rp, s->ci, s->v32, s->x, s->q);
   for (int32_t i = 0; i < s->n; ++i) s->r[i] = b32[i] - s->q[i];
-  for (int32_t i = 0; i < s->n; ++i) s->d[i] = s->r[i];
+  if (s->dinv) {
+    for (int32_t i = 0; i < s->n; ++i) s->z[i] = s->dinv[i] * s->r[i];
+    for (int32_t i = 0; i < s->n; ++i) s->d[i] = s->z[i];
+    s->rz = orc_dot32(s->n, s->r, s->z);
+  } else {
+    for (int32_t i = 0; i < s->n; ++i) s->d[i] = s->r[i];
+  }
   s->rr = orc_dot32(s->n, s->r, s->r);
 }
 
@@ -111,13 +125,23 @@ static int cg32_iter(cg32_t* s) {
   double dq = orc_dot32(n, s->d, s->q);                      /* d^T A d      */
   if (!isfinite(dq)) return IT_NAN;
   if (!(dq > 0.0)) return IT_BREAKDOWN;
-  float alpha = (float)(s->rr / dq);                         /* alpha_i      */
+  const double num = s->dinv ? s->rz : s->rr;                /* PCG: r^T z   */
+  float alpha = (float)(num / dq);                           /* alpha_i      */
   for (int32_t i = 0; i < n; ++i) s->x[i] = fmaf(alpha, s->d[i], s->x[i]);
   for (int32_t i = 0; i < n; ++i) s->r[i] = fmaf(-alpha, s->q[i], s->r[i]);
   double rr_new = orc_dot32(n, s->r, s->r);
   if (!isfinite(rr_new)) return IT_NAN;
-  float beta = (float)(rr_new / s->rr);                      /* beta_{i+1}   */
-  for (int32_t i = 0; i < n; ++i) s->d[i] = fmaf(beta, s->d[i], s->r[i]);
+  if (s->dinv) {                                             /* z = M^-1 r   */
+    for (int32_t i = 0; i < n; ++i) s->z[i] = s->dinv[i] * s->r[i];
+    double rz_new = orc_dot32(n, s->r, s->z);
+    if (!isfinite(rz_new)) return IT_NAN;
+    float beta = (float)(rz_new / s->rz);
+    for (int32_t i = 0; i < n; ++i) s->d[i] = fmaf(beta, s->d[i], s->z[i]);
+    s->rz = rz_new;
+  } else {
+    float beta = (float)(rr_new / s->rr);                    /* beta_{i+1}   */
+    for (int32_t i = 0; i < n; ++i) s->d[i] = fmaf(beta, s->d[i], s->r[i]);
+  }
   s->rr = rr_new;
   return IT_OK;
 }
@@ -129,28 +153,40 @@ typedef struct {
   const orc_csr* A;
   double *x, *r, *d, *q; /* x is caller memory */
   double rr;
+  const double* dinv;    /* Jacobi: 1 / diag(A); NULL: plain CG */
+  double *z, rz;
 } cg64_t;
 
-static int cg64_alloc(cg64_t* s, const orc_csr* A, double* x) {
+static int cg64_alloc(cg64_t* s, const orc_csr* A, double* x, const double* dinv) {
   s->A = A;
   s->x = x;
+  s->dinv = dinv;
+  s->rz = 0.0;
   size_t bytes = sizeof(double) * (size_t)(A->n > 0 ? A->n : 1);
   s->r = (double*)malloc(bytes);
   s->d = (double*)malloc(bytes);
   s->q = (double*)malloc(bytes);
-  if (s->r && s->d && s->q) return 1;
-  free(s->r); free(s->d); free(s->q);
-  s->r = s->d = s->q = NULL;
+  s->z = (double*)malloc(bytes);
+  if (s->r && s->d && s->q && s->z) return 1;
+  free(s->r); free(s->d); free(s->q); free(s->z);
+  s->r = s->d = s->q = s->z = NULL;
   return 0;
 }
-static void cg64_free(cg64_t* s) { free(s->r); free(s->d); free(s->q); }
+static void cg64_free(cg64_t* s) { free(s->r); free(s->d); free(s->q); free(s->z); }
 
-/* CG line 1 from the current x: r0 = b - A x0 in double, d0 = r0. */
+/* CG line 1 from the current x: r0 = b - A x0 in double, d0 = r0
+ * (PCG: z0 = M^-1 r0, d0 = z0). */
 static void cg64_start(cg64_t* s, const double* b) {
   const int32_t n = s->A->n;
   orc_spmv64(s->A, s->x, s->q);
   for (int32_t i = 0; i < n; ++i) s->r[i] = b[i] - s->q[i];
-  for (int32_t i = 0; i < n; ++i) s->d[i] = s->r[i];
+  if (s->dinv) {
+    for (int32_t i = 0; i < n; ++i) s->z[i] = s->dinv[i] * s->r[i];
+    for (int32_t i = 0; i < n; ++i) s->d[i] = s->z[i];
+    s->rz = orc_dot64(n, s->r, s->z);
+  } else {
+    for (int32_t i = 0; i < n; ++i) s->d[i] = s->r[i];
+  }
   s->rr = orc_dot64(n, s->r, s->r);
 }
 
@@ -160,15 +196,41 @@ static int cg64_iter(cg64_t* s) {
   double dq = orc_dot64(n, s->d, s->q);
   if (!isfinite(dq)) return IT_NAN;
   if (!(dq > 0.0)) return IT_BREAKDOWN;
-  double alpha = s->rr / dq;
+  double alpha = (s->dinv ? s->rz : s->rr) / dq;
   for (int32_t i = 0; i < n; ++i) s->x[i] = fma(alpha, s->d[i], s->x[i]);
   for (int32_t i = 0; i < n; ++i) s->r[i] = fma(-alpha, s->q[i], s->r[i]);
   double rr_new = orc_dot64(n, s->r, s->r);
   if (!isfinite(rr_new)) return IT_NAN;
-  double beta = rr_new / s->rr;
-  for (int32_t i = 0; i < n; ++i) s->d[i] = fma(beta, s->d[i], s->r[i]);
+  if (s->dinv) {
+    for (int32_t i = 0; i < n; ++i) s->z[i] = s->dinv[i] * s->r[i];
+    double rz_new = orc_dot64(n, s->r, s->z);
+    if (!isfinite(rz_new)) return IT_NAN;
+    double beta = rz_new / s->rz;
+    for (int32_t i = 0; i < n; ++i) s->d[i] = fma(beta, s->d[i], s->z[i]);
+    s->rz = rz_new;
+  } else {
+    double beta = rr_new / s->rr;
+    for (int32_t i = 0; i < n; ++i) s->d[i] = fma(beta, s->d[i], s->r[i]);
+  }
   s->rr = rr_new;
   return IT_OK;
+}
+
+/* Jacobi preconditioner M = diag(A) (Sec. 5): dinv64[i] = 1 / a_ii and
+ * dinv32[i] = 1 / float32(a_ii), each a correctly rounded division in its
+ * precision.  0 if a row has no stored diagonal or a_ii is zero or not
+ * finite (M is then not invertible). */
+static int jacobi_dinv(const orc_csr* A, double* dinv64, float* dinv32) {
+  for (int32_t i = 0; i < A->n; ++i) {
+    double a = 0.0;
+    int found = 0;
+    for (int32_t e = A->row_ptr[i]; e < A->row_ptr[i + 1]; ++e)
+      if (A->col[e] == i) { a = A->val[e]; found = 1; }
+    if (!found || !(a != 0.0) || !isfinite(a)) return 0;
+    if (dinv64) dinv64[i] = 1.0 / a;
+    if (dinv32) dinv32[i] = 1.0f / (float)a;
+  }
+  return 1;
 }
 
 static int32_t it_status(int st) {
@@ -189,14 +251,19 @@ static int csr_ok(const orc_csr* A) {
 /* Plain CG drivers (Sec. 3).                                                */
 /* ------------------------------------------------------------------------ */
 int32_t orc_cg64(const orc_csr* A, const double* b, double* x, double eps,
-                 int32_t tol_relative, int32_t max_it, int32_t* iters,
+                 int32_t tol_relative, int32_t max_it, int32_t precond, int32_t* iters,
                  double* res_hist) {
   *iters = 0;
   if (!csr_ok(A)) return ORC_ERR_INVALID_ARG;
   double bnorm = sqrt(orc_dot64(A->n, b, b));
   if (!isfinite(bnorm)) return ORC_ERR_NAN;
+  double* dinv = NULL;
+  if (precond) {
+    dinv = (double*)malloc(sizeof(double) * (size_t)A->n);
+    if (!dinv || !jacobi_dinv(A, dinv, NULL)) { free(dinv); return ORC_ERR_INVALID_ARG; }
+  }
   cg64_t s;
-  if (!cg64_alloc(&s, A, x)) { cg64_free(&s); return ORC_ERR_INVALID_ARG; }
+  if (!cg64_alloc(&s, A, x, dinv)) { cg64_free(&s); free(dinv); return ORC_ERR_INVALID_ARG; }
   cg64_start(&s, b);
   int32_t st = ORC_OK, it = 0;
   for (;;) {
@@ -211,24 +278,27 @@ int32_t orc_cg64(const orc_csr* A, const double* b, double* x, double eps,
   }
   *iters = it;
   cg64_free(&s);
+  free(dinv);
   return st;
 }
 
 int32_t orc_cg32(const orc_csr* A, const double* b, float* x, double eps,
-                 int32_t tol_relative, int32_t max_it, int32_t* iters,
+                 int32_t tol_relative, int32_t max_it, int32_t precond, int32_t* iters,
                  double* res_hist) {
   *iters = 0;
   if (!csr_ok(A)) return ORC_ERR_INVALID_ARG;
   const int32_t n = A->n;
   float* v32 = (float*)malloc(sizeof(float) * (size_t)(A->nnz > 0 ? A->nnz : 1));
   float* b32 = (float*)malloc(sizeof(float) * (size_t)n);
+  float* dinv = precond ? (float*)malloc(sizeof(float) * (size_t)n) : NULL;
   cg32_t s;
   int32_t st = ORC_OK, it = 0;
   if (v32 && b32) {
     for (int32_t e = 0; e < A->nnz; ++e) v32[e] = (float)A->val[e];
     for (int32_t i = 0; i < n; ++i) b32[i] = (float)b[i];
   }
-  int ok = v32 && b32 && cg32_alloc(&s, A, v32);
+  int ok = v32 && b32 && (!precond || (dinv && jacobi_dinv(A, NULL, dinv))) &&
+           cg32_alloc(&s, A, v32, dinv);
   if (ok) {
     double bnorm = sqrt(orc_dot32(n, b32, b32));
     cg32_start(&s, b32);
@@ -249,6 +319,7 @@ int32_t orc_cg32(const orc_csr* A, const double* b, float* x, double eps,
   }
   free(v32);
   free(b32);
+  free(dinv);
   *iters = it;
   return st;
 }
@@ -449,6 +520,7 @@ orc_opts orc_opts_default(void) {
   o.max_true_restarts = 2;
   o.feat_mask = 0xFu;
   o.bfs_starts = 1;
+  o.precond = 0;
   return o;
 }
 
@@ -503,10 +575,14 @@ int32_t orc_features(const orc_csr* A, const double* b, const orc_opts* o,
   float* v32 = (float*)malloc(sizeof(float) * (size_t)(A->nnz > 0 ? A->nnz : 1));
   float* b32 = (float*)malloc(sizeof(float) * (size_t)n);
   cg32_t s;
-  if (!v32 || !b32) { free(v32); free(b32); return ORC_ERR_INVALID_ARG; }
+  float* dinv = o->precond ? (float*)malloc(sizeof(float) * (size_t)n) : NULL;
+  if (!v32 || !b32 || (o->precond && (!dinv || !jacobi_dinv(A, NULL, dinv)))) {
+    free(v32); free(b32); free(dinv);
+    return ORC_ERR_INVALID_ARG;
+  }
   for (int32_t e = 0; e < A->nnz; ++e) v32[e] = (float)A->val[e];
   for (int32_t i = 0; i < n; ++i) b32[i] = (float)b[i];
-  if (!cg32_alloc(&s, A, v32)) { free(v32); free(b32); return ORC_ERR_INVALID_ARG; }
+  if (!cg32_alloc(&s, A, v32, dinv)) { free(v32); free(b32); free(dinv); return ORC_ERR_INVALID_ARG; }
   double bnorm32 = sqrt(orc_dot32(n, b32, b32));
   cg32_start(&s, b32);
   int32_t n1 = 0, broke = 0;
@@ -523,6 +599,7 @@ int32_t orc_features(const orc_csr* A, const double* b, const orc_opts* o,
   cg32_free(&s);
   free(v32);
   free(b32);
+  free(dinv);
   return st;
 }
 
@@ -551,10 +628,19 @@ int32_t orc_solve(const orc_csr* A, const double* b, double* x,
   float* b32 = (float*)malloc(sizeof(float) * (size_t)n);
   cg32_t s;
   cg64_t s64;
-  if (!v32 || !b32) { free(v32); free(b32); return res->status = ORC_ERR_INVALID_ARG; }
+  /* Jacobi preconditioning in both stages (the PCG form of Sec. 5) */
+  float* dinv32 = o->precond ? (float*)malloc(sizeof(float) * (size_t)n) : NULL;
+  double* dinv64 = o->precond ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
+  if (!v32 || !b32 || (o->precond && (!dinv32 || !dinv64 || !jacobi_dinv(A, dinv64, dinv32)))) {
+    free(v32); free(b32); free(dinv32); free(dinv64);
+    return res->status = ORC_ERR_INVALID_ARG;
+  }
   for (int32_t e = 0; e < A->nnz; ++e) v32[e] = (float)A->val[e];
   for (int32_t i = 0; i < n; ++i) b32[i] = (float)b[i];
-  if (!cg32_alloc(&s, A, v32)) { free(v32); free(b32); return res->status = ORC_ERR_INVALID_ARG; }
+  if (!cg32_alloc(&s, A, v32, dinv32)) {
+    free(v32); free(b32); free(dinv32); free(dinv64);
+    return res->status = ORC_ERR_INVALID_ARG;
+  }
   double bnorm32 = sqrt(orc_dot32(n, b32, b32));
   int32_t status = ORC_OK;
   int warn_eps1 = 0, warn_restart = 0, broke = 0;
@@ -597,7 +683,7 @@ int32_t orc_solve(const orc_csr* A, const double* b, double* x,
 
   /* Promote: x0 = float64(x~); restart FP64 CG with r0 = b - A x0. */
   for (int32_t i = 0; i < n; ++i) x[i] = (double)s.x[i];
-  if (!cg64_alloc(&s64, A, x)) { cg64_free(&s64); status = ORC_ERR_INVALID_ARG; goto done32; }
+  if (!cg64_alloc(&s64, A, x, dinv64)) { cg64_free(&s64); status = ORC_ERR_INVALID_ARG; goto done32; }
   for (int32_t restart = 0;; ++restart) {
     cg64_start(&s64, b);
     for (;;) {
@@ -628,5 +714,7 @@ done32:
   cg32_free(&s);
   free(v32);
   free(b32);
+  free(dinv32);
+  free(dinv64);
   return res->status = status;
 }

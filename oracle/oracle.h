@@ -64,6 +64,7 @@ typedef struct {
   int32_t max_true_restarts; /* extra FP64 restarts when the true residual misses eps2 */
   uint32_t feat_mask;   /* bit c set: feature c used in the distance */
   int32_t bfs_starts;   /* 2BFS runs for l~ (Sec. 6 remark; <= 1: the single run) */
+  int32_t precond;      /* 1: Jacobi-preconditioned CG in both stages (Sec. 5); 0: plain */
 } orc_opts;
 
 typedef struct {
@@ -95,10 +96,10 @@ double orc_dot32(int32_t n, const float* a, const float* b);
  * res_hist (nullable, max_it+1 entries) receives the stop measure at the
  * head of every iteration.  Returns status; *iters = iterations performed. */
 int32_t orc_cg64(const orc_csr* A, const double* b, double* x, double eps,
-                 int32_t tol_relative, int32_t max_it, int32_t* iters,
+                 int32_t tol_relative, int32_t max_it, int32_t precond, int32_t* iters,
                  double* res_hist);
 int32_t orc_cg32(const orc_csr* A, const double* b, float* x, double eps,
-                 int32_t tol_relative, int32_t max_it, int32_t* iters,
+                 int32_t tol_relative, int32_t max_it, int32_t precond, int32_t* iters,
                  double* res_hist);
 
 /* ---- sparsity-graph features (Sec. 6) ---- */

@@ -8,8 +8,10 @@ import math
 import numpy as np
 import pytest
 import scipy.linalg
+from scipy.sparse import csr_matrix, diags
 
 import oracle
+import oracle.metrics  # noqa: F401 (oracle.metrics.cg_iter_bound)
 import synth
 
 
@@ -205,3 +207,93 @@ def test_decay_rate_v_closed_form_two_eigenvalues():
     assert k0d == 1 and feat[3] == pytest.approx(ratio1, rel=2e-6)
     feat, k0d, _ = oracle.features(A, b, k0=2, eps2=0.0)
     assert k0d == 2 and feat[3] == pytest.approx(ratio1 / 2, rel=1e-5)
+
+
+# ---- Jacobi-preconditioned CG (the PCG form of Sec. 5), pinned by identities -------------
+
+def _scaled(A):
+    """D^-1/2 A D^-1/2 as a CSR, and the scaling vector D^-1/2."""
+    M = csr_matrix((A.val, A.col, A.row_ptr), shape=(A.n, A.n))
+    s = 1.0 / np.sqrt(M.diagonal())
+    S = (diags(s) @ M @ diags(s)).tocsr()
+    S.sort_indices()
+    return synth.CSR(S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data), s
+
+
+def _varying_diagonal(n=300, seed=3):
+    return synth.random_tree_plus(n, 2.0, 1.1, seed=seed)   # a_ii = 1.1 sum_j |a_ij|, uneven
+
+
+def test_pcg_on_a_diagonal_matrix_takes_one_iteration():
+    n = 50
+    d = np.linspace(0.5, 40.0, n)
+    A = synth.from_edges(n, [], [], np.zeros(0), d)
+    b = np.random.default_rng(1).uniform(-1, 1, n)
+    x, it, st = oracle.cg64(A, b, 1e-14, precond=1)
+    assert st == 0 and it == 1 and np.allclose(x, b / d, rtol=1e-15, atol=0)
+    x, it, st = oracle.cg64(A, b, 1e-10)                    # plain CG needs one per distinct value
+    assert it > 10
+    x32, it32, st32 = oracle.cg32(A, b, 1e-6, precond=1)
+    assert st32 == 0 and it32 == 1
+
+
+def test_pcg_with_a_power_of_two_diagonal_equals_cg_bit_for_bit():
+    """z = r / 4 is exact, so every PCG quantity is CG's scaled by a power of two."""
+    A = synth.laplacian_2d(23, 17)                            # a_ii = 4
+    _, b = synth.rhs(A, seed=4)
+    for k in (1, 3, 12):
+        xc, ic, _ = oracle.cg64(A, b, 0.0, max_it=k)
+        xp, ip, _ = oracle.cg64(A, b, 0.0, max_it=k, precond=1)
+        assert ic == ip == k and np.array_equal(xc, xp)
+        xc32, _, _ = oracle.cg32(A, b, 0.0, max_it=k)
+        xp32, _, _ = oracle.cg32(A, b, 0.0, max_it=k, precond=1)
+        assert np.array_equal(xc32, xp32)
+    _, nc, _ = oracle.cg64(A, b, 1e-10)
+    _, np_, _ = oracle.cg64(A, b, 1e-10, precond=1)
+    assert nc == np_
+
+
+def test_pcg_iterates_are_cg_iterates_of_the_scaled_system():
+    """x_k(PCG on A) = D^-1/2 x^_k(CG on D^-1/2 A D^-1/2, b^ = D^-1/2 b) in exact
+    arithmetic; both from x = 0 and for the first iterations they agree to rounding."""
+    A = _varying_diagonal()
+    _, b = synth.rhs(A, seed=5)
+    As, s = _scaled(A)
+    for k in (1, 2, 5, 10):
+        xp, _, _ = oracle.cg64(A, b, 0.0, max_it=k, precond=1)
+        xh, _, _ = oracle.cg64(As, s * b, 0.0, max_it=k)
+        assert np.linalg.norm(xp - s * xh) <= 1e-11 * np.linalg.norm(xp), k
+
+
+def test_pcg_helps_on_a_badly_scaled_system_and_rejects_a_zero_diagonal():
+    n = 400
+    rng = np.random.default_rng(2)
+    i = np.arange(n - 1)
+    j = i + 1
+    off = -np.ones(n - 1)
+    d = np.exp(rng.uniform(0, np.log(1e4), n)) + 2.0          # diagonals over four decades
+    A = synth.from_edges(n, i, j, off, d)
+    b = rng.uniform(-1, 1, n)
+    _, nc, sc = oracle.cg64(A, b, 1e-10)
+    _, np_, sp = oracle.cg64(A, b, 1e-10, precond=1)
+    assert sc == sp == 0 and np_ * 4 < nc
+    Z = synth.from_edges(3, [0], [1], np.array([1.0]), np.array([2.0, 0.0, 1.0]))
+    assert oracle.cg64(Z, np.ones(3), 1e-10, precond=1)[2] == oracle.ERR_INVALID_ARG
+    _, r = oracle.solve(Z, np.ones(3), eps1=1e-4, precond=1)
+    assert r["status"] == oracle.ERR_INVALID_ARG
+
+
+def test_mixed_pcg_reaches_eps2_and_its_features_follow_the_preconditioned_iterations():
+    A = _varying_diagonal(500, seed=7)
+    _, b = synth.rhs(A, seed=8)
+    for eps1 in (1e-3, 1e-6):
+        x, r = oracle.solve(A, b, eps1=eps1, precond=1)
+        _, rp = oracle.solve(A, b, eps1=eps1)
+        assert r["status"] >= 0 and r["true_rel_resid"] <= 1e-10
+        assert r["n1"] + r["n2"] < rp["n1"] + rp["n2"]
+    f_plain = oracle.features(A, b)[0]
+    f_pc = oracle.features(A, b, precond=1)[0]
+    assert np.array_equal(f_pc[:3], f_plain[:3]) and f_pc[3] != f_plain[3]  # v from PCG
+    L = synth.laplacian_2d(20, 20)
+    _, bl = synth.rhs(L, seed=2)
+    assert oracle.features(L, bl, precond=1)[0][3] == oracle.features(L, bl)[0][3]
