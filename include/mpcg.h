@@ -124,7 +124,12 @@ typedef struct {
                                 mpcg_solve and mpcg_features only: the batched solve and the
                                 server refuse Algorithm II with bfs_starts > 1
                                 (MPCG_ERR_UNIMPLEMENTED) */
-  int32_t reserved[1];
+  int32_t precond;           /* 1: Jacobi-preconditioned CG (M = diag A, the PCG form of Sec. 5)
+                                in both stages; 0: plain CG (default).  mpcg_solve and
+                                mpcg_features only (the batched solve and the server refuse it:
+                                MPCG_ERR_UNIMPLEMENTED); Algorithm II then runs its steps as
+                                separate launches in the paper's order.  The workspace grows by
+                                16 n bytes: size it with these options */
 } mpcg_options_t;
 
 /* Result record, written by the device at the end of the call's work into

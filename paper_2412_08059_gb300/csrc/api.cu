@@ -24,6 +24,7 @@ bool options_ok(const mpcg_options_t* o) {
   if (o->k0 < 0 || o->knn_k < 1 || o->knn_k > MPCG_KNN_MAX_K) return false;
   if (o->grid_blocks < 0 || o->timeout_ms < 0) return false;
   if (o->bfs_starts < 0) return false;
+  if (o->precond != 0 && o->precond != 1) return false;
   return true;
 }
 
@@ -46,14 +47,28 @@ int grid_size(int requested) {
 }
 
 int32_t prepare(const mpcg_csr_t* A, void* ws, size_t ws_bytes, mpcg_stream_t stream,
-                int grid_req, Launch* L) {
+                int grid_req, Launch* L, int precond = 0) {
   if (!A || A->n <= 0 || A->nnz < 0 || !A->row_ptr || (A->nnz > 0 && (!A->col || !A->val)))
     return MPCG_ERR_INVALID_ARG;
   Dims d;
   if (!dims_for(A->n, A->nnz, &d)) return MPCG_ERR_INVALID_ARG;
   const size_t need = carve(d, nullptr, nullptr);
-  if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < need) return MPCG_ERR_WORKSPACE;
+  if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < need + precond_bytes(d.n, precond))
+    return MPCG_ERR_WORKSPACE;
   carve(d, (char*)ws, &L->ws);
+  L->precond = precond ? 1 : 0;
+  L->dinv64 = nullptr;
+  L->dinv32 = nullptr;
+  L->z32 = nullptr;
+  if (precond) {  // the preconditioner arrays, past the workspace map (256-byte aligned)
+    char* p = (char*)ws + need;
+    const size_t n = (size_t)d.n;
+    L->dinv64 = (double*)p;
+    p += (sizeof(double) * n + 255) & ~(size_t)255;
+    L->dinv32 = (float*)p;
+    p += (sizeof(float) * n + 255) & ~(size_t)255;
+    L->z32 = (float*)p;
+  }
   L->d = d;
   L->A = A;
   L->st = (cudaStream_t)stream;
@@ -86,6 +101,7 @@ mpcg_options_t mpcg_options_default(void) {
   o.grid_blocks = 0;
   o.timeout_ms = 20000;
   o.bfs_starts = 1;
+  o.precond = 0;
   return o;
 }
 
@@ -108,21 +124,21 @@ const char* mpcg_status_string(int32_t s) {
 }
 
 size_t mpcg_workspace_bytes(int32_t n, int32_t nnz, const mpcg_options_t* opts) {
-  (void)opts;
   Dims d;
   if (!dims_for(n, nnz, &d)) return 0;
-  return carve(d, nullptr, nullptr);
+  return carve(d, nullptr, nullptr) + precond_bytes(d.n, opts ? opts->precond : 0);
 }
 
 int32_t mpcg_features(const mpcg_csr_t* A, const double* b, const mpcg_options_t* opts,
                       void* ws, size_t ws_bytes, mpcg_features_t* out, mpcg_stream_t stream) {
   if (!b || !out || !options_ok(opts)) return MPCG_ERR_INVALID_ARG;
   Launch L;
-  int32_t st = prepare(A, ws, ws_bytes, stream, opts->grid_blocks, &L);
+  int32_t st = prepare(A, ws, ws_bytes, stream, opts->grid_blocks, &L, opts->precond);
   if (st != MPCG_OK) return st;
   cudaError_t e;
   if ((e = launch_init(L, *opts, 0)) != cudaSuccess) return cuda_status(e);
   if ((e = launch_prep(L, b)) != cudaSuccess) return cuda_status(e);
+  if (L.precond && (e = launch_jacobi(L)) != cudaSuccess) return cuda_status(e);
   if ((e = launch_pseudo_diameter(L, kSlotPd)) != cudaSuccess) return cuda_status(e);
   if ((e = launch_cg32(L, kCgK0, kSlotCgK0)) != cudaSuccess) return cuda_status(e);
   return cuda_status(launch_finalize(L, nullptr, out));
@@ -154,12 +170,21 @@ int32_t mpcg_solve(const mpcg_csr_t* A, const double* b, double* x, const mpcg_s
   const int auto_eps1 = !fp64_only && !(opts->eps1 > 0.0);
   if (auto_eps1 && !sample_ok(sample)) return MPCG_ERR_INVALID_ARG;
   Launch L;
-  int32_t st = prepare(A, ws, ws_bytes, stream, opts->grid_blocks, &L);
+  int32_t st = prepare(A, ws, ws_bytes, stream, opts->grid_blocks, &L, opts->precond);
   if (st != MPCG_OK) return st;
   cudaError_t e;
   if ((e = launch_init(L, *opts, fp64_only)) != cudaSuccess) return cuda_status(e);
   if ((e = launch_prep(L, b)) != cudaSuccess) return cuda_status(e);
-  if (!fp64_only) {
+  if (L.precond && (e = launch_jacobi(L)) != cudaSuccess) return cuda_status(e);
+  if (!fp64_only && auto_eps1 && L.precond) {
+    // Algorithm II with Jacobi PCG, its steps as separate launches in the
+    // paper's order: 2BFS, k0 iterations (v), kNN, stage 1 from iterate k0
+    if ((e = launch_pseudo_diameter(L, kSlotPd)) != cudaSuccess) return cuda_status(e);
+    if ((e = launch_cg32(L, kCgK0, kSlotCgK0)) != cudaSuccess) return cuda_status(e);
+    if ((e = launch_knn(L.st, nullptr, *sample, *opts, L.ws.ctl, nullptr, nullptr)) != cudaSuccess)
+      return cuda_status(e);
+    if ((e = launch_cg32(L, kCgContinue, kSlotCg32)) != cudaSuccess) return cuda_status(e);
+  } else if (!fp64_only) {
     if (auto_eps1) {  // Algorithm II: features, kNN and stage 1 in one fused launch
       if ((e = launch_stage1(L, *sample, *opts, kSlotCg32, kSlotPd)) != cudaSuccess)
         return cuda_status(e);

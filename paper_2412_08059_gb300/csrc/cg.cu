@@ -85,6 +85,10 @@ struct CgArgs {
   const double* b64;
   double *x64, *r64, *d64, *q64;
   float* snap;  // stage-1 snapshots of x~ ([slot][n]); ctl->x32_src picks one
+  // Jacobi preconditioning (the k_cg32 / k_cg64 instances with kPc)
+  const double* dinv64;
+  const float* dinv32;
+  float* z32;
 };
 
 template <typename T>
@@ -538,8 +542,57 @@ __device__ __forceinline__ void p2_32(const CgArgs& a, int R0, int R1, int lane,
   }
 }
 
+// Preconditioned form: also z = dinv r (stored; the next P1 forms d from it)
+// and r^T z.  Four rows per lane, every operand loaded before the stores.
+__device__ __forceinline__ void p2_32_pc(const CgArgs& a, int R0, int R1, int lane, const float* d,
+                                         float alpha, FF& prr, FF& prz) {
+  for (int base = R0 + 4 * lane; base < R1; base += 4 * kSlice) {
+    if (base + 4 <= R1) {
+      const float4 d4 = ld4(d + base), q4 = ld4(a.q32 + base), m4 = ld4(a.dinv32 + base);
+      float4 x4 = ld4(a.x32 + base), r4 = ld4(a.r32 + base), z4;
+      x4.x = __fmaf_rn(alpha, d4.x, x4.x);
+      x4.y = __fmaf_rn(alpha, d4.y, x4.y);
+      x4.z = __fmaf_rn(alpha, d4.z, x4.z);
+      x4.w = __fmaf_rn(alpha, d4.w, x4.w);
+      r4.x = __fmaf_rn(-alpha, q4.x, r4.x);
+      r4.y = __fmaf_rn(-alpha, q4.y, r4.y);
+      r4.z = __fmaf_rn(-alpha, q4.z, r4.z);
+      r4.w = __fmaf_rn(-alpha, q4.w, r4.w);
+      z4.x = __fmul_rn(m4.x, r4.x);
+      z4.y = __fmul_rn(m4.y, r4.y);
+      z4.z = __fmul_rn(m4.z, r4.z);
+      z4.w = __fmul_rn(m4.w, r4.w);
+      *reinterpret_cast<float4*>(a.x32 + base) = x4;
+      *reinterpret_cast<float4*>(a.r32 + base) = r4;
+      *reinterpret_cast<float4*>(a.z32 + base) = z4;
+      ff_add_prod(prr, r4.x, r4.x);
+      ff_add_prod(prr, r4.y, r4.y);
+      ff_add_prod(prr, r4.z, r4.z);
+      ff_add_prod(prr, r4.w, r4.w);
+      ff_add_prod(prz, r4.x, z4.x);
+      ff_add_prod(prz, r4.y, z4.y);
+      ff_add_prod(prz, r4.z, z4.z);
+      ff_add_prod(prz, r4.w, z4.w);
+    } else {
+      for (int i = base; i < R1; ++i) {
+        a.x32[i] = __fmaf_rn(alpha, d[i], a.x32[i]);
+        const float ri = __fmaf_rn(-alpha, a.q32[i], a.r32[i]);
+        const float zi = __fmul_rn(a.dinv32[i], ri);
+        a.r32[i] = ri;
+        a.z32[i] = zi;
+        ff_add_prod(prr, ri, ri);
+        ff_add_prod(prz, ri, zi);
+      }
+    }
+  }
+}
+
 enum Dec { kGo = 0, kStop = 1, kNan = 2, kBroke = 3, kBreakdown = 4 };
 
+// kPc: Jacobi-preconditioned CG (the PCG form of Sec. 5): z = dinv r is
+// kept beside r, d is formed from z, alpha = r^T z / d^T q and
+// beta = r'^T z' / r^T z; the stop test and v stay on r.
+template <bool kPc>
 __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
   constexpr int NC = kNC;
   extern __shared__ __align__(128) char smem[];
@@ -573,19 +626,26 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
   bool ok = true;
 
   double rr, bnorm;  // identical in every thread after each broadcast
+  double rz = 0.0;   // r^T z (kPc; thread 0)
   float beta;
   int first, parity, it;
   if (a.mode != kCgContinue) {
-    // CG line 1: x0 = 0, r0 = b - A x0 = b~, d0 = r0.
-    FF acc{0.f, 0.f};
+    // CG line 1: x0 = 0, r0 = b - A x0 = b~, d0 = r0 (kPc: z0 = dinv r0, d0 = z0).
+    FF acc{0.f, 0.f}, accz{0.f, 0.f};
     for (int i = R0 + lane; i < R1; i += kSlice) {
       const float bi = a.b32[i];
       a.x32[i] = 0.0f;
       a.r32[i] = bi;
       a.da[i] = 0.0f;  // d_{-1}
       ff_add_prod(acc, bi, bi);
+      if constexpr (kPc) {
+        const float zi = __fmul_rn(a.dinv32[i], bi);
+        a.z32[i] = zi;
+        ff_add_prod(accz, bi, zi);
+      }
     }
     const double tot = cgrid_total(block_ff(acc, S), a.partials, red, ctl, a.slot, round, S, ok);
+    if constexpr (kPc) rz = cgrid_total(block_ff(accz, S), a.partials, red, ctl, a.slot, round, S, ok);
     if (lead) {
       S.rr = tot;
       S.val = sqrt(tot);  // ||b~|| = ||r0||
@@ -609,6 +669,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
     first = ctl->first;
     parity = ctl->parity;
     it = ctl->n1;
+    if constexpr (kPc) rz = ctl->rz;
   }
   const double eps = a.mode == kCgK0 ? ctl->eps2 : ctl->eps1;
   const int limit = a.mode == kCgK0 ? min(ctl->k0, ctl->max1) : ctl->max1;
@@ -632,7 +693,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
     // this launch, so they must not go through the read-only data path.
     const float* dold = parity ? a.db : a.da;
     float* dnew = parity ? a.da : a.db;
-    const float* r = a.r32;
+    const float* r = kPc ? a.z32 : a.r32;  // d is formed from z under kPc
     float* q = a.q32;
     FF pdq{0.f, 0.f};
     // d_0 = r_0 is the same formula with beta = 0 and d_{-1} = 0 (zeroed at
@@ -655,7 +716,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
         int dec = kGo;
         if (!isfinite(dq)) dec = kNan;
         else if (!(dq > 0.0)) dec = kBroke;  // stage 1 ends here; x and r are unchanged
-        else S.alpha = (float)(rr / dq);
+        else S.alpha = (float)((kPc ? rz : rr) / dq);
         S.dec = dec;
         if (dec == kNan && lead0) set_status(ctl, MPCG_ERR_NAN);
       }
@@ -669,19 +730,28 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
     if (S.dec != kGo) break;
     const float alpha = S.alpha;
 
-    // ---- P2: x += alpha d_k, r -= alpha q, r^T r ----
-    FF prr{0.f, 0.f};
-    p2_32(a, R0, R1, lane, dnew, alpha, prr);
+    // ---- P2: x += alpha d_k, r -= alpha q, r^T r (kPc: also z = dinv r, r^T z) ----
+    FF prr{0.f, 0.f}, prz{0.f, 0.f};
+    if constexpr (kPc) p2_32_pc(a, R0, R1, lane, dnew, alpha, prr, prz);
+    else p2_32(a, R0, R1, lane, dnew, alpha, prr);
     {
       const double rrn = cgrid_total(block_ff(prr, S), a.partials, red, ctl, a.slot, round, S, ok);
+      double rzn = 0.0;
+      if constexpr (kPc)
+        rzn = cgrid_total(block_ff(prz, S), a.partials, red, ctl, a.slot, round, S, ok);
       if (lead) {
         int dec = kGo;
-        if (!isfinite(rrn)) {
+        if (!isfinite(rrn) || (kPc && !isfinite(rzn))) {
           dec = kNan;
           if (lead0) set_status(ctl, MPCG_ERR_NAN);
         } else {
           if (a.mode == kCgK0) vsum += sqrt(rrn) / sqrt(rr);  // Eq. (13) ratio
-          S.beta = (float)(rrn / rr);
+          if constexpr (kPc) {
+            S.beta = (float)(rzn / rz);
+            rz = rzn;
+          } else {
+            S.beta = (float)(rrn / rr);
+          }
           S.rr = rrn;
         }
         S.dec = dec;
@@ -700,6 +770,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
 
   if (lead0) {
     ctl->rr = rr;
+    if constexpr (kPc) ctl->rz = rz;
     ctl->beta32 = beta;
     ctl->first = first;
     ctl->parity = parity;
@@ -811,9 +882,59 @@ __device__ __forceinline__ void p3_64(const CgArgs& a, int R0, int R1, int lane,
   }
 }
 
+// Preconditioned P2: x += alpha d, r -= alpha q; returns r^T r and, in
+// *prz, r^T z with z = dinv r (z is not stored: P3 forms it again).
+__device__ __forceinline__ double p2_64_pc(const CgArgs& a, int R0, int R1, int lane, double alpha,
+                                           double* prz) {
+  double prr = 0.0, pz = 0.0;
+  for (int g = R0 + 2 * lane; g < R1; g += 2 * kSlice) {
+    if (g + 2 <= R1) {
+      const double2 d2 = ld2(a.d64 + g), q2 = ld2(a.q64 + g), m2 = ld2(a.dinv64 + g);
+      double2 x2 = ld2(a.x64 + g), r2 = ld2(a.r64 + g);
+      x2.x = __fma_rn(alpha, d2.x, x2.x);
+      x2.y = __fma_rn(alpha, d2.y, x2.y);
+      r2.x = __fma_rn(-alpha, q2.x, r2.x);
+      r2.y = __fma_rn(-alpha, q2.y, r2.y);
+      *reinterpret_cast<double2*>(a.x64 + g) = x2;
+      *reinterpret_cast<double2*>(a.r64 + g) = r2;
+      prr = __fma_rn(r2.x, r2.x, prr);
+      prr = __fma_rn(r2.y, r2.y, prr);
+      pz = __fma_rn(r2.x, __dmul_rn(m2.x, r2.x), pz);
+      pz = __fma_rn(r2.y, __dmul_rn(m2.y, r2.y), pz);
+    } else if (g < R1) {
+      a.x64[g] = __fma_rn(alpha, a.d64[g], a.x64[g]);
+      const double ri = __fma_rn(-alpha, a.q64[g], a.r64[g]);
+      a.r64[g] = ri;
+      prr = __fma_rn(ri, ri, prr);
+      pz = __fma_rn(ri, __dmul_rn(a.dinv64[g], ri), pz);
+    }
+  }
+  *prz = pz;
+  return prr;
+}
+
+// Preconditioned P3: d = dinv r + beta d.
+__device__ __forceinline__ void p3_64_pc(const CgArgs& a, int R0, int R1, int lane, double beta) {
+  for (int g = R0 + 2 * lane; g < R1; g += 2 * kSlice) {
+    if (g + 2 <= R1) {
+      double2 d2 = ld2(a.d64 + g);
+      const double2 r2 = ld2(a.r64 + g), m2 = ld2(a.dinv64 + g);
+      d2.x = __fma_rn(beta, d2.x, __dmul_rn(m2.x, r2.x));
+      d2.y = __fma_rn(beta, d2.y, __dmul_rn(m2.y, r2.y));
+      *reinterpret_cast<double2*>(a.d64 + g) = d2;
+    } else if (g < R1) {
+      a.d64[g] = __fma_rn(beta, a.d64[g], __dmul_rn(a.dinv64[g], a.r64[g]));
+    }
+  }
+}
+
 // Kinds of SpMV pass in the double-precision stage.
 enum Pass64 { kRestart = 0, kTrueRes = 1, kIterate = 2, kFinalRes = 3, kDone = 4 };
 
+// kPc: Jacobi-preconditioned CG (the PCG form of Sec. 5): restarts set
+// d = z = dinv r, alpha = r^T z / d^T q, beta = r'^T z' / r^T z and
+// d = z + beta d; the stop test and the true residual stay on r.
+template <bool kPc>
 __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
   constexpr int NC = kNC;
   extern __shared__ __align__(128) char smem[];
@@ -855,6 +976,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
   double true_rel = NAN;  // thread 0
   const StopThr thr2 = stop_thr(eps2, bnorm, rel);  // used by thread 0
   double rr = 0.0;                 // thread 0
+  double rz = 0.0;                 // r^T z (kPc; thread 0)
 
   // Promote: x0 = float64(x~) (or 0).
   {
@@ -873,7 +995,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
   const double* x = a.x64;
   while (ok && kind != kDone) {
     const double* gv = kind == kIterate ? a.d64 : x;
-    double p = 0.0;
+    double p = 0.0, pz = 0.0;
     {
       const int knd = kind;
       double* r = a.r64;
@@ -890,7 +1012,13 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
             const double ri = b[i] - acc;
             if (knd == kRestart) {
               r[i] = ri;
-              d[i] = ri;
+              if constexpr (kPc) {
+                const double zi = __dmul_rn(a.dinv64[i], ri);
+                d[i] = zi;
+                pz = __fma_rn(ri, zi, pz);
+              } else {
+                d[i] = ri;
+              }
             } else if (knd == kTrueRes) {
               q[i] = ri;
             }
@@ -901,6 +1029,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
       if (!ring_spmv<NC, double>(a, R, C, S0, S1, G, Rw)) set_status(ctl, MPCG_ERR_TIMEOUT);
     }
     const double tot = cgrid_total(block_d(p, S), a.partials, red, ctl, a.slot, round, S, ok);
+    if constexpr (kPc) {
+      if (kind == kRestart) {  // uniform: r^T z of the restart
+        const double tz = cgrid_total(block_d(pz, S), a.partials, red, ctl, a.slot, round, S, ok);
+        if (lead) rz = tz;
+      }
+    }
     if (!ok) break;
 
     // ---- thread 0: the scalars and the next pass ----
@@ -921,7 +1055,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
         } else if (!(tot > 0.0)) {
           failed = MPCG_ERR_BREAKDOWN;
         } else {
-          S.val = rr / tot;  // alpha
+          S.val = (kPc ? rz : rr) / tot;  // alpha
           next = kIterate;
         }
       } else {  // kRestart
@@ -936,33 +1070,57 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
     if (kind == kIterate && next == kIterate) {
       // ---- P2: x += alpha d, r -= alpha q, r^T r ----
       const double alpha = S.val;
-      const double prr = p2_64(a, R0, R1, lane, alpha);
+      double przl = 0.0;
+      double prr;
+      if constexpr (kPc) prr = p2_64_pc(a, R0, R1, lane, alpha, &przl);
+      else prr = p2_64(a, R0, R1, lane, alpha);
       const double rrn = cgrid_total(block_d(prr, S), a.partials, red, ctl, a.slot, round, S, ok);
+      double rzn = 0.0;
+      if constexpr (kPc)
+        rzn = cgrid_total(block_d(przl, S), a.partials, red, ctl, a.slot, round, S, ok);
       if (lead) {
-        if (!isfinite(rrn)) {
+        if (!isfinite(rrn) || (kPc && !isfinite(rzn))) {
           failed = MPCG_ERR_NAN;
           S.dec = kDone;
         } else {
-          S.val = rrn / rr;  // beta
+          if constexpr (kPc) {
+            S.val = rzn / rz;  // beta
+            rz = rzn;
+          } else {
+            S.val = rrn / rr;  // beta
+          }
           rr = rrn;
           S.dec = -1;
         }
       }
       cbar<NC>();
       if (!ok || S.dec == kDone) break;
-      // ---- P3: d = r + beta d ----
-      p3_64(a, R0, R1, lane, S.val);
+      // ---- P3: d = r + beta d (kPc: d = dinv r + beta d) ----
+      if constexpr (kPc) p3_64_pc(a, R0, R1, lane, S.val);
+      else p3_64(a, R0, R1, lane, S.val);
       ok = cgrid_barrier<NC>(ctl, a.slot, round, &S.ok);
       ++it;
       next = -1;
     } else if (next == kTrueRes + 100) {
       ++restarts;
+      double pzr = 0.0;
       for (int i = R0 + lane; i < R1; i += kSlice) {
         const double ri = a.q64[i];
         a.r64[i] = ri;
-        a.d64[i] = ri;
+        if constexpr (kPc) {
+          const double zi = __dmul_rn(a.dinv64[i], ri);
+          a.d64[i] = zi;
+          pzr = __fma_rn(ri, zi, pzr);
+        } else {
+          a.d64[i] = ri;
+        }
       }
-      ok = cgrid_barrier<NC>(ctl, a.slot, round, &S.ok);
+      if constexpr (kPc) {
+        const double tz = cgrid_total(block_d(pzr, S), a.partials, red, ctl, a.slot, round, S, ok);
+        if (lead) rz = tz;
+      } else {
+        ok = cgrid_barrier<NC>(ctl, a.slot, round, &S.ok);
+      }
       next = -1;
     }
     if (next == -1) {  // loop head: stop test on the recursive residual
@@ -1458,6 +1616,9 @@ static CgArgs make_args(const Launch& L, int slot, int mode) {
   a.d64 = L.ws.d64;
   a.q64 = L.ws.q64;
   a.snap = L.ws.snap;
+  a.dinv64 = L.dinv64;
+  a.dinv32 = L.dinv32;
+  a.z32 = L.z32;
   return a;
 }
 
@@ -1474,9 +1635,11 @@ int cg_grid(int requested) {
     struct K {
       const void* f;
       size_t smem;
-    } ks[3] = {{(const void*)k_cg32, ring_smem_bytes<float>()},
-               {(const void*)k_cg64, ring_smem_bytes<double>()},
-               {(const void*)k_stage1, ring_smem_bytes<float>()}};
+    } ks[5] = {{(const void*)k_cg32<false>, ring_smem_bytes<float>()},
+               {(const void*)k_cg64<false>, ring_smem_bytes<double>()},
+               {(const void*)k_stage1, ring_smem_bytes<float>()},
+               {(const void*)k_cg32<true>, ring_smem_bytes<float>()},
+               {(const void*)k_cg64<true>, ring_smem_bytes<double>()}};
     int sms = 0, per = 1 << 30;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return 0;
@@ -1498,8 +1661,8 @@ int cg_grid(int requested) {
   return (requested > 0 && requested < c) ? requested : c;
 }
 
-const void* cg32_kernel() { return (const void*)k_cg32; }
-const void* cg64_kernel() { return (const void*)k_cg64; }
+const void* cg32_kernel() { return (const void*)k_cg32<false>; }
+const void* cg64_kernel() { return (const void*)k_cg64<false>; }
 const void* stage1_kernel() { return (const void*)k_stage1; }
 
 cudaError_t launch_cg32(const Launch& L, int mode, int slot) {
@@ -1507,8 +1670,9 @@ cudaError_t launch_cg32(const Launch& L, int mode, int slot) {
   void* args[] = {&a};
   const int g = cg_grid(L.grid_req);
   if (g <= 0) return cudaErrorInvalidConfiguration;
-  return cudaLaunchCooperativeKernel((const void*)k_cg32, dim3(g), dim3(kTmaThreads), args,
-                                    ring_smem_bytes<float>(), L.st);
+  const void* k = L.precond ? (const void*)k_cg32<true> : (const void*)k_cg32<false>;
+  return cudaLaunchCooperativeKernel(k, dim3(g), dim3(kTmaThreads), args, ring_smem_bytes<float>(),
+                                     L.st);
 }
 
 cudaError_t launch_cg64(const Launch& L, const double* b, double* x, int from_zero, int slot) {
@@ -1518,8 +1682,9 @@ cudaError_t launch_cg64(const Launch& L, const double* b, double* x, int from_ze
   void* args[] = {&a};
   const int g = cg_grid(L.grid_req);
   if (g <= 0) return cudaErrorInvalidConfiguration;
-  return cudaLaunchCooperativeKernel((const void*)k_cg64, dim3(g), dim3(kTmaThreads), args,
-                                    ring_smem_bytes<double>(), L.st);
+  const void* k = L.precond ? (const void*)k_cg64<true> : (const void*)k_cg64<false>;
+  return cudaLaunchCooperativeKernel(k, dim3(g), dim3(kTmaThreads), args,
+                                     ring_smem_bytes<double>(), L.st);
 }
 
 cudaError_t launch_stage1(const Launch& L, const mpcg_sample_t& S, const mpcg_options_t& o,

@@ -53,6 +53,7 @@ struct Ctl {
   // device clock marks (ns)
   unsigned long long t_start, t_prep, t_features, t_fp32, t_fp64, t_end;
   int bfs_starts;  // 2BFS runs for l~ (the repeated 2BFS of Sec. 6; 1 = the single run)
+  double rz;       // r^T z of the preconditioned single-precision stage (carried to Continue)
 };
 
 // ---------------------------------------------------------------------------------------

@@ -26,7 +26,15 @@ struct Launch {
   cudaStream_t st;
   int grid;      // persistent grid of the BFS / component kernels
   int grid_req;  // requested grid (0 = one full wave)
+  // Jacobi preconditioning (option precond), carved past the workspace map
+  int precond;
+  double* dinv64;  // 1 / a_ii
+  float* dinv32;   // 1 / float32(a_ii)
+  float* z32;      // z = dinv32 r of the single-precision stage
 };
+
+// Bytes of the preconditioner arrays past the workspace map (0 without).
+size_t precond_bytes(int n, int precond);
 
 int persistent_grid(const void* kernel, int threads, int requested, size_t dyn_smem = 0);
 
@@ -36,6 +44,7 @@ bool sample_ok(const mpcg_sample_t* s);
 
 // prep.cu
 cudaError_t launch_init(const Launch& L, const mpcg_options_t& o, int fp64_only);
+cudaError_t launch_jacobi(const Launch& L);
 cudaError_t launch_prep(const Launch& L, const double* b);
 cudaError_t launch_finalize(const Launch& L, mpcg_result_t* res, mpcg_features_t* feat);
 

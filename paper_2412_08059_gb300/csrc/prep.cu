@@ -98,6 +98,43 @@ __global__ void k_init(Ctl* c, int n, int nnz, int nslices, int wcap, mpcg_optio
   c->first = 1;
   c->x32_src = -1;
   c->bfs_starts = o.bfs_starts > 1 ? o.bfs_starts : 1;
+  c->rz = 0.0;
+}
+
+// Jacobi preconditioner M = diag(A) (the PCG form of Sec. 5), one thread per
+// row: dinv64 = 1 / a_ii and dinv32 = 1 / float32(a_ii), each a correctly
+// rounded division in its precision.  A row without a stored diagonal, or
+// with a_ii zero or not finite, makes M singular: MPCG_ERR_INVALID_ARG.
+__global__ void k_jacobi(Ctl* c, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                         const double* __restrict__ val, int n, double* dinv64, float* dinv32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = 0.0;
+  int found = 0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e)
+    if (col[e] == i) {
+      a = val[e];
+      found = 1;
+    }
+  if (!found || !(a != 0.0) || !isfinite(a)) {
+    set_status(c, MPCG_ERR_INVALID_ARG);
+    a = 1.0;
+  }
+  dinv64[i] = __ddiv_rn(1.0, a);
+  dinv32[i] = __fdiv_rn(1.0f, __double2float_rn(a));
+}
+
+size_t precond_bytes(int n, int precond) {
+  if (!precond || n <= 0) return 0;
+  auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  return a(sizeof(double) * (size_t)n) + a(sizeof(float) * (size_t)n) + a(sizeof(float) * (size_t)n);
+}
+
+cudaError_t launch_jacobi(const Launch& L) {
+  const int n = L.d.n;
+  k_jacobi<<<(n + 255) / 256, 256, 0, L.st>>>(L.ws.ctl, L.A->row_ptr, L.A->col, L.A->val, n,
+                                              L.dinv64, L.dinv32);
+  return cudaGetLastError();
 }
 
 // One thread per row (padded to whole slices): checks the CSR rules, writes

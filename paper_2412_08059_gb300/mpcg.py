@@ -56,7 +56,7 @@ class Options(C.Structure):
                 ("fp64_only", C.c_int32), ("grid_blocks", C.c_int32), ("timeout_ms", C.c_int32),
                 ("stage1_only", C.c_int32), ("team_rows", C.c_int32),
                 ("serve_split", C.c_int32), ("bfs_starts", C.c_int32),
-                ("reserved", C.c_int32 * 1)]
+                ("precond", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -209,20 +209,22 @@ class DeviceSample:
                                (C.c_double * 4)(*fmin), (C.c_double * 4)(*fmax))
 
 
-def workspace_bytes(n: int, nnz: int) -> int:
-    return int(load().mpcg_workspace_bytes(n, nnz, None))
+def workspace_bytes(n: int, nnz: int, opts: Options | None = None) -> int:
+    """mpcg_workspace_bytes; the options matter only with precond (16 n more bytes)."""
+    return int(load().mpcg_workspace_bytes(n, nnz, C.byref(opts) if opts is not None else None))
 
 
-def workspace(n: int, nnz: int, device="cuda") -> torch.Tensor:
-    """A device byte buffer large enough for (n, nnz), base 256-byte aligned."""
-    nb = workspace_bytes(n, nnz)
+def workspace(n: int, nnz: int, device="cuda", opts: Options | None = None) -> torch.Tensor:
+    """A device byte buffer large enough for (n, nnz) and the options, base
+    256-byte aligned."""
+    nb = workspace_bytes(n, nnz, opts)
     if nb == 0:
         raise ValueError("invalid sizes")
     return torch.empty(nb, dtype=torch.uint8, device=device)
 
 
-def _ws_for(A: DeviceCSR, ws):
-    return workspace(A.n, A.nnz, A.val.device) if ws is None else ws
+def _ws_for(A: DeviceCSR, ws, opts: Options | None = None):
+    return workspace(A.n, A.nnz, A.val.device, opts) if ws is None else ws
 
 
 def result_buffer(count: int = 1, device="cuda") -> torch.Tensor:
@@ -260,15 +262,17 @@ def solve(A: DeviceCSR, b: torch.Tensor, sample: DeviceSample | None = None, ws=
     """mpcg_solve; returns (x, result dict) after synchronising."""
     x = torch.empty(A.n, dtype=torch.float64, device=b.device)
     res = result_buffer(1, b.device)
-    solve_async(A, b, x, options(**kw), _ws_for(A, ws), res, sample)
+    o = options(**kw)
+    solve_async(A, b, x, o, _ws_for(A, ws, o), res, sample)
     torch.cuda.synchronize(b.device)
     return x, read_results(res)[0]
 
 
 def features(A: DeviceCSR, b: torch.Tensor, ws=None, **kw) -> dict:
     out = torch.zeros(C.sizeof(Features), dtype=torch.uint8, device=b.device)
-    w = _ws_for(A, ws)
-    st = load().mpcg_features(C.byref(A.desc), _ptr(b), C.byref(options(**kw)), _ptr(w),
+    o = options(**kw)
+    w = _ws_for(A, ws, o)
+    st = load().mpcg_features(C.byref(A.desc), _ptr(b), C.byref(o), _ptr(w),
                               w.numel(), _ptr(out), _stream())
     _check(st, "mpcg_features")
     f = Features.from_buffer_copy(bytes(out.cpu().numpy()))
