@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving section")
     ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--no-pcg", action="store_true", help="skip the preconditioned-CG section")
+    ap.add_argument("--pcg-only", action="store_true", help="run only the preconditioned-CG section")
     ap.add_argument("--paper-eval", type=float, default=0.0,
                     help="run the paper's evaluation protocol (Sec. 12) at this fraction of its "
                          "general-sample sizes (0: skip)")
@@ -68,6 +70,61 @@ def parse():
     ap.add_argument("--paper-eval-only", action="store_true",
                     help="run only the evaluation protocol")
     return ap.parse_args()
+
+
+def pcg_section(dev, steps=5, warmup=2):
+    """Jacobi-preconditioned mixed CG (the PCG form of Sec. 5; option precond)
+    against plain CG on a system with an uneven diagonal: a random banded
+    matrix, n = 2^20, full bandwidth 15, density 0.6, values by Algorithm III
+    and a_ii = 1.1 sum_j |a_ij|; x* ~ U[-1, 1], eps2 = 1e-10.  Algorithm I at
+    eps1 = 1e-5 and pure FP64, each with and without the preconditioner:
+    time to solution (CUDA events, inputs resident), N1, N2 and the
+    algorithmic bandwidth of each stage (the preconditioner adds 8 n bytes to
+    an FP32 iteration -- dinv read, z written -- and 16 n to an FP64 one)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2412_08059_gb300 import mpcg
+
+    A = synth.banded(1 << 20, 15, 0.6, 1.1, seed=13)
+    _, b = synth.rhs(A, seed=14)
+    dA = mpcg.DeviceCSR.from_host(A, dev)
+    db = torch.from_numpy(b).to(dev)
+    n, m = A.n, A.nnz
+    runs = {}
+    for name, kw in (("mixed_pcg", dict(eps1=1e-5, precond=1)), ("mixed_cg", dict(eps1=1e-5)),
+                     ("fp64_pcg", dict(fp64_only=1, precond=1)), ("fp64_cg", dict(fp64_only=1))):
+        o = mpcg.options(**kw)
+        ws = mpcg.workspace(n, m, dev, o)
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        res = mpcg.result_buffer(1, dev)
+        for _ in range(warmup):
+            mpcg.solve_async(dA, db, x, o, ws, res)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            mpcg.solve_async(dA, db, x, o, ws, res)
+        e1.record()
+        torch.cuda.synchronize()
+        r = mpcg.read_results(res)[0]
+        pc = kw.get("precond", 0)
+        b32 = algorithmic_bytes(n, m, 4) + (8 * n if pc else 0)
+        b64 = algorithmic_bytes(n, m, 8) + (16 * n if pc else 0)
+        out = {"ms": round(e0.elapsed_time(e1) / steps, 3), "n1": r["n1"], "n2": r["n2"],
+               "status": r["status"], "true_rel_resid": r["true_rel_resid"]}
+        if r["n1"] > 0 and r["ms_fp32"] > 0:
+            out["stage1_GBps"] = round(b32 * r["n1"] / (r["ms_fp32"] / 1e3) / 1e9, 1)
+        if r["n2"] > 0 and r["ms_fp64"] > 0:
+            out["stage2_GBps"] = round(b64 * r["n2"] / (r["ms_fp64"] / 1e3) / 1e9, 1)
+        runs[name] = out
+        del ws
+    return {"workload": "banded n=2^20, b=15, p=0.6, Algorithm III values, mu=1.1; eps1=1e-5 "
+                        "(Algorithm I), eps2=1e-10", "n": n, "nnz": m, "runs": runs,
+            "speedup_pcg_over_cg": {"mixed": runs["mixed_cg"]["ms"] / runs["mixed_pcg"]["ms"],
+                                    "fp64": runs["fp64_cg"]["ms"] / runs["fp64_pcg"]["ms"]},
+            "speedup_mixed_over_fp64_with_pcg": runs["fp64_pcg"]["ms"] / runs["mixed_pcg"]["ms"]}
 
 
 def paper_eval_section(args):
@@ -518,6 +575,10 @@ def native_arm(args, rank, world, local_rank):
         if rank == 0:
             print(json.dumps({"serve": serve_section(args, dev)}), flush=True)
         return
+    if args.pcg_only:
+        if rank == 0:
+            print(json.dumps({"pcg": pcg_section(dev)}), flush=True)
+        return
     if args.paper_eval_only:
         if rank == 0:
             args.paper_eval = args.paper_eval or 0.1
@@ -795,6 +856,9 @@ def native_arm(args, rank, world, local_rank):
     serve = None
     if not args.no_serve and rank == 0 and world == 1:
         serve = serve_section(args, dev)
+    pcg = None
+    if not args.no_pcg and rank == 0 and world == 1:
+        pcg = pcg_section(dev)
     paper = None
     if args.paper_eval > 0 and rank == 0 and world == 1:
         paper = paper_eval_section(args)
@@ -817,7 +881,7 @@ def native_arm(args, rank, world, local_rank):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": KERNELS_PER_SOLVE_AUTO * nsys * args.steps,
                 "clocks": clocks, "systems": per, "eps1_sweep": sweep, "batch": batch, "serve": serve,
-                "paper_eval": paper,
+                "pcg": pcg, "paper_eval": paper,
                 "sample": {"desc": sample_desc, "seconds_to_build": round(t_sample, 1),
                            "labels": np.bincount(cls, minlength=8)[2:].tolist()}}
         print(json.dumps(line), flush=True)
