@@ -145,6 +145,19 @@ def test_knn_batch_matches_oracle(mp, count, k, weighted, mask):
 
 
 @pytest.mark.gpu
+def test_knn_batch_empty_query_and_small_sample(mp):
+    feat, cls = synth.random_sample(3, seed=1)
+    S = mp.DeviceSample(feat, cls)
+    got, nbr = mp.knn_batch(np.zeros((0, 4)), S, neighbours=True, knn_k=5)
+    assert got.numel() == 0 and tuple(nbr.shape) == (0, 5)
+    got, nbr = mp.knn_batch(feat, S, neighbours=True, knn_k=5)   # k > sample size
+    for i in range(3):
+        t, nb, _ = oracle.knn(feat[i], oracle.sample(feat, cls), k=5, details=True)
+        assert got[i].item() == t and list(nbr[i, :3].cpu().numpy()) == list(nb)
+        assert np.all(nbr[i, 3:].cpu().numpy() == -1)
+
+
+@pytest.mark.gpu
 def test_sweep_of_a_small_general_sample_matches_oracle(mp):
     descs = ev.general_sample("xstar", 301, per=1, seed=9)[::3]   # 10 stars, one per (lc, nc)
     rec = ev.sweep_records(descs)
