@@ -18,7 +18,10 @@
  *   - Every array argument is DEVICE memory owned by the caller unless the
  *     parameter says otherwise.  The library never allocates device memory:
  *     it carves the caller's workspace `ws` (size from mpcg_workspace_bytes).
- *   - Calls are stream-ordered on `stream` and never synchronise the host.
+ *   - Calls are stream-ordered on `stream`.  The single-system calls never
+ *     synchronise the host; mpcg_solve_batch and mpcg_batch_step copy their
+ *     descriptor tables from pageable host memory, which by CUDA's rule
+ *     waits for earlier work on the stream; mpcg_batch_tune synchronises.
  *     The workspace, the outputs and the inputs must stay valid until the
  *     stream reaches the end of the call's work.  Two calls that share a
  *     workspace must not overlap on the GPU.
