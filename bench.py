@@ -38,9 +38,9 @@ UNIT = "solves/s"
 KERNELS_PER_SOLVE_AUTO = 9    # k_init, k_rows, k_scan, k_fill, k_bnorm_*(2), k_stage1, k_cg64,
                                # k_finalize: the kernels one Algorithm II solve launches
 KERNELS_PER_SOLVE_FP64 = 8
-# DRAM bytes per FP64 iteration of k_cg64 at 128^3 from one ncu capture (65.61 GB over 307
+# DRAM bytes per FP64 iteration of k_cg64 at 128^3 from one ncu capture (65.92 GB over 307
 # passes of the captured launch); profiles/k_cg64_lap3d128.md.
-K_CG64_DRAM_BYTES_PER_ITER = 65.61e9 / 307
+K_CG64_DRAM_BYTES_PER_ITER = 65.92e9 / 307
 
 
 def parse():
