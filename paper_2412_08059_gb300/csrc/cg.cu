@@ -44,7 +44,6 @@
 namespace mpcg {
 
 constexpr int kNC = 15;                       // consumer warps per block
-constexpr int kMaxTaggedGrid = 14 * 32;        // blocks a tagged grid sum can serve
 constexpr int kTmaThreads = (kNC + 1) * 32;   // + one producer warp
 constexpr int kLogCH = 12;
 constexpr int kCH = 1 << kLogCH;              // elements per streamed chunk
@@ -116,7 +115,6 @@ __device__ __forceinline__ void cbar() {
 template <int NC>
 struct CShared {
   double part[NC * 32];
-  double gpart[NC * 32];  // the grid's partials of cgrid_sum_tagged, by block
   float ffp[2 * NC];
   double rr, val;
   float alpha, beta;
@@ -210,105 +208,6 @@ __device__ __forceinline__ double cgrid_total(double block_part, double* partial
   double s = 0.0;
   if (threadIdx.x < 32) {
     for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) s += buf[i];
-    s = warp_sum(s);
-  }
-  return s;
-}
-
-// Grid-wide sum through tagged slots: no arrival counter, so the partials
-// arrive with the synchronisation itself.
-//
-// Block b's thread 0 writes its partial into slot b as two 64-bit words, each
-// holding the reduction's tag in its upper half and one half of the double's
-// bits in its lower half.  Each word is a single-copy atomic access, so a
-// word that carries the current tag carries the current half.  Consumer
-// thread j of every block polls slot j until both tags match and parks the
-// value in shared memory; warp 0 then adds the partials in the order of
-// cgrid_total, so the total is bitwise the same.  Needs gridDim.x <= NC * 32
-// (cg_grid caps the grid at kMaxTaggedGrid).
-//
-// Tags: ((slot + 1) << 24) | count.  A launch owns its barrier slot within
-// one library call and the host zeroes the tagged area at the start of every
-// call, so a stale word never carries a current tag.  The two buffers
-// alternate: a block writes reduction k + 2 only after reading reduction
-// k + 1 complete, which every block wrote after it had read reduction k.
-//
-// fence = false is for reductions after which every thread reads only rows
-// of its own block (ordered by the block barrier): no fence on either side,
-// so the writer does not wait for its block's vector stores to drain.  With
-// fence = true, a fence before the write and after the reads makes it a
-// grid barrier for memory as well, like cgrid_barrier; every polling thread
-// then fences, which costs more than cgrid_total's single acquire (measured:
-// 42.9 -> 46.4 us per single-precision iteration when used for r^T r), so it
-// serves only the rare passes.
-template <int NC>
-__device__ __forceinline__ bool cbar_and(bool v) {
-  int r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 q, %1, 0;\n\t"
-      "bar.red.and.pred p, 1, %2, q;\n\tselp.s32 %0, 1, 0, p;\n\t}"
-      : "=r"(r)
-      : "r"((int)v), "r"(NC * 32)
-      : "memory");
-  return r != 0;
-}
-
-template <int NC>
-__device__ __forceinline__ double cgrid_sum_tagged(double block_part, double* partials,
-                                                   unsigned& cnt, int slot, bool fence, Ctl* ctl,
-                                                   CShared<NC>& S, bool& ok) {
-  ++cnt;
-  const unsigned tag = ((unsigned)(slot + 1) << 24) | (cnt & 0xffffffu);
-  unsigned long long* buf = reinterpret_cast<unsigned long long*>(partials + 2 * kMaxGrid) +
-                            (size_t)(cnt & 1u) * 2 * kMaxGrid;
-  const int nb = (int)gridDim.x;
-  if (threadIdx.x == 0) {
-    if (fence) __threadfence();
-    const unsigned long long t = (unsigned long long)tag << 32;
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(block_part);
-    st_relaxed_v2(buf + 2 * blockIdx.x, t | (bits & 0xffffffffull), t | (bits >> 32));
-  }
-  const int j = threadIdx.x;
-  bool good = true;
-  if ((j & ~31) < nb) {  // warp-uniform: the warps that hold slots
-    unsigned lo = 0u, hi = 0u;
-    unsigned spins = 0;
-    unsigned long long t0 = 0;
-    for (;;) {
-      bool ready = true;
-      if (j < nb) {
-        unsigned long long w0, w1;
-        ld_relaxed_v2(buf + 2 * j, w0, w1);
-        ready = (unsigned)(w0 >> 32) == tag && (unsigned)(w1 >> 32) == tag;
-        lo = (unsigned)w0;
-        hi = (unsigned)w1;
-      }
-      if (__all_sync(0xffffffffu, ready)) break;
-      if ((++spins & 63u) == 0) {
-        int bad = 0;
-        if ((j & 31) == 0) {
-          const unsigned long long now = globaltimer();
-          if (t0 == 0) t0 = now;
-          if (volatile_status(ctl) != 0) {
-            bad = 1;
-          } else if (now - t0 > (unsigned long long)ctl->timeout_ns) {
-            set_status(ctl, MPCG_ERR_TIMEOUT);
-            bad = 1;
-          }
-        }
-        if (__shfl_sync(0xffffffffu, bad, 0)) {
-          good = false;
-          break;
-        }
-      }
-    }
-    if (j < nb) S.gpart[j] = __hiloint2double((int)hi, (int)lo);
-    if (fence) __threadfence();
-  }
-  ok = cbar_and<NC>(good);
-  double s = 0.0;
-  if (threadIdx.x < 32) {
-    for (int i = threadIdx.x; i < nb; i += 32) s += S.gpart[i];
     s = warp_sum(s);
   }
   return s;
@@ -724,7 +623,6 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
   const int rel = ctl->tol_relative;
   unsigned long long round = 0;
   int red = 0;
-  unsigned tcnt = 0;
   bool ok = true;
 
   double rr, bnorm;  // identical in every thread after each broadcast
@@ -813,8 +711,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
     const bool pass_ok = ring_spmv<NC, float>(a, R, C, S0, S1, G, Rw);
     if (!pass_ok) set_status(ctl, MPCG_ERR_TIMEOUT);
     {
-      // P2 reads only the block's own rows of d_k and q: no fence.
-      const double dq = cgrid_sum_tagged(block_ff(pdq, S), a.partials, tcnt, a.slot, false, ctl, S, ok);
+      const double dq = cgrid_total(block_ff(pdq, S), a.partials, red, ctl, a.slot, round, S, ok);
       if (lead) {
         int dec = kGo;
         if (!isfinite(dq)) dec = kNan;
@@ -901,8 +798,7 @@ __device__ __forceinline__ double2 ld2(const double* p) {
 
 // x += alpha d, r -= alpha q over rows [R0, R1): two rows per lane, two
 // pairs per step with every operand loaded before the first store; returns
-// this thread's part of r^T r.  (Loading the next step's operands before
-// this step's stores needs 32 more registers and spilled.)
+// this thread's part of r^T r.
 __device__ __forceinline__ double p2_64(const CgArgs& a, int R0, int R1, int lane, double alpha) {
   double prr = 0.0;
   for (int base = R0 + 2 * lane; base < R1; base += 4 * kSlice) {
@@ -956,8 +852,6 @@ __device__ __forceinline__ double p2_64(const CgArgs& a, int R0, int R1, int lan
 }
 
 // d = r + beta d over rows [R0, R1), both pairs of a step loaded first.
-// (Loading the next step's pairs before this step's stores spilled and ran
-// 2.6 % slower.)
 __device__ __forceinline__ void p3_64(const CgArgs& a, int R0, int R1, int lane, double beta) {
   for (int base = R0 + 2 * lane; base < R1; base += 4 * kSlice) {
     const int g1 = base + 2 * kSlice;
@@ -1076,7 +970,6 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
   const int max_restarts = ctl->max_restarts;
   unsigned long long round = 0;
   int red = 0;
-  unsigned tcnt = 0;
   bool ok = true;
   int it = 0, restarts = 0;
   int failed = 0;                  // thread 0
@@ -1135,10 +1028,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
       };
       if (!ring_spmv<NC, double>(a, R, C, S0, S1, G, Rw)) set_status(ctl, MPCG_ERR_TIMEOUT);
     }
-    // After an iterate pass every block reads only its own rows until the
-    // next barrier: no fence.  The other passes are followed by gathers.
-    const double tot = cgrid_sum_tagged(block_d(p, S), a.partials, tcnt, a.slot, kind != kIterate,
-                                        ctl, S, ok);
+    const double tot = cgrid_total(block_d(p, S), a.partials, red, ctl, a.slot, round, S, ok);
     if constexpr (kPc) {
       if (kind == kRestart) {  // uniform: r^T z of the restart
         const double tz = cgrid_total(block_d(pz, S), a.partials, red, ctl, a.slot, round, S, ok);
@@ -1184,11 +1074,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
       double prr;
       if constexpr (kPc) prr = p2_64_pc(a, R0, R1, lane, alpha, &przl);
       else prr = p2_64(a, R0, R1, lane, alpha);
-      // P3 reads only the block's own rows: no fence (its barrier has one).
-      const double rrn = cgrid_sum_tagged(block_d(prr, S), a.partials, tcnt, a.slot, false, ctl, S, ok);
+      const double rrn = cgrid_total(block_d(prr, S), a.partials, red, ctl, a.slot, round, S, ok);
       double rzn = 0.0;
       if constexpr (kPc)
-        rzn = cgrid_sum_tagged(block_d(przl, S), a.partials, tcnt, a.slot, false, ctl, S, ok);
+        rzn = cgrid_total(block_d(przl, S), a.partials, red, ctl, a.slot, round, S, ok);
       if (lead) {
         if (!isfinite(rrn) || (kPc && !isfinite(rzn))) {
           failed = MPCG_ERR_NAN;
@@ -1291,7 +1180,6 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
 // decisions.
 // ---------------------------------------------------------------------------------------
 constexpr int kNC1 = 14;      // consumer warps; warp 14 = feature warp, warp 15 = producer
-static_assert(kNC1 * 32 >= kMaxTaggedGrid, "a tagged slot per consumer thread");
 constexpr int kSnapSlots = 6; // snapshots of x~ kept in the workspace
 
 struct Stage1Args {
@@ -1410,7 +1298,6 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
   const double eps2 = ctl->eps2;
   unsigned long long round = 0;
   int red = 0;
-  unsigned tcnt = 0;
   bool ok = true;
 
   // Classes present in the sample (block 0 reads the labels; the mask rides
@@ -1560,8 +1447,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
     };
     if (!ring_spmv<NC, float>(a, R, C, S0, S1, G, Rw)) set_status(ctl, MPCG_ERR_TIMEOUT);
     {
-      // P2 reads only the block's own rows of d_k and q: no fence.
-      const double dq = cgrid_sum_tagged(block_ff(pdq, S), a.partials, tcnt, a.slot, false, ctl, S, ok);
+      const double dq = cgrid_total(block_ff(pdq, S), a.partials, red, ctl, a.slot, round, S, ok);
       if (lead) {
         int d2 = kGoOn;
         if (!isfinite(dq)) {
@@ -1768,7 +1654,6 @@ int cg_grid(int requested) {
     }
     int c = per > 0 ? sms * per : -1;
     if (c > kMaxGrid - 1) c = kMaxGrid - 1;  // one reduction slot stays free
-    if (c > kMaxTaggedGrid) c = kMaxTaggedGrid;  // a slot per consumer thread
     cached[dev] = c;
   }
   const int c = cached[dev];

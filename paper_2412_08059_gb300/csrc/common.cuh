@@ -95,19 +95,6 @@ __device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned 
   asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Two 64-bit words as one instruction; each word is a relaxed, single-copy
-// atomic access at GPU scope (the pair as a whole is not).
-__device__ __forceinline__ void st_relaxed_v2(unsigned long long* p, unsigned long long a,
-                                              unsigned long long b) {
-  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b)
-               : "memory");
-}
-__device__ __forceinline__ void ld_relaxed_v2(const unsigned long long* p, unsigned long long& a,
-                                              unsigned long long& b) {
-  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p)
-               : "memory");
-}
-
 __device__ __forceinline__ void set_status(Ctl* c, int s) { atomicCAS(&c->status, 0, s); }
 
 // Stop measure of the CG procedure: ||r|| / ||b|| (relative) or ||r||.

@@ -35,10 +35,7 @@ size_t carve(const Dims& d, char* base, Ws* ws) {
   const size_t n = (size_t)d.n, S = (size_t)d.nslices, P = (size_t)d.pcap;
   Ws w{};
   w.ctl = (Ctl*)take(sizeof(Ctl));
-  // [0, 2 kMaxGrid): the counter-synchronised reductions (two buffers);
-  // [2 kMaxGrid, 6 kMaxGrid): the tagged slots of cgrid_sum_tagged (two
-  // buffers of kMaxGrid two-word slots), zeroed by launch_init.
-  w.partials = (double*)take(sizeof(double) * 6 * kMaxGrid);
+  w.partials = (double*)take(sizeof(double) * 4 * kMaxGrid);
   w.slice_w = (uint32_t*)take(sizeof(uint32_t) * S);
   w.slice_ptr = (int32_t*)take(sizeof(int32_t) * (S + 1));
   w.scol = (int32_t*)take(sizeof(int32_t) * P);
@@ -281,8 +278,6 @@ __global__ void k_bnorm_final(Ctl* c, const double* __restrict__ part, int nb) {
 
 cudaError_t launch_init(const Launch& L, const mpcg_options_t& o, int fp64_only) {
   cudaError_t e = cudaMemsetAsync(L.ws.ctl, 0, sizeof(Ctl), L.st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(L.ws.partials + 2 * kMaxGrid, 0, sizeof(double) * 4 * kMaxGrid, L.st);
   if (e != cudaSuccess) return e;
   mpcg_options_t oo = o;
   if (fp64_only) oo.eps1 = 0.0;
