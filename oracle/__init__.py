@@ -61,7 +61,8 @@ class Opts(C.Structure):
                 ("knn_k", C.c_int32), ("weighted", C.c_int32), ("tol_relative", C.c_int32),
                 ("max_it_fp32", C.c_int32), ("max_it_fp64", C.c_int32),
                 ("max_true_restarts", C.c_int32), ("feat_mask", C.c_uint32),
-                ("bfs_starts", C.c_int32), ("precond", C.c_int32)]
+                ("bfs_starts", C.c_int32), ("precond", C.c_int32),
+                ("stop_true_residual", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -89,7 +90,7 @@ def lib():
             L.orc_dot32.argtypes = [C.c_int32, P, P]
             L.orc_dot32.restype = C.c_double
             L.orc_cg64.argtypes = [C.POINTER(Csr), P, P, C.c_double, C.c_int32, C.c_int32,
-                                   C.c_int32, C.POINTER(C.c_int32), P]
+                                   C.c_int32, C.c_int32, C.POINTER(C.c_int32), P]
             L.orc_cg64.restype = C.c_int32
             L.orc_cg32.argtypes = L.orc_cg64.argtypes
             L.orc_cg32.restype = C.c_int32
@@ -199,9 +200,11 @@ def dot64(a, b):
     return lib().orc_dot64(a.size, _ptr(a), _ptr(b))
 
 
-def cg64(A, b, eps, x0=None, tol_relative=1, max_it=None, history=False, precond=0):
-    """Plain FP64 CG (Sec. 3), or with precond=1 the Jacobi PCG of Sec. 5.
-    Returns (x, iters, status[, res_hist])."""
+def cg64(A, b, eps, x0=None, tol_relative=1, max_it=None, history=False, precond=0,
+         true_res=0):
+    """Plain FP64 CG (Sec. 3), or with precond=1 the Jacobi PCG of Sec. 5;
+    true_res=1 stops on ||b - A x|| (the loop test as printed) instead of
+    the recursive r.  Returns (x, iters, status[, res_hist])."""
     h = csr(A)
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(h.n) if x0 is None else np.array(x0, dtype=np.float64)
@@ -209,14 +212,15 @@ def cg64(A, b, eps, x0=None, tol_relative=1, max_it=None, history=False, precond
     it = C.c_int32(0)
     hist = np.full(max_it + 1, np.nan) if history else None
     st = lib().orc_cg64(C.byref(h.s), _ptr(b), _ptr(x), eps, tol_relative, max_it,
-                        int(precond), C.byref(it), _ptr(hist) if history else None)
+                        int(precond), int(true_res), C.byref(it),
+                        _ptr(hist) if history else None)
     out = (x, it.value, st)
     return out + (hist[: it.value + 1],) if history else out
 
 
-def cg32(A, b, eps, tol_relative=1, max_it=None, history=False, precond=0):
-    """Plain FP32 CG on float32(A), float32(b) from 0 (precond=1: Jacobi PCG).
-    Returns (x32, iters, status[, hist])."""
+def cg32(A, b, eps, tol_relative=1, max_it=None, history=False, precond=0, true_res=0):
+    """Plain FP32 CG on float32(A), float32(b) from 0 (precond=1: Jacobi PCG;
+    true_res=1: stop on ||b~ - A~ x~||).  Returns (x32, iters, status[, hist])."""
     h = csr(A)
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(h.n, dtype=np.float32)
@@ -224,7 +228,8 @@ def cg32(A, b, eps, tol_relative=1, max_it=None, history=False, precond=0):
     it = C.c_int32(0)
     hist = np.full(max_it + 1, np.nan) if history else None
     st = lib().orc_cg32(C.byref(h.s), _ptr(b), _ptr(x), eps, tol_relative, max_it,
-                        int(precond), C.byref(it), _ptr(hist) if history else None)
+                        int(precond), int(true_res), C.byref(it),
+                        _ptr(hist) if history else None)
     out = (x, it.value, st)
     return out + (hist[: it.value + 1],) if history else out
 

@@ -216,6 +216,31 @@ static int cg64_iter(cg64_t* s) {
   return IT_OK;
 }
 
+/* Paper-literal stop measure (the loop test of Sec. 3 is on ||A x_i - b||):
+ * ||b - A x||^2 of the current iterate in the stage's precision -- the
+ * product by the stage's matrix and the difference rounded in that
+ * precision, the squares summed in double as for the other norms.  NAN if
+ * the scratch vector cannot be had. */
+static double true_rr32(const cg32_t* s, const float* b32) {
+  float* t = (float*)malloc(sizeof(float) * (size_t)(s->n > 0 ? s->n : 1));
+  if (!t) return NAN;
+  orc_spmv32(s->n, s->rp, s->ci, s->v32, s->x, t);
+  for (int32_t i = 0; i < s->n; ++i) t[i] = b32[i] - t[i];
+  const double rr = orc_dot32(s->n, t, t);
+  free(t);
+  return rr;
+}
+static double true_rr64(const cg64_t* s, const double* b) {
+  const int32_t n = s->A->n;
+  double* t = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!t) return NAN;
+  orc_spmv64(s->A, s->x, t);
+  for (int32_t i = 0; i < n; ++i) t[i] = b[i] - t[i];
+  const double rr = orc_dot64(n, t, t);
+  free(t);
+  return rr;
+}
+
 /* Jacobi preconditioner M = diag(A) (Sec. 5): dinv64[i] = 1 / a_ii and
  * dinv32[i] = 1 / float32(a_ii), each a correctly rounded division in its
  * precision.  0 if a row has no stored diagonal or a_ii is zero or not
@@ -251,8 +276,8 @@ static int csr_ok(const orc_csr* A) {
 /* Plain CG drivers (Sec. 3).                                                */
 /* ------------------------------------------------------------------------ */
 int32_t orc_cg64(const orc_csr* A, const double* b, double* x, double eps,
-                 int32_t tol_relative, int32_t max_it, int32_t precond, int32_t* iters,
-                 double* res_hist) {
+                 int32_t tol_relative, int32_t max_it, int32_t precond, int32_t true_res,
+                 int32_t* iters, double* res_hist) {
   *iters = 0;
   if (!csr_ok(A)) return ORC_ERR_INVALID_ARG;
   double bnorm = sqrt(orc_dot64(A->n, b, b));
@@ -267,7 +292,7 @@ int32_t orc_cg64(const orc_csr* A, const double* b, double* x, double eps,
   cg64_start(&s, b);
   int32_t st = ORC_OK, it = 0;
   for (;;) {
-    double m = stop_measure(s.rr, bnorm, tol_relative);
+    double m = stop_measure(true_res ? true_rr64(&s, b) : s.rr, bnorm, tol_relative);
     if (res_hist) res_hist[it] = m;
     if (isnan(m)) { st = ORC_ERR_NAN; break; }
     if (m <= eps) break;
@@ -283,8 +308,8 @@ int32_t orc_cg64(const orc_csr* A, const double* b, double* x, double eps,
 }
 
 int32_t orc_cg32(const orc_csr* A, const double* b, float* x, double eps,
-                 int32_t tol_relative, int32_t max_it, int32_t precond, int32_t* iters,
-                 double* res_hist) {
+                 int32_t tol_relative, int32_t max_it, int32_t precond, int32_t true_res,
+                 int32_t* iters, double* res_hist) {
   *iters = 0;
   if (!csr_ok(A)) return ORC_ERR_INVALID_ARG;
   const int32_t n = A->n;
@@ -303,7 +328,7 @@ int32_t orc_cg32(const orc_csr* A, const double* b, float* x, double eps,
     double bnorm = sqrt(orc_dot32(n, b32, b32));
     cg32_start(&s, b32);
     for (;;) {
-      double m = stop_measure(s.rr, bnorm, tol_relative);
+      double m = stop_measure(true_res ? true_rr32(&s, b32) : s.rr, bnorm, tol_relative);
       if (res_hist) res_hist[it] = m;
       if (isnan(m)) { st = ORC_ERR_NAN; break; }
       if (m <= eps) break;
@@ -521,6 +546,7 @@ orc_opts orc_opts_default(void) {
   o.feat_mask = 0xFu;
   o.bfs_starts = 1;
   o.precond = 0;
+  o.stop_true_residual = 0;
   return o;
 }
 
@@ -545,14 +571,15 @@ double orc_true_rel_resid(const orc_csr* A, const double* b, const double* x) {
  * single-precision iterations that define v (Eq. 13).  Reading: the loop
  * ends early when the residual reaches eps2 or 0, and v averages the ratios
  * completed; the ratio uses norms computed in double (Remark 3). */
-static int32_t k0_phase(cg32_t* s, double bnorm32, const orc_opts* o,
+static int32_t k0_phase(cg32_t* s, const float* b32, double bnorm32, const orc_opts* o,
                         int32_t max1, int32_t* n1, int32_t* k0_done, double* v,
                         int* broke) {
   double sum = 0.0;
   int32_t done = 0;
   *broke = 0;
   while (done < o->k0 && *n1 < max1) {
-    double m = stop_measure(s->rr, bnorm32, o->tol_relative);
+    double m = stop_measure(o->stop_true_residual ? true_rr32(s, b32) : s->rr, bnorm32,
+                            o->tol_relative);
     if (isnan(m)) return ORC_ERR_NAN;
     if (m <= o->eps2 || s->rr == 0.0) break;
     double rr_prev = s->rr;
@@ -589,7 +616,7 @@ int32_t orc_features(const orc_csr* A, const double* b, const orc_opts* o,
   double v = 0.0;
   int32_t st = ORC_OK;
   if (bnorm32 > 0.0 || !o->tol_relative)
-    st = k0_phase(&s, bnorm32, o, cap_or(o->max_it_fp32, n), &n1, k0_done, &v, &broke);
+    st = k0_phase(&s, b32, bnorm32, o, cap_or(o->max_it_fp32, n), &n1, k0_done, &v, &broke);
   else
     *k0_done = 0;
   feat[0] = (double)n;
@@ -653,7 +680,7 @@ int32_t orc_solve(const orc_csr* A, const double* b, double* x,
     /* Algorithm II: k0 FP32 iterations -> v; 2BFS -> l~; kNN -> eps1. */
     int32_t k0_done = 0;
     double v = 0.0;
-    status = k0_phase(&s, bnorm32, o, max1, &n1, &k0_done, &v, &broke);
+    status = k0_phase(&s, b32, bnorm32, o, max1, &n1, &k0_done, &v, &broke);
     if (status != ORC_OK) goto done32;
     res->k0_done = k0_done;
     res->v = v;
@@ -670,8 +697,9 @@ int32_t orc_solve(const orc_csr* A, const double* b, double* x,
   res->eps1 = eps1;
 
   /* Stage 1: FP32 CG to eps1, continuing from the current iterate. */
+  const int tres = o->stop_true_residual;
   while (!broke) {
-    double m = stop_measure(s.rr, bnorm32, rel);
+    double m = stop_measure(tres ? true_rr32(&s, b32) : s.rr, bnorm32, rel);
     if (isnan(m)) { status = ORC_ERR_NAN; goto done32; }
     if (m <= eps1 || n1 >= max1) break;
     int r = cg32_iter(&s);
@@ -679,7 +707,7 @@ int32_t orc_solve(const orc_csr* A, const double* b, double* x,
     if (r == IT_BREAKDOWN) { broke = 1; break; }
     ++n1;
   }
-  if (stop_measure(s.rr, bnorm32, rel) > eps1) warn_eps1 = 1;
+  if (stop_measure(tres ? true_rr32(&s, b32) : s.rr, bnorm32, rel) > eps1) warn_eps1 = 1;
 
   /* Promote: x0 = float64(x~); restart FP64 CG with r0 = b - A x0. */
   for (int32_t i = 0; i < n; ++i) x[i] = (double)s.x[i];
@@ -687,7 +715,7 @@ int32_t orc_solve(const orc_csr* A, const double* b, double* x,
   for (int32_t restart = 0;; ++restart) {
     cg64_start(&s64, b);
     for (;;) {
-      double m = stop_measure(s64.rr, bnorm, rel);
+      double m = stop_measure(tres ? true_rr64(&s64, b) : s64.rr, bnorm, rel);
       if (isnan(m)) { status = ORC_ERR_NAN; goto done64; }
       if (m <= o->eps2) break;
       if (n2 >= max2) { status = ORC_ERR_NOT_CONVERGED; goto done64; }
@@ -695,7 +723,8 @@ int32_t orc_solve(const orc_csr* A, const double* b, double* x,
       if (r != IT_OK) { status = it_status(r); goto done64; }
       ++n2;
     }
-    /* Reading: if the true residual misses eps2, restart from x. */
+    /* Reading: if the true residual misses eps2, restart from x.  (With the
+     * paper-literal stop test the loop above already ended on it.) */
     double tr = orc_true_rel_resid(A, b, x);
     double tm = rel ? tr : tr * bnorm;
     res->true_rel_resid = tr;

@@ -297,3 +297,101 @@ def test_mixed_pcg_reaches_eps2_and_its_features_follow_the_preconditioned_itera
     L = synth.laplacian_2d(20, 20)
     _, bl = synth.rhs(L, seed=2)
     assert oracle.features(L, bl, precond=1)[0][3] == oracle.features(L, bl)[0][3]
+
+
+# ---- the stop test as printed: ||A x_i - b|| at the head of every iteration (Sec. 3) ----
+
+def _csr_scipy(A, dtype):
+    return csr_matrix((A.val.astype(dtype), A.col, A.row_ptr), shape=(A.n, A.n))
+
+
+@pytest.mark.parametrize("A", [synth.laplacian_2d(40, 30), synth.path(401, 1.01),
+                               synth.random_tree_plus(600, 3.0, 1.1, seed=2)],
+                         ids=["lap2d", "path", "tree"])
+def test_true_residual_stop_is_the_first_iterate_under_eps(A):
+    """With true_res the run ends at the first iterate whose residual
+    ||b - A x_k|| / ||b|| is at most eps.  The iterates themselves do not
+    depend on the stop test, so x_k and x_{k-1} come from runs capped at k
+    and k - 1 iterations, and their residuals are recomputed here with
+    scipy (a different summation order; the eps are far from the rounding
+    level, so the order does not decide)."""
+    _, b = synth.rhs(A, seed=7)
+    M64 = _csr_scipy(A, np.float64)
+    bn = np.linalg.norm(b)
+    for eps in (1e-6, 1e-8, 1e-10):
+        _, k, st = oracle.cg64(A, b, eps, true_res=1)
+        assert st == 0 and k > 0
+        xk, _, _ = oracle.cg64(A, b, 0.0, max_it=k)
+        xp, _, _ = oracle.cg64(A, b, 0.0, max_it=k - 1)
+        assert np.linalg.norm(b - M64 @ xk) / bn <= eps * (1 + 1e-9)
+        assert np.linalg.norm(b - M64 @ xp) / bn > eps * (1 - 1e-9)
+    b32 = b.astype(np.float32).astype(np.float64)
+    M32 = _csr_scipy(A, np.float32).astype(np.float64)   # float32(A), exact in double
+    bn32 = np.linalg.norm(b32)
+    for eps in (1e-3, 1e-4, 1e-5):
+        _, k, st = oracle.cg32(A, b, eps, true_res=1)
+        assert st == 0 and k > 0
+        xk, _, _ = oracle.cg32(A, b, 0.0, max_it=k)
+        xp, _, _ = oracle.cg32(A, b, 0.0, max_it=k - 1)
+        rk = np.linalg.norm(b32 - M32 @ xk.astype(np.float64)) / bn32
+        rp = np.linalg.norm(b32 - M32 @ xp.astype(np.float64)) / bn32
+        assert rk <= eps * (1 + 1e-3) and rp > eps * (1 - 1e-3)
+
+
+def test_true_residual_stop_shows_the_stagnation_of_fig2():
+    """Sec. 7, Fig. 2: on the path with a_ii = 1.001 sum_j a_ij (n = 1001) the
+    true residual of single-precision CG stops improving after a couple of
+    hundred iterations (the paper: k = 176) near 1e-7 relative, and that of
+    double precision hundreds of iterations later (the paper: k = 506) near
+    1e-15, while the recursive residual keeps falling.  So with the stop test
+    as printed, eps1 = 1e-7 cannot be met in single precision (the dashes of
+    Table 5), whereas the recursive residual meets it."""
+    A = synth.path(1001, 1.001)
+    _, b = synth.rhs(A, seed=1)
+    _, _, _, h32 = oracle.cg32(A, b, 0.0, max_it=1200, history=True, true_res=1)
+    _, _, _, r32 = oracle.cg32(A, b, 0.0, max_it=1200, history=True)
+    _, _, _, h64 = oracle.cg64(A, b, 0.0, max_it=1200, history=True, true_res=1)
+
+    def stagnation(h):  # first k whose running minimum is within 2x of the final one
+        best = np.minimum.accumulate(h)
+        return int(np.argmax(best <= 2 * best[-1])), best[-1]
+
+    k32, f32 = stagnation(h32)
+    k64, f64 = stagnation(h64)
+    assert 120 <= k32 <= 300 and 1e-8 < f32 < 1e-5
+    assert k64 > k32 + 200 and f64 < 1e-13
+    assert r32.min() < 1e-20                     # the recursive residual does not stagnate
+    _, k, st = oracle.cg32(A, b, 1e-7, max_it=3 * A.n, true_res=1)
+    assert st == oracle.ERR_NOT_CONVERGED and k == 3 * A.n
+    _, k, st = oracle.cg32(A, b, 1e-7, max_it=3 * A.n)
+    assert st == 0 and k < 400
+    # Algorithm I with eps1 = 1e-7: stage 1 runs to its cap and warns; the
+    # FP64 stage then ends on the true residual, with no restart.
+    x, r = oracle.solve(A, b, eps1=1e-7, stop_true_residual=1, max_it_fp32=600)
+    assert r["status"] == oracle.WARN_EPS1_NOT_REACHED and r["n1"] == 600
+    assert r["true_rel_resid"] <= 1e-10
+    x0, r0 = oracle.solve(A, b, eps1=1e-7, max_it_fp32=600)
+    assert r0["status"] == 0 and r0["n1"] < 400
+
+
+@pytest.mark.parametrize("name", ["lap2d", "xstar", "tree"])
+def test_true_residual_stop_in_both_algorithms(name):
+    """With the stop test as printed the FP64 stage ends on the true residual,
+    so it never needs the restart of the recursive reading; Algorithm II's
+    v (Eq. 13) still comes from the recursive r of the k0 iterations, so the
+    features do not change."""
+    A = {"lap2d": synth.laplacian_2d(50, 37),
+         "xstar": synth.extended_star(20, 50, 3.0, extra=None, seed=6),
+         "tree": synth.random_tree_plus(900, 2.0, 1.1, seed=4)}[name]
+    _, b = synth.rhs(A, seed=5)
+    for eps1 in (1e-3, 1e-5):
+        x, r = oracle.solve(A, b, eps1=eps1, stop_true_residual=1)
+        assert r["status"] in (0, oracle.WARN_EPS1_NOT_REACHED)
+        assert r["true_rel_resid"] <= 1e-10
+        assert oracle.true_rel_resid(A, b, x) == r["true_rel_resid"]
+    feat, cls = synth.random_sample(50, seed=2)
+    f0 = oracle.features(A, b)[0]
+    f1 = oracle.features(A, b, stop_true_residual=1)[0]
+    assert list(f0) == list(f1)
+    _, r = oracle.solve(A, b, S=(feat, cls), stop_true_residual=1)
+    assert r["v"] == f0[3] and r["true_rel_resid"] <= 1e-10
