@@ -133,6 +133,17 @@ typedef struct {
                                 MPCG_ERR_UNIMPLEMENTED); Algorithm II then runs its steps as
                                 separate launches in the paper's order.  The workspace grows by
                                 16 n bytes: size it with these options */
+  int32_t stop_true_residual; /* 1: every stop test on ||b - A x|| of the current iterate, the
+                                loop test of the CG procedure as Sec. 3 prints it (in the
+                                single-precision stage b~ - A~ x~ rounded in single precision;
+                                one more pass over the matrix per iteration; the FP64 stage then
+                                needs no true-residual restart); 0: on the recursively updated
+                                r (default).  A stage whose recursive r has fallen 1e3 times
+                                below ||b - A x|| has stagnated and ends as at its iteration
+                                cap.  v (Eq. 13) stays on the recursive r.  mpcg_solve
+                                and mpcg_features only (MPCG_ERR_UNIMPLEMENTED in the batched
+                                solve and the server); Algorithm II then runs its steps as
+                                separate launches in the paper's order */
 } mpcg_options_t;
 
 /* Result record, written by the device at the end of the call's work into

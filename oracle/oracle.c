@@ -216,6 +216,13 @@ static int cg64_iter(cg64_t* s) {
   return IT_OK;
 }
 
+/* Reading for the stop test on the true residual: once the recursive r has
+ * fallen 1e3 times below ||b - A x||, the rounding of the iteration decides
+ * the true residual and it no longer falls (the stagnation of Sec. 7,
+ * Fig. 2), so a stage that has not met its tolerance then ends as it would
+ * at its iteration cap.  Compared on squares: r^T r <= 1e-6 ||b - A x||^2. */
+#define STAGNATION_RR 1e-6
+
 /* Paper-literal stop measure (the loop test of Sec. 3 is on ||A x_i - b||):
  * ||b - A x||^2 of the current iterate in the stage's precision -- the
  * product by the stage's matrix and the difference rounded in that
@@ -292,11 +299,15 @@ int32_t orc_cg64(const orc_csr* A, const double* b, double* x, double eps,
   cg64_start(&s, b);
   int32_t st = ORC_OK, it = 0;
   for (;;) {
-    double m = stop_measure(true_res ? true_rr64(&s, b) : s.rr, bnorm, tol_relative);
+    const double trr = true_res ? true_rr64(&s, b) : s.rr;
+    double m = stop_measure(trr, bnorm, tol_relative);
     if (res_hist) res_hist[it] = m;
     if (isnan(m)) { st = ORC_ERR_NAN; break; }
     if (m <= eps) break;
-    if (it >= max_it) { st = ORC_ERR_NOT_CONVERGED; break; }
+    if (it >= max_it || (true_res && s.rr <= STAGNATION_RR * trr)) {
+      st = ORC_ERR_NOT_CONVERGED;
+      break;
+    }
     int r = cg64_iter(&s);
     if (r != IT_OK) { st = it_status(r); break; }
     ++it;
@@ -328,11 +339,15 @@ int32_t orc_cg32(const orc_csr* A, const double* b, float* x, double eps,
     double bnorm = sqrt(orc_dot32(n, b32, b32));
     cg32_start(&s, b32);
     for (;;) {
-      double m = stop_measure(true_res ? true_rr32(&s, b32) : s.rr, bnorm, tol_relative);
+      const double trr = true_res ? true_rr32(&s, b32) : s.rr;
+      double m = stop_measure(trr, bnorm, tol_relative);
       if (res_hist) res_hist[it] = m;
       if (isnan(m)) { st = ORC_ERR_NAN; break; }
       if (m <= eps) break;
-      if (it >= max_it) { st = ORC_ERR_NOT_CONVERGED; break; }
+      if (it >= max_it || (true_res && s.rr <= STAGNATION_RR * trr)) {
+        st = ORC_ERR_NOT_CONVERGED;
+        break;
+      }
       int r = cg32_iter(&s);
       if (r != IT_OK) { st = it_status(r); break; }
       ++it;
@@ -578,10 +593,11 @@ static int32_t k0_phase(cg32_t* s, const float* b32, double bnorm32, const orc_o
   int32_t done = 0;
   *broke = 0;
   while (done < o->k0 && *n1 < max1) {
-    double m = stop_measure(o->stop_true_residual ? true_rr32(s, b32) : s->rr, bnorm32,
-                            o->tol_relative);
+    const double trr = o->stop_true_residual ? true_rr32(s, b32) : s->rr;
+    double m = stop_measure(trr, bnorm32, o->tol_relative);
     if (isnan(m)) return ORC_ERR_NAN;
     if (m <= o->eps2 || s->rr == 0.0) break;
+    if (o->stop_true_residual && s->rr <= STAGNATION_RR * trr) break;
     double rr_prev = s->rr;
     int r = cg32_iter(s);
     if (r == IT_NAN) return ORC_ERR_NAN;
@@ -699,9 +715,10 @@ int32_t orc_solve(const orc_csr* A, const double* b, double* x,
   /* Stage 1: FP32 CG to eps1, continuing from the current iterate. */
   const int tres = o->stop_true_residual;
   while (!broke) {
-    double m = stop_measure(tres ? true_rr32(&s, b32) : s.rr, bnorm32, rel);
+    const double trr = tres ? true_rr32(&s, b32) : s.rr;
+    double m = stop_measure(trr, bnorm32, rel);
     if (isnan(m)) { status = ORC_ERR_NAN; goto done32; }
-    if (m <= eps1 || n1 >= max1) break;
+    if (m <= eps1 || n1 >= max1 || (tres && s.rr <= STAGNATION_RR * trr)) break;
     int r = cg32_iter(&s);
     if (r == IT_NAN) { status = ORC_ERR_NAN; goto done32; }
     if (r == IT_BREAKDOWN) { broke = 1; break; }
@@ -715,10 +732,14 @@ int32_t orc_solve(const orc_csr* A, const double* b, double* x,
   for (int32_t restart = 0;; ++restart) {
     cg64_start(&s64, b);
     for (;;) {
-      double m = stop_measure(tres ? true_rr64(&s64, b) : s64.rr, bnorm, rel);
+      const double trr = tres ? true_rr64(&s64, b) : s64.rr;
+      double m = stop_measure(trr, bnorm, rel);
       if (isnan(m)) { status = ORC_ERR_NAN; goto done64; }
       if (m <= o->eps2) break;
-      if (n2 >= max2) { status = ORC_ERR_NOT_CONVERGED; goto done64; }
+      if (n2 >= max2 || (tres && s64.rr <= STAGNATION_RR * trr)) {
+        status = ORC_ERR_NOT_CONVERGED;
+        goto done64;
+      }
       int r = cg64_iter(&s64);
       if (r != IT_OK) { status = it_status(r); goto done64; }
       ++n2;

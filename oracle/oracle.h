@@ -66,7 +66,9 @@ typedef struct {
   int32_t bfs_starts;   /* 2BFS runs for l~ (Sec. 6 remark; <= 1: the single run) */
   int32_t precond;      /* 1: Jacobi-preconditioned CG in both stages (Sec. 5); 0: plain */
   int32_t stop_true_residual; /* 1: every stop test on ||b - A x|| (the loop test of Sec. 3
-                                 as printed); 0: on the recursive r (default) */
+                                 as printed), and a stage that has stagnated (recursive r
+                                 1e3 times below it) ends as at its cap; 0: on the recursive r
+                                 (default) */
 } orc_opts;
 
 typedef struct {
@@ -96,7 +98,9 @@ double orc_dot32(int32_t n, const float* a, const float* b);
 /* ---- plain CG in one precision from x0 (Sec. 3) ----
  * Runs while the stop measure exceeds eps and it < max_it.  x is in/out.
  * The stop measure uses the recursive r, or with true_res the residual
- * b - A x of the iterate in the stage's precision (the loop test as printed).
+ * b - A x of the iterate in the stage's precision (the loop test as printed);
+ * with true_res a run whose recursive r has fallen 1e3 times below it has
+ * stagnated and ends as NOT_CONVERGED.
  * res_hist (nullable, max_it+1 entries) receives the stop measure at the
  * head of every iteration.  Returns status; *iters = iterations performed. */
 int32_t orc_cg64(const orc_csr* A, const double* b, double* x, double eps,

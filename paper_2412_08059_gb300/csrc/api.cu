@@ -25,6 +25,7 @@ bool options_ok(const mpcg_options_t* o) {
   if (o->grid_blocks < 0 || o->timeout_ms < 0) return false;
   if (o->bfs_starts < 0) return false;
   if (o->precond != 0 && o->precond != 1) return false;
+  if (o->stop_true_residual != 0 && o->stop_true_residual != 1) return false;
   return true;
 }
 
@@ -57,6 +58,7 @@ int32_t prepare(const mpcg_csr_t* A, void* ws, size_t ws_bytes, mpcg_stream_t st
     return MPCG_ERR_WORKSPACE;
   carve(d, (char*)ws, &L->ws);
   L->precond = precond ? 1 : 0;
+  L->true_res = 0;
   L->dinv64 = nullptr;
   L->dinv32 = nullptr;
   L->z32 = nullptr;
@@ -102,6 +104,7 @@ mpcg_options_t mpcg_options_default(void) {
   o.timeout_ms = 20000;
   o.bfs_starts = 1;
   o.precond = 0;
+  o.stop_true_residual = 0;
   return o;
 }
 
@@ -135,6 +138,7 @@ int32_t mpcg_features(const mpcg_csr_t* A, const double* b, const mpcg_options_t
   Launch L;
   int32_t st = prepare(A, ws, ws_bytes, stream, opts->grid_blocks, &L, opts->precond);
   if (st != MPCG_OK) return st;
+  L.true_res = opts->stop_true_residual;
   cudaError_t e;
   if ((e = launch_init(L, *opts, 0)) != cudaSuccess) return cuda_status(e);
   if ((e = launch_prep(L, b)) != cudaSuccess) return cuda_status(e);
@@ -172,13 +176,15 @@ int32_t mpcg_solve(const mpcg_csr_t* A, const double* b, double* x, const mpcg_s
   Launch L;
   int32_t st = prepare(A, ws, ws_bytes, stream, opts->grid_blocks, &L, opts->precond);
   if (st != MPCG_OK) return st;
+  L.true_res = opts->stop_true_residual;
   cudaError_t e;
   if ((e = launch_init(L, *opts, fp64_only)) != cudaSuccess) return cuda_status(e);
   if ((e = launch_prep(L, b)) != cudaSuccess) return cuda_status(e);
   if (L.precond && (e = launch_jacobi(L)) != cudaSuccess) return cuda_status(e);
-  if (!fp64_only && auto_eps1 && L.precond) {
-    // Algorithm II with Jacobi PCG, its steps as separate launches in the
-    // paper's order: 2BFS, k0 iterations (v), kNN, stage 1 from iterate k0
+  if (!fp64_only && auto_eps1 && (L.precond || L.true_res)) {
+    // Algorithm II with Jacobi PCG or with the stop test on b - A x, its
+    // steps as separate launches in the paper's order: 2BFS, k0 iterations
+    // (v), kNN, stage 1 from iterate k0
     if ((e = launch_pseudo_diameter(L, kSlotPd)) != cudaSuccess) return cuda_status(e);
     if ((e = launch_cg32(L, kCgK0, kSlotCgK0)) != cudaSuccess) return cuda_status(e);
     if ((e = launch_knn(L.st, nullptr, *sample, *opts, L.ws.ctl, nullptr, nullptr)) != cudaSuccess)

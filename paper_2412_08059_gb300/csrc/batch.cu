@@ -377,7 +377,8 @@ extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const dou
   const int auto_eps1 = !opts->fp64_only && !(opts->eps1 > 0.0);
   if (auto_eps1 && !sample_ok(sample)) return MPCG_ERR_INVALID_ARG;
   if (auto_eps1 && opts->bfs_starts > 1) return MPCG_ERR_UNIMPLEMENTED;  // one 2BFS run in teams
-  if (opts->precond) return MPCG_ERR_UNIMPLEMENTED;  // plain CG in teams
+  if (opts->precond || opts->stop_true_residual)  // plain CG, recursive stop test in teams
+    return MPCG_ERR_UNIMPLEMENTED;
   if (!ws || ((uintptr_t)ws & 255u)) return MPCG_ERR_WORKSPACE;
   std::vector<int> nv(nsys), mv(nsys);
   for (int32_t i = 0; i < nsys; ++i) {

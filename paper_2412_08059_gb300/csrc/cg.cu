@@ -592,7 +592,15 @@ enum Dec { kGo = 0, kStop = 1, kNan = 2, kBroke = 3, kBreakdown = 4 };
 // kPc: Jacobi-preconditioned CG (the PCG form of Sec. 5): z = dinv r is
 // kept beside r, d is formed from z, alpha = r^T z / d^T q and
 // beta = r'^T z' / r^T z; the stop test and v stay on r.
-template <bool kPc>
+// kTrue: the stop test as the CG procedure of Sec. 3 prints it, on
+// ||b~ - A~ x~|| of the current iterate: one more pass over the matrix at the
+// head of every iteration, t = b~ - A~ x~ rounded in single precision and
+// t^T t summed like the other norms.  v (Eq. 13) stays on the recursive r.
+// A stage whose recursive r has fallen 1e3 times below ||b - A x|| has
+// stagnated (Sec. 7, Fig. 2): it ends as at its iteration cap.
+constexpr double kStagnationRR = 1e-6;  // on squares: r^T r <= 1e-6 ||b - A x||^2
+
+template <bool kPc, bool kTrue>
 __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
   constexpr int NC = kNC;
   extern __shared__ __align__(128) char smem[];
@@ -676,12 +684,31 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
   const StopThr thr = stop_thr(eps, bnorm, rel);  // used by thread 0
   double vsum = 0.0;  // thread 0
   int k0done = 0, broke = 0;
+  double trr = 0.0;   // kTrue: ||b~ - A~ x~||^2 of the current iterate (thread 0)
 
   while (ok) {
+    if constexpr (kTrue) {
+      FF pt{0.f, 0.f};
+      const float* xv = a.x32;
+      const float* bv = a.b32;
+      auto Gx = [&](int c) -> float { return xv[c]; };
+      auto Rt = [&](int i, float acc) {
+        if (i < n) {
+          const float t = __fsub_rn(bv[i], acc);
+          ff_add_prod(pt, t, t);
+        }
+      };
+      if (!ring_spmv<NC, float>(a, R, C, S0, S1, Gx, Rt)) set_status(ctl, MPCG_ERR_TIMEOUT);
+      trr = cgrid_total(block_ff(pt, S), a.partials, red, ctl, a.slot, round, S, ok);
+      if (!ok) break;
+    }
     if (lead) {
+      const double rs = kTrue ? trr : rr;  // the stop test's r^T r
       int dec = kGo;
-      if (isnan(rr)) dec = kNan;
-      else if (stop_pass(thr, rr) || it >= limit || (a.mode == kCgK0 && rr == 0.0)) dec = kStop;
+      if (isnan(rr) || isnan(rs)) dec = kNan;
+      else if (stop_pass(thr, rs) || it >= limit || (a.mode == kCgK0 && rr == 0.0) ||
+               (kTrue && rr <= kStagnationRR * rs))
+        dec = kStop;
       S.dec = dec;
       if (dec == kNan && lead0) set_status(ctl, MPCG_ERR_NAN);
     }
@@ -775,7 +802,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
     ctl->first = first;
     ctl->parity = parity;
     ctl->n1 = it;
-    ctl->res32 = stop_measure(rr, bnorm, rel);
+    ctl->res32 = stop_measure(kTrue ? trr : rr, bnorm, rel);
     if (broke) ctl->broke32 = 1;
     if (a.mode == kCgK0) {
       ctl->k0_done = k0done;
@@ -929,12 +956,16 @@ __device__ __forceinline__ void p3_64_pc(const CgArgs& a, int R0, int R1, int la
 }
 
 // Kinds of SpMV pass in the double-precision stage.
-enum Pass64 { kRestart = 0, kTrueRes = 1, kIterate = 2, kFinalRes = 3, kDone = 4 };
+enum Pass64 { kRestart = 0, kTrueRes = 1, kIterate = 2, kFinalRes = 3, kDone = 4, kCheck = 5 };
 
 // kPc: Jacobi-preconditioned CG (the PCG form of Sec. 5): restarts set
 // d = z = dinv r, alpha = r^T z / d^T q, beta = r'^T z' / r^T z and
 // d = z + beta d; the stop test and the true residual stay on r.
-template <bool kPc>
+// kTrue: the stop test as the CG procedure of Sec. 3 prints it: a kCheck
+// pass computes ||b - A x||^2 at the head of every iteration and decides on
+// it, so the stage ends on its true residual (no true-residual restart), or
+// as not converged at the cap or once stagnated (as k_cg32).
+template <bool kPc, bool kTrue>
 __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
   constexpr int NC = kNC;
   extern __shared__ __align__(128) char smem[];
@@ -974,6 +1005,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
   int it = 0, restarts = 0;
   int failed = 0;                  // thread 0
   double true_rel = NAN;  // thread 0
+  double trr = NAN;       // kTrue: ||b - A x||^2 of the last check (thread 0)
   const StopThr thr2 = stop_thr(eps2, bnorm, rel);  // used by thread 0
   double rr = 0.0;                 // thread 0
   double rz = 0.0;                 // r^T z (kPc; thread 0)
@@ -991,6 +1023,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
   //   kTrueRes:  q = b - A x, ||q||^2           (true residual at eps2)
   //   kIterate:  q = A d, d^T q; then the x, r update and d = r + beta d
   //   kFinalRes: ||b - A x||^2 after the cap
+  //   kCheck:    ||b - A x||^2, the stop test of kTrue
   int kind = kRestart;
   const double* x = a.x64;
   while (ok && kind != kDone) {
@@ -1040,7 +1073,14 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
     // ---- thread 0: the scalars and the next pass ----
     if (lead) {
       int next = kDone;
-      if (kind == kFinalRes) {
+      if (kTrue && kind == kCheck) {
+        true_rel = bnorm > 0.0 ? sqrt(tot) / bnorm : sqrt(tot);
+        trr = tot;
+        if (isnan(tot)) failed = MPCG_ERR_NAN;
+        else if (stop_pass(thr2, tot)) next = kDone;
+        else if (it >= max2 || rr <= kStagnationRR * tot) failed = MPCG_ERR_NOT_CONVERGED;
+        else next = kIterate;
+      } else if (kind == kFinalRes) {
         true_rel = bnorm > 0.0 ? sqrt(tot) / bnorm : sqrt(tot);
       } else if (kind == kTrueRes) {
         true_rel = bnorm > 0.0 ? sqrt(tot) / bnorm : sqrt(tot);
@@ -1129,6 +1169,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
         if (isnan(rr)) {
           failed = MPCG_ERR_NAN;
           nk = kDone;
+        } else if (kTrue) {
+          nk = kCheck;  // the decision follows the check pass
         } else if (stop_pass(thr2, rr)) {
           nk = kTrueRes;
         } else if (it >= max2) {
@@ -1149,7 +1191,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
     ctl->n2 = it;
     ctl->restarts = restarts;
     if (restarts) ctl->warn_restart = 1;
-    ctl->res64 = stop_measure(rr, bnorm, rel);
+    ctl->res64 = stop_measure(kTrue ? trr : rr, bnorm, rel);
     ctl->true_rel = true_rel;
     ctl->rr = rr;
     ctl->t_fp64 = globaltimer();
@@ -1635,11 +1677,15 @@ int cg_grid(int requested) {
     struct K {
       const void* f;
       size_t smem;
-    } ks[5] = {{(const void*)k_cg32<false>, ring_smem_bytes<float>()},
-               {(const void*)k_cg64<false>, ring_smem_bytes<double>()},
+    } ks[9] = {{(const void*)k_cg32<false, false>, ring_smem_bytes<float>()},
+               {(const void*)k_cg64<false, false>, ring_smem_bytes<double>()},
                {(const void*)k_stage1, ring_smem_bytes<float>()},
-               {(const void*)k_cg32<true>, ring_smem_bytes<float>()},
-               {(const void*)k_cg64<true>, ring_smem_bytes<double>()}};
+               {(const void*)k_cg32<true, false>, ring_smem_bytes<float>()},
+               {(const void*)k_cg64<true, false>, ring_smem_bytes<double>()},
+               {(const void*)k_cg32<false, true>, ring_smem_bytes<float>()},
+               {(const void*)k_cg64<false, true>, ring_smem_bytes<double>()},
+               {(const void*)k_cg32<true, true>, ring_smem_bytes<float>()},
+               {(const void*)k_cg64<true, true>, ring_smem_bytes<double>()}};
     int sms = 0, per = 1 << 30;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return 0;
@@ -1661,8 +1707,8 @@ int cg_grid(int requested) {
   return (requested > 0 && requested < c) ? requested : c;
 }
 
-const void* cg32_kernel() { return (const void*)k_cg32<false>; }
-const void* cg64_kernel() { return (const void*)k_cg64<false>; }
+const void* cg32_kernel() { return (const void*)k_cg32<false, false>; }
+const void* cg64_kernel() { return (const void*)k_cg64<false, false>; }
 const void* stage1_kernel() { return (const void*)k_stage1; }
 
 cudaError_t launch_cg32(const Launch& L, int mode, int slot) {
@@ -1670,7 +1716,9 @@ cudaError_t launch_cg32(const Launch& L, int mode, int slot) {
   void* args[] = {&a};
   const int g = cg_grid(L.grid_req);
   if (g <= 0) return cudaErrorInvalidConfiguration;
-  const void* k = L.precond ? (const void*)k_cg32<true> : (const void*)k_cg32<false>;
+  const void* k = L.true_res
+                      ? (L.precond ? (const void*)k_cg32<true, true> : (const void*)k_cg32<false, true>)
+                      : (L.precond ? (const void*)k_cg32<true, false> : (const void*)k_cg32<false, false>);
   return cudaLaunchCooperativeKernel(k, dim3(g), dim3(kTmaThreads), args, ring_smem_bytes<float>(),
                                      L.st);
 }
@@ -1682,7 +1730,9 @@ cudaError_t launch_cg64(const Launch& L, const double* b, double* x, int from_ze
   void* args[] = {&a};
   const int g = cg_grid(L.grid_req);
   if (g <= 0) return cudaErrorInvalidConfiguration;
-  const void* k = L.precond ? (const void*)k_cg64<true> : (const void*)k_cg64<false>;
+  const void* k = L.true_res
+                      ? (L.precond ? (const void*)k_cg64<true, true> : (const void*)k_cg64<false, true>)
+                      : (L.precond ? (const void*)k_cg64<true, false> : (const void*)k_cg64<false, false>);
   return cudaLaunchCooperativeKernel(k, dim3(g), dim3(kTmaThreads), args,
                                      ring_smem_bytes<double>(), L.st);
 }

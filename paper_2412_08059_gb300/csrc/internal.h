@@ -31,6 +31,7 @@ struct Launch {
   double* dinv64;  // 1 / a_ii
   float* dinv32;   // 1 / float32(a_ii)
   float* z32;      // z = dinv32 r of the single-precision stage
+  int true_res;    // stop tests on b - A x (option stop_true_residual)
 };
 
 // Bytes of the preconditioner arrays past the workspace map (0 without).

@@ -276,7 +276,8 @@ extern "C" int32_t mpcg_server_create(void* ws, size_t ws_bytes, int32_t max_slo
   const int auto_eps1 = !opts->fp64_only && !(opts->eps1 > 0.0);
   if (auto_eps1 && !sample_ok(sample)) return MPCG_ERR_INVALID_ARG;
   if (auto_eps1 && opts->bfs_starts > 1) return MPCG_ERR_UNIMPLEMENTED;  // one 2BFS run in teams
-  if (opts->precond) return MPCG_ERR_UNIMPLEMENTED;  // plain CG in teams
+  if (opts->precond || opts->stop_true_residual)  // plain CG, recursive stop test in teams
+    return MPCG_ERR_UNIMPLEMENTED;
   if (!ws || ((uintptr_t)ws & 255u) || ws_bytes <= fixed_bytes(max_slots)) return MPCG_ERR_WORKSPACE;
   const int smem = team_smem((const void*)k_serve<1>, 1);
   const int smem2 = team_smem((const void*)k_serve<2>, 1);

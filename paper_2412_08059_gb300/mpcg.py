@@ -56,7 +56,7 @@ class Options(C.Structure):
                 ("fp64_only", C.c_int32), ("grid_blocks", C.c_int32), ("timeout_ms", C.c_int32),
                 ("stage1_only", C.c_int32), ("team_rows", C.c_int32),
                 ("serve_split", C.c_int32), ("bfs_starts", C.c_int32),
-                ("precond", C.c_int32)]
+                ("precond", C.c_int32), ("stop_true_residual", C.c_int32)]
 
 
 class Result(C.Structure):

@@ -345,7 +345,9 @@ def test_true_residual_stop_shows_the_stagnation_of_fig2():
     double precision hundreds of iterations later (the paper: k = 506) near
     1e-15, while the recursive residual keeps falling.  So with the stop test
     as printed, eps1 = 1e-7 cannot be met in single precision (the dashes of
-    Table 5), whereas the recursive residual meets it."""
+    Table 5), whereas the recursive residual meets it.  The run ends once its
+    recursive r has fallen 1e3 times below the true residual (the reading
+    for a stagnated stage), well before its cap."""
     A = synth.path(1001, 1.001)
     _, b = synth.rhs(A, seed=1)
     _, _, _, h32 = oracle.cg32(A, b, 0.0, max_it=1200, history=True, true_res=1)
@@ -362,16 +364,18 @@ def test_true_residual_stop_shows_the_stagnation_of_fig2():
     assert k64 > k32 + 200 and f64 < 1e-13
     assert r32.min() < 1e-20                     # the recursive residual does not stagnate
     _, k, st = oracle.cg32(A, b, 1e-7, max_it=3 * A.n, true_res=1)
-    assert st == oracle.ERR_NOT_CONVERGED and k == 3 * A.n
-    _, k, st = oracle.cg32(A, b, 1e-7, max_it=3 * A.n)
-    assert st == 0 and k < 400
-    # Algorithm I with eps1 = 1e-7: stage 1 runs to its cap and warns; the
-    # FP64 stage then ends on the true residual, with no restart.
-    x, r = oracle.solve(A, b, eps1=1e-7, stop_true_residual=1, max_it_fp32=600)
-    assert r["status"] == oracle.WARN_EPS1_NOT_REACHED and r["n1"] == 600
+    assert st == oracle.ERR_NOT_CONVERGED and k32 < k < 3 * A.n
+    hk = r32[k] ** 2          # the recursive r^T r / ||b~||^2 where the run ended
+    assert hk <= 1e-6 * h32[k] ** 2 and r32[k - 1] ** 2 > 1e-6 * h32[k - 1] ** 2
+    _, k1, st = oracle.cg32(A, b, 1e-7, max_it=3 * A.n)
+    assert st == 0 and k1 < k32 + 100
+    # Algorithm I with eps1 = 1e-7: stage 1 ends at the stagnation and warns;
+    # the FP64 stage then ends on the true residual, with no restart.
+    x, r = oracle.solve(A, b, eps1=1e-7, stop_true_residual=1)
+    assert r["status"] == oracle.WARN_EPS1_NOT_REACHED and r["n1"] == k
     assert r["true_rel_resid"] <= 1e-10
-    x0, r0 = oracle.solve(A, b, eps1=1e-7, max_it_fp32=600)
-    assert r0["status"] == 0 and r0["n1"] < 400
+    x0, r0 = oracle.solve(A, b, eps1=1e-7)
+    assert r0["status"] == 0 and r0["n1"] == k1
 
 
 @pytest.mark.parametrize("name", ["lap2d", "xstar", "tree"])
