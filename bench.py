@@ -67,6 +67,8 @@ def parse():
                     help="run the paper's evaluation protocol (Sec. 12) at this fraction of its "
                          "general-sample sizes (0: skip)")
     ap.add_argument("--paper-eval-splits", type=int, default=100)
+    ap.add_argument("--diameter-sweep-only", action="store_true",
+                    help="run only the diameter sweep (thin grids, random 8-regular graph)")
     ap.add_argument("--paper-eval-only", action="store_true",
                     help="run only the evaluation protocol")
     return ap.parse_args()
@@ -125,6 +127,85 @@ def pcg_section(dev, steps=5, warmup=2):
             "speedup_pcg_over_cg": {"mixed": runs["mixed_cg"]["ms"] / runs["mixed_pcg"]["ms"],
                                     "fp64": runs["fp64_cg"]["ms"] / runs["fp64_pcg"]["ms"]},
             "speedup_mixed_over_fp64_with_pcg": runs["fp64_pcg"]["ms"] / runs["mixed_pcg"]["ms"]}
+
+
+def diameter_sweep_section(dev, steps=3, warmup=1):
+    """The diameter sweep: thin 2-D grids 65536x16 and 4096x256 (large
+    pseudo-diameter) and a random 8-regular-like graph Laplacian, n = 2^20,
+    + 1e-3 I (small pseudo-diameter); x* ~ U[-1, 1] (seed 31), eps2 = 1e-10.
+    Per matrix (CUDA events, inputs resident): the 2BFS alone
+    (mpcg_pseudo_diameter), Algorithm II with its fused stage 1 (when the
+    label is known, from the device clock marks), Algorithm I at the eps1
+    that Algorithm II chose, and pure FP64, with N1, N2 and the algorithmic
+    bandwidth of each stage.  The kNN sample is 200 synthetic labelled
+    feature rows spread over the sweep's sizes and diameters: it sets eps1,
+    and what is measured here is the cost of each step at that eps1."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2412_08059_gb300 import mpcg
+
+    mats = [("grid 65536x16", synth.laplacian_2d(65536, 16)),
+            ("grid 4096x256", synth.laplacian_2d(4096, 256)),
+            ("random 8-regular 2^20", synth.random_regular_laplacian(1 << 20, 8, 1e-3, seed=3))]
+    feat, cls = synth.random_sample(200, seed=8)
+    feat[:, 0] = np.linspace(0.5, 2.0, 200) * np.mean([A.n for _, A in mats])
+    feat[:, 1] = np.linspace(0.5, 2.0, 200)[::-1] * np.mean([A.nnz for _, A in mats])
+    feat[:, 2] = np.exp(np.linspace(np.log(3.0), np.log(1.5e5), 200))
+    S = mpcg.DeviceSample(feat, cls, device=dev)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    rows = []
+    for name, A in mats:
+        _, b = synth.rhs(A, seed=31)
+        dA = mpcg.DeviceCSR.from_host(A, dev)
+        db = torch.from_numpy(b).to(dev)
+        n, m = A.n, A.nnz
+        b32, b64 = algorithmic_bytes(n, m, 4), algorithmic_bytes(n, m, 8)
+        ws = mpcg.workspace(n, m, dev)
+        pd = mpcg.pseudo_diameter(dA, ws)[0]
+        row = {"matrix": name, "n": n, "nnz": m, "pdiam": pd,
+               "ms_2bfs": round(timed(lambda: mpcg.pseudo_diameter(dA, ws)), 3)}
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        res = mpcg.result_buffer(1, dev)
+        runs = {}
+        eps1 = None
+        for label, kw in (("algorithm_ii", {}), ("algorithm_i", None), ("fp64", dict(fp64_only=1))):
+            if kw is None:
+                kw = dict(eps1=eps1)
+            o = mpcg.options(**kw)
+            smp = S if label == "algorithm_ii" else None
+            ms = timed(lambda: mpcg.solve_async(dA, db, x, o, ws, res, smp))
+            r = mpcg.read_results(res)[0]
+            out = {"ms": round(ms, 3), "n1": r["n1"], "n2": r["n2"], "status": r["status"],
+                   "true_rel_resid": r["true_rel_resid"]}
+            if label == "algorithm_ii":
+                eps1 = r["eps1"]
+                out.update(eps1=eps1, ms_label_known=round(r["ms_features"], 3))
+            if r["n1"] > 0:
+                out["ms_stage1"] = round(r["ms_fp32"], 3)
+                out["stage1_GBps"] = round(b32 * r["n1"] / (r["ms_fp32"] / 1e3) / 1e9, 1)
+            out["ms_stage2"] = round(r["ms_fp64"], 3)
+            out["stage2_GBps"] = round(b64 * (r["n2"] + 2) / (r["ms_fp64"] / 1e3) / 1e9, 1)
+            runs[label] = out
+        row["runs"] = runs
+        rows.append(row)
+        del ws, dA
+    return {"workload": "diameter sweep: grids 65536x16 and 4096x256, random 8-regular-like "
+                        "Laplacian n=2^20 + 1e-3 I; eps2=1e-10; synthetic kNN sample",
+            "rows": rows}
 
 
 def paper_eval_section(args):
@@ -578,6 +659,10 @@ def native_arm(args, rank, world, local_rank):
     if args.pcg_only:
         if rank == 0:
             print(json.dumps({"pcg": pcg_section(dev)}), flush=True)
+        return
+    if args.diameter_sweep_only:
+        if rank == 0:
+            print(json.dumps({"diameter_sweep": diameter_sweep_section(dev)}), flush=True)
         return
     if args.paper_eval_only:
         if rank == 0:
