@@ -344,8 +344,8 @@ def test_true_residual_stop_shows_the_stagnation_of_fig2():
     hundred iterations (the paper: k = 176) near 1e-7 relative, and that of
     double precision hundreds of iterations later (the paper: k = 506) near
     1e-15, while the recursive residual keeps falling.  So with the stop test
-    as printed, eps1 = 1e-7 cannot be met in single precision (the dashes of
-    Table 5), whereas the recursive residual meets it.  The run ends once its
+    as printed, eps1 = 1e-7 cannot be met in single precision (as Table 5
+    marks for the Jacobi method), whereas the recursive residual meets it.  The run ends once its
     recursive r has fallen 1e3 times below the true residual (the reading
     for a stagnated stage), well before its cap."""
     A = synth.path(1001, 1.001)
