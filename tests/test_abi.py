@@ -68,3 +68,37 @@ def test_oracle_and_library_share_no_code():
             assert "import paper_2412_08059_gb300" not in txt
             assert "from paper_2412_08059_gb300" not in txt
             assert "mpcg.h" not in txt and "libmpcg.so" not in txt
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the header's struct (gcc on the host)."""
+    import shutil
+    import subprocess
+
+    from paper_2412_08059_gb300 import mpcg
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    pairs = {"mpcg_csr_t": mpcg.CsrDesc, "mpcg_features_t": mpcg.Features,
+             "mpcg_sample_t": mpcg.SampleDesc, "mpcg_options_t": mpcg.Options,
+             "mpcg_result_t": mpcg.Result}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mpcg.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe),
+                    str(src)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                               text=True).stdout.splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, py in pairs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
