@@ -925,12 +925,13 @@ def native_arm(args, rank, world, local_rank):
     # ---- CPU oracle baseline (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        costs = oracle_costs(args.size, iters=10)
+        iters = 400  # about 10 s of one core
+        costs = oracle_costs(args.size, iters=iters)
         rate, per_solve = oracle_rate(costs, args.size)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": ("2BFS + 10 FP32 + 10 FP64 oracle iterations on the sigma=0 128^3 system "
+               "sample": ("2BFS + %d FP32 + %d FP64 oracle iterations on the sigma=0 128^3 system "
                           "(%.1f s of CPU); scaled to whole solves by the oracle's own (N1, N2) at "
-                          "its best eps1 per system" % costs["sample_s"]),
+                          "its best eps1 per system" % (iters, iters, costs["sample_s"])),
                "per_iteration_ms": {"fp32": round(costs["t_it32"] * 1e3, 2),
                                     "fp64": round(costs["t_it64"] * 1e3, 2)},
                "host_cores_available": os.cpu_count()}
