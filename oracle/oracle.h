@@ -9,7 +9,10 @@
  * header, table or helper with the CUDA library (libmpcg); neither includes
  * or links the other.  It is written from the paper's text:
  *
- *   CG                 Sec. 3 (the CG procedure), unpreconditioned
+ *   CG                 Sec. 3 (the CG procedure), unpreconditioned; optionally
+ *                      the loop test on ||A x_i - b|| as printed, with the
+ *                      stagnation of Sec. 7 (Fig. 2) ending a stage
+ *   PCG                Sec. 5 (CG with the Jacobi preconditioner)
  *   Algorithm I        Sec. 1 (two stages: FP32 to eps1, promote, FP64 to eps2)
  *   Algorithm II       Sec. 9 (k0 FP32 iterations, features, kNN, continue)
  *   decay rate v       Sec. 9, Eq. (13) and Remark 3
