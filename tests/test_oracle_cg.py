@@ -399,3 +399,19 @@ def test_true_residual_stop_in_both_algorithms(name):
     assert list(f0) == list(f1)
     _, r = oracle.solve(A, b, S=(feat, cls), stop_true_residual=1)
     assert r["v"] == f0[3] and r["true_rel_resid"] <= 1e-10
+
+
+def test_true_residual_stop_with_the_absolute_test():
+    """tol_relative = 0 (the paper's absolute ||A x_i - b|| > eps): the run ends
+    at the first iterate whose unscaled residual is at most eps (rerun as in
+    the relative case, residuals recomputed with scipy)."""
+    A = synth.laplacian_2d(40, 30)
+    _, b = synth.rhs(A, seed=7)
+    M64 = _csr_scipy(A, np.float64)
+    for eps in (1e-4, 1e-7):
+        _, k, st = oracle.cg64(A, b, eps, tol_relative=0, true_res=1)
+        assert st == 0 and k > 0
+        xk, _, _ = oracle.cg64(A, b, 0.0, max_it=k)
+        xp, _, _ = oracle.cg64(A, b, 0.0, max_it=k - 1)
+        assert np.linalg.norm(b - M64 @ xk) <= eps * (1 + 1e-9)
+        assert np.linalg.norm(b - M64 @ xp) > eps * (1 - 1e-9)
