@@ -69,7 +69,7 @@ class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n1", C.c_int32), ("n2", C.c_int32),
                 ("cls", C.c_int32), ("k0_done", C.c_int32), ("eps1", C.c_double),
                 ("true_rel_resid", C.c_double), ("pdiam", C.c_double), ("v", C.c_double),
-                ("feat", C.c_double * 4)]
+                ("feat", C.c_double * 4), ("restarts", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "feat"} | {

@@ -216,11 +216,14 @@ static int cg64_iter(cg64_t* s) {
   return IT_OK;
 }
 
-/* Reading for the stop test on the true residual: once the recursive r has
- * fallen 1e3 times below ||b - A x||, the rounding of the iteration decides
- * the true residual and it no longer falls (the stagnation of Sec. 7,
- * Fig. 2), so a stage that has not met its tolerance then ends as it would
- * at its iteration cap.  Compared on squares: r^T r <= 1e-6 ||b - A x||^2. */
+/* Builder's rule for the stop test on the true residual.  The paper does
+ * not say how a stage ends whose tolerance its precision cannot reach on the
+ * true residual; Sec. 7 (Fig. 2) shows ||b - A x|| ceasing to fall while the
+ * recursively updated residual keeps falling.  This implementation takes a
+ * stage as stagnated once the recursive r has fallen 1e3 times below
+ * ||b - A x|| (the factor 1e3 is its own choice, not the paper's) and ends
+ * it as it would end at its iteration cap.  Compared on squares:
+ * r^T r <= 1e-6 ||b - A x||^2. */
 #define STAGNATION_RR 1e-6
 
 /* Paper-literal stop measure (the loop test of Sec. 3 is on ||A x_i - b||):
@@ -744,13 +747,18 @@ int32_t orc_solve(const orc_csr* A, const double* b, double* x,
       if (r != IT_OK) { status = it_status(r); goto done64; }
       ++n2;
     }
-    /* Reading: if the true residual misses eps2, restart from x.  (With the
+    /* Reading: if the true residual misses eps2, restart from x, at most
+     * max_true_restarts times; if it still misses eps2 after the last one,
+     * the stage has not met its tolerance (eps2 bounds the final residual of
+     * Algorithm I), which is reported as for the iteration cap.  (With the
      * paper-literal stop test the loop above already ended on it.) */
     double tr = orc_true_rel_resid(A, b, x);
     double tm = rel ? tr : tr * bnorm;
     res->true_rel_resid = tr;
-    if (!(tm > o->eps2) || restart >= o->max_true_restarts) break;
+    if (!(tm > o->eps2)) break;
+    if (restart >= o->max_true_restarts) { status = ORC_ERR_NOT_CONVERGED; goto done64; }
     warn_restart = 1;
+    res->restarts = restart + 1;
   }
   status = warn_restart ? ORC_WARN_TRUE_RESID_RESTARTED
                         : (warn_eps1 ? ORC_WARN_EPS1_NOT_REACHED : ORC_OK);

@@ -64,7 +64,8 @@ typedef struct {
   int32_t tol_relative; /* 1: ||r||/||b|| <= eps; 0: ||r|| <= eps (paper-literal) */
   int32_t max_it_fp32;  /* cap on N1 (<= 0: n) */
   int32_t max_it_fp64;  /* cap on N2 (<= 0: 10 n) */
-  int32_t max_true_restarts; /* extra FP64 restarts when the true residual misses eps2 */
+  int32_t max_true_restarts; /* extra FP64 restarts when the true residual misses eps2;
+                                still missing it after the last: ORC_ERR_NOT_CONVERGED */
   uint32_t feat_mask;   /* bit c set: feature c used in the distance */
   int32_t bfs_starts;   /* 2BFS runs for l~ (Sec. 6 remark; <= 1: the single run) */
   int32_t precond;      /* 1: Jacobi-preconditioned CG in both stages (Sec. 5); 0: plain */
@@ -79,6 +80,7 @@ typedef struct {
   int32_t n1, n2, cls, k0_done;
   double eps1, true_rel_resid, pdiam, v;
   double feat[4];
+  int32_t restarts;     /* FP64 restarts taken because the true residual missed eps2 */
 } orc_result;
 
 enum {

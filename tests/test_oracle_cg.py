@@ -415,3 +415,86 @@ def test_true_residual_stop_with_the_absolute_test():
         xp, _, _ = oracle.cg64(A, b, 0.0, max_it=k - 1)
         assert np.linalg.norm(b - M64 @ xk) <= eps * (1 + 1e-9)
         assert np.linalg.norm(b - M64 @ xp) > eps * (1 - 1e-9)
+
+
+# ---- the true-residual restart of the FP64 stage (reading of Algorithm I) ----
+# When the recursive residual meets eps2 and the true one does not, the FP64
+# stage restarts from x (r = b - A x again), at most max_true_restarts times;
+# if the last restart still misses eps2 the run ends NOT_CONVERGED.  The
+# star with a_ii = 1.001 sum_j |a_ij| (n = 1001) shows the branch at eps2 near
+# the rounding level: its first FP64 leg ends with the true residual a few
+# times above 5e-16, one restart brings it several times below.
+
+def _restart_legs(A, b, eps1, eps2, max_restarts):
+    """Algorithm I composed from the separately pinned plain CG runs: FP32 CG
+    from 0 to eps1, then FP64 CG legs from float64(x~), each to eps2 on its
+    recursive residual (a leg starts with r = b - A x), restarting from the
+    leg's x while the true residual -- recomputed here with scipy, not by the
+    oracle -- misses eps2.  Returns x, N1, N2 (all legs), restarts, met."""
+    M = _csr_scipy(A, np.float64)
+    bn = np.linalg.norm(b)
+    x32, n1, st1 = oracle.cg32(A, b, eps1)
+    assert st1 == 0
+    x = x32.astype(np.float64)
+    n2 = restarts = 0
+    legs = []
+    while True:
+        x, it, st = oracle.cg64(A, b, eps2, x0=x)
+        assert st == 0
+        n2 += it
+        tr = np.linalg.norm(b - M @ x) / bn
+        legs.append(tr)
+        if tr <= eps2:
+            return x, n1, n2, restarts, True, legs
+        if restarts >= max_restarts:
+            return x, n1, n2, restarts, False, legs
+        restarts += 1
+
+
+@pytest.mark.parametrize("seed", [3, 8])
+def test_true_residual_restart_fires_and_succeeds(seed):
+    """eps2 = 5e-16: the first leg's true residual misses it (checked with
+    scipy, by a margin), a restart meets it; status, N2 = the sum of both legs,
+    the restart count and x equal the composition of plain CG runs."""
+    A = synth.star(1001, 1.001)
+    _, b = synth.rhs(A, seed=seed)
+    eps2 = 5e-16
+    xc, n1c, n2c, rc, met, legs = _restart_legs(A, b, 1e-4, eps2, 2)
+    assert legs[0] > 2 * eps2 and met and rc == 1 and legs[1] < eps2 / 2
+    x, r = oracle.solve(A, b, eps1=1e-4, eps2=eps2, max_true_restarts=2)
+    assert r["status"] == oracle.WARN_TRUE_RESID_RESTARTED
+    assert (r["n1"], r["n2"], r["restarts"]) == (n1c, n2c, 1)
+    assert np.array_equal(x, xc)
+    M = _csr_scipy(A, np.float64)
+    assert np.linalg.norm(b - M @ x) / np.linalg.norm(b) <= eps2
+    assert r["true_rel_resid"] <= eps2
+
+
+@pytest.mark.parametrize("max_restarts", [0, 2])
+def test_true_residual_restart_exhausted_is_not_converged(max_restarts):
+    """A tolerance below what the rounding allows (eps2 = 1e-19) is never met
+    by the true residual: after max_true_restarts restarts (0 or 2) the run
+    ends NOT_CONVERGED, not with a success status, and N2 counts every leg."""
+    A = synth.star(1001, 1.001)
+    _, b = synth.rhs(A, seed=3)
+    eps2 = 1e-19
+    xc, n1c, n2c, rc, met, legs = _restart_legs(A, b, 1e-4, eps2, max_restarts)
+    assert not met and rc == max_restarts and len(legs) == max_restarts + 1
+    assert min(legs) > 100 * eps2
+    x, r = oracle.solve(A, b, eps1=1e-4, eps2=eps2, max_true_restarts=max_restarts)
+    assert r["status"] == oracle.ERR_NOT_CONVERGED
+    assert (r["n1"], r["n2"], r["restarts"]) == (n1c, n2c, max_restarts)
+    assert np.array_equal(x, xc)
+    M = _csr_scipy(A, np.float64)
+    tr = np.linalg.norm(b - M @ x) / np.linalg.norm(b)
+    assert tr > eps2 and abs(r["true_rel_resid"] - tr) <= 1e-3 * tr
+
+
+def test_true_residual_restart_with_none_allowed_at_5e16():
+    """The same star and eps2 = 5e-16 as the successful restart, but no
+    restart allowed: the first leg's miss is reported as NOT_CONVERGED."""
+    A = synth.star(1001, 1.001)
+    _, b = synth.rhs(A, seed=3)
+    x, r = oracle.solve(A, b, eps1=1e-4, eps2=5e-16, max_true_restarts=0)
+    assert r["status"] == oracle.ERR_NOT_CONVERGED and r["restarts"] == 0
+    assert r["true_rel_resid"] > 5e-16
