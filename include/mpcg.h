@@ -66,7 +66,8 @@ typedef enum {
   MPCG_ERR_WORKSPACE = -2,            /* ws NULL, misaligned (256 B) or smaller than required */
   MPCG_ERR_BREAKDOWN = -3,            /* d^T A d <= 0 in the FP64 stage: A is not SPD */
   MPCG_ERR_NAN = -4,                  /* non-finite value in b, A or an iterate */
-  MPCG_ERR_NOT_CONVERGED = -5,        /* FP64 stage reached max_it_fp64 */
+  MPCG_ERR_NOT_CONVERGED = -5,        /* FP64 stage reached max_it_fp64, or its true residual
+                                         still missed eps2 after max_true_restarts restarts */
   MPCG_ERR_TIMEOUT = -6,              /* a device-side wait exceeded timeout_ms */
   MPCG_ERR_CUDA = -7,                 /* a CUDA launch or runtime call failed */
   MPCG_ERR_CANCELLED = -8,
@@ -111,7 +112,9 @@ typedef struct {
   int32_t tol_relative;      /* 1: ||r||/||b|| <= eps (default); 0: ||r|| <= eps */
   int32_t max_it_fp32;       /* cap on N1 including k0 (<= 0: n) */
   int32_t max_it_fp64;       /* cap on N2 (<= 0: 10 n) */
-  int32_t max_true_restarts; /* extra FP64 restarts if the true residual misses eps2 (default 2) */
+  int32_t max_true_restarts; /* extra FP64 restarts if the true residual misses eps2 (default 2);
+                                if it still misses eps2 after the last one, the status is
+                                MPCG_ERR_NOT_CONVERGED (x holds the last iterate) */
   uint32_t feat_mask;        /* bit c: feature c enters the distance (default 0xF) */
   int32_t fp64_only;         /* 1: pure FP64 CG from x0 = 0 (the baseline); no stage 1 */
   int32_t grid_blocks;       /* persistent grid size; 0 = one full wave of the device */
@@ -324,8 +327,10 @@ int32_t mpcg_server_retire(mpcg_server_t* srv, int32_t slot);
  * callers that must not allocate device memory.  Same arguments, results
  * and status codes as mpcg_solve, minus ws and ws_bytes; the scratch is a
  * fixed array of MPCG_STATIC_WS_BYTES bytes in the library's device code,
- * one per device, whose address is looked up once per device (with that
- * device current).
+ * one per device.  Every call looks up the array's device address in the
+ * calling thread's current context (a host-side name of the array is not a
+ * device address), so the call also works after cudaDeviceReset and under
+ * a context the caller created.
  *   Limit: systems whose mpcg_workspace_bytes(n, nnz, opts) exceeds
  *   MPCG_STATIC_WS_BYTES are rejected with MPCG_ERR_WORKSPACE before
  *   anything is launched (about n <= 200000 for a 7-point stencil).
@@ -334,8 +339,9 @@ int32_t mpcg_server_retire(mpcg_server_t* srv, int32_t slot);
  *   at the same time (different streams, or host threads) share the one
  *   array and corrupt each other's results.  Issue the calls of one device
  *   on one stream, or order them.
- * Errors: as mpcg_solve; MPCG_ERR_CUDA if the array's address cannot be
- * obtained on the current device. */
+ * Errors: as mpcg_solve (argument and option checks first); MPCG_ERR_CUDA
+ * if the array's address cannot be obtained in the current context (the
+ * failed lookup leaves no pending CUDA error behind). */
 int32_t mpcg_solve_static(const mpcg_csr_t* A, const double* b, double* x,
                           const mpcg_sample_t* sample, const mpcg_options_t* opts,
                           mpcg_result_t* res, mpcg_stream_t stream);

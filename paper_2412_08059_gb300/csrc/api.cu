@@ -117,7 +117,8 @@ const char* mpcg_status_string(int32_t s) {
     case MPCG_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case MPCG_ERR_BREAKDOWN: return "breakdown: d^T A d <= 0 (matrix not SPD)";
     case MPCG_ERR_NAN: return "non-finite value";
-    case MPCG_ERR_NOT_CONVERGED: return "FP64 stage did not converge within max_it_fp64";
+    case MPCG_ERR_NOT_CONVERGED:
+      return "FP64 stage did not reach eps2 (iteration cap, or true residual after the last restart)";
     case MPCG_ERR_TIMEOUT: return "device-side wait timed out";
     case MPCG_ERR_CUDA: return "CUDA error";
     case MPCG_ERR_CANCELLED: return "cancelled";

@@ -596,8 +596,10 @@ enum Dec { kGo = 0, kStop = 1, kNan = 2, kBroke = 3, kBreakdown = 4 };
 // ||b~ - A~ x~|| of the current iterate: one more pass over the matrix at the
 // head of every iteration, t = b~ - A~ x~ rounded in single precision and
 // t^T t summed like the other norms.  v (Eq. 13) stays on the recursive r.
-// A stage whose recursive r has fallen 1e3 times below ||b - A x|| has
-// stagnated (Sec. 7, Fig. 2): it ends as at its iteration cap.
+// A stage whose recursive r has fallen 1e3 times below ||b - A x|| is taken
+// as stagnated (the true residual of Sec. 7, Fig. 2, no longer falls) and
+// ends as at its iteration cap.  The paper gives no such rule; the factor
+// 1e3 is this implementation's choice.
 constexpr double kStagnationRR = 1e-6;  // on squares: r^T r <= 1e-6 ||b - A x||^2
 
 template <bool kPc, bool kTrue>
@@ -1085,9 +1087,13 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
       } else if (kind == kTrueRes) {
         true_rel = bnorm > 0.0 ? sqrt(tot) / bnorm : sqrt(tot);
         const double tm = rel ? true_rel : sqrt(tot);
-        if ((tm > eps2) && restarts < max_restarts) {
-          next = kTrueRes + 100;  // restart from x: r = d = q, then the loop head
-          rr = tot;
+        if (tm > eps2) {
+          if (restarts < max_restarts) {
+            next = kTrueRes + 100;  // restart from x: r = d = q, then the loop head
+            rr = tot;
+          } else {
+            failed = MPCG_ERR_NOT_CONVERGED;  // the last restart still missed eps2
+          }
         }
       } else if (kind == kIterate) {
         if (!isfinite(tot)) {

@@ -932,14 +932,15 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
         });
     double tot;
     if (!team_sum_d(t, pt, s.w.partials, red, tot)) return false;
-    int again = 0;
+    int again = 0;  // 1: restart from x; 2: the last restart still missed eps2
     if (lead) {
       true_rel = bnorm > 0.0 ? sqrt(tot) / bnorm : sqrt(tot);
       const double tm = rel ? true_rel : sqrt(tot);
-      again = converged && tm > eps2 && restarts < max_restarts;
+      if (converged && tm > eps2) again = restarts < max_restarts ? 1 : 2;
     }
     again = bcast_dec(t, again);
-    if (!again) break;
+    if (again == 2) failed = MPCG_ERR_NOT_CONVERGED;
+    if (again != 1) break;
     ++restarts;
   }
   if (lead0) {

@@ -102,3 +102,26 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_static_variant_checks_options_before_the_size(lib_path):
+    """mpcg_solve_static validates its arguments and options the way
+    mpcg_solve does before it looks at the size: an invalid option on a
+    system too large for the fixed array is an invalid argument, and a valid
+    one is refused for its size.  Both answers come from host checks alone
+    (the descriptor's pointers are never dereferenced), so no GPU is needed."""
+    import ctypes as C
+
+    from paper_2412_08059_gb300 import mpcg
+    L = mpcg.load(lib_path)
+    n, nnz = 4_000_000, 28_000_000
+    assert mpcg.workspace_bytes(n, nnz) > mpcg.STATIC_WS_BYTES
+    fake = C.c_void_p(256)  # stands in for device memory; no call reaches it
+    A = mpcg.CsrDesc(n, nnz, fake, fake, fake)
+    res = C.c_void_p(512)
+    bad = mpcg.options(knn_k=0)
+    good = mpcg.options(eps1=1e-4)
+    f = L.mpcg_solve_static
+    assert f(C.byref(A), fake, fake, None, C.byref(bad), res, None) == mpcg.ERR_INVALID_ARG
+    assert f(C.byref(A), fake, fake, None, C.byref(good), res, None) == mpcg.ERR_WORKSPACE
+    assert f(C.byref(A), fake, fake, None, None, res, None) == mpcg.ERR_INVALID_ARG
