@@ -70,7 +70,7 @@ struct WarpGroupSync {
         unsigned spins = 0;
         while (ld_acquire(&ctl->bar[slot]) < target) {
           if ((++spins & 1023u) == 0) {
-            if (volatile_status(ctl) != 0) {
+            if (volatile_status(ctl) != 0 || poll_cancel(ctl)) {
               ok = 0;
               break;
             }
@@ -410,6 +410,10 @@ __device__ __noinline__ bool pseudo_diameter_repeats(const BfsGraph& g, int32_t*
   const int R = ctl->bfs_starts;
   for (int r = 1; r < R; ++r) {
     const int s = (int)(((long long)r * g.n) / R);
+    // Every thread has read the previous run's farthest-vertex key before it
+    // is reset: a thread that read the reset key would take another branch
+    // (and another number of barriers) than the rest of the group.
+    if (!sync()) return false;
     if (tid == 0) ctl->key = 0ull;
     if (!sync()) return false;
     const int prev = *reinterpret_cast<volatile int*>(&ctl->pdiam);
