@@ -70,7 +70,7 @@ typedef enum {
                                          still missed eps2 after max_true_restarts restarts */
   MPCG_ERR_TIMEOUT = -6,              /* a device-side wait exceeded timeout_ms */
   MPCG_ERR_CUDA = -7,                 /* a CUDA launch or runtime call failed */
-  MPCG_ERR_CANCELLED = -8,
+  MPCG_ERR_CANCELLED = -8,            /* the caller set the options' cancel word */
   MPCG_ERR_UNIMPLEMENTED = -9
 } mpcg_status_t;
 
@@ -147,6 +147,16 @@ typedef struct {
                                 and mpcg_features only (MPCG_ERR_UNIMPLEMENTED in the batched
                                 solve and the server); Algorithm II then runs its steps as
                                 separate launches in the paper's order */
+  const volatile int32_t* cancel; /* NULL (default), or a word the GPU can read -- mapped pinned
+                                host memory (cudaHostAlloc with cudaHostAllocMapped) or device
+                                memory -- that the caller sets to non-zero to cancel the call
+                                while its work runs.  mpcg_solve, mpcg_solve_static and
+                                mpcg_features poll it at every CG iteration and in every
+                                device-side wait; once they see it set, the call's work ends
+                                with MPCG_ERR_CANCELLED in the result record (x then holds a
+                                partial iterate).  A set word also cancels later calls that
+                                pass it.  The batched solve and the server do not poll it
+                                (the server cancels a system by retiring it between steps) */
 } mpcg_options_t;
 
 /* Result record, written by the device at the end of the call's work into

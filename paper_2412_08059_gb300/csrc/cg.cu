@@ -176,7 +176,7 @@ __device__ __forceinline__ bool cgrid_barrier(Ctl* ctl, int slot, unsigned long 
       unsigned spins = 0;
       while (ld_acquire(&ctl->bar[slot]) < target) {
         if ((++spins & 1023u) == 0) {
-          if (volatile_status(ctl) != 0) {
+          if (volatile_status(ctl) != 0 || poll_cancel(ctl)) {
             ok = 0;
             break;
           }
@@ -587,7 +587,7 @@ __device__ __forceinline__ void p2_32_pc(const CgArgs& a, int R0, int R1, int la
   }
 }
 
-enum Dec { kGo = 0, kStop = 1, kNan = 2, kBroke = 3, kBreakdown = 4 };
+enum Dec { kGo = 0, kStop = 1, kNan = 2, kBroke = 3, kBreakdown = 4, kCancel = 5 };
 
 // kPc: Jacobi-preconditioned CG (the PCG form of Sec. 5): z = dinv r is
 // kept beside r, d is formed from z, alpha = r^T z / d^T q and
@@ -687,6 +687,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
   double vsum = 0.0;  // thread 0
   int k0done = 0, broke = 0;
   double trr = 0.0;   // kTrue: ||b~ - A~ x~||^2 of the current iterate (thread 0)
+  int cw = 0;         // the cancel word as block 0's thread 0 read it during the last pass
 
   while (ok) {
     if constexpr (kTrue) {
@@ -711,11 +712,16 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
       else if (stop_pass(thr, rs) || it >= limit || (a.mode == kCgK0 && rr == 0.0) ||
                (kTrue && rr <= kStagnationRR * rs))
         dec = kStop;
+      if (lead0 && cw != 0) {  // the caller cancelled; the other blocks stop at their next wait
+        set_status(ctl, MPCG_ERR_CANCELLED);
+        dec = kCancel;
+      }
       S.dec = dec;
       if (dec == kNan && lead0) set_status(ctl, MPCG_ERR_NAN);
     }
     cbar<NC>();
     if (S.dec != kGo) break;
+    if (lead0) cw = cancel_word(ctl);  // consumed at the next loop head: latency hidden
 
     // ---- P1: q = A d_k with d_k = r_k + beta_k d_{k-1} formed on the fly ----
     // Plain (coherent) pointers: these vectors change between iterations of
@@ -1028,7 +1034,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
   //   kCheck:    ||b - A x||^2, the stop test of kTrue
   int kind = kRestart;
   const double* x = a.x64;
+  int cw = 0;  // the cancel word as block 0's thread 0 read it during the last pass
   while (ok && kind != kDone) {
+    if (lead0) cw = cancel_word(ctl);  // consumed at the next loop head: latency hidden
     const double* gv = kind == kIterate ? a.d64 : x;
     double p = 0.0, pz = 0.0;
     {
@@ -1172,7 +1180,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
     if (next == -1) {  // loop head: stop test on the recursive residual
       if (lead) {
         int nk = kIterate;
-        if (isnan(rr)) {
+        if (lead0 && cw != 0) {  // the caller cancelled; the other blocks stop at their next wait
+          failed = MPCG_ERR_CANCELLED;
+          set_status(ctl, MPCG_ERR_CANCELLED);
+          nk = kDone;
+        } else if (isnan(rr)) {
           failed = MPCG_ERR_NAN;
           nk = kDone;
         } else if (kTrue) {
@@ -1249,7 +1261,7 @@ __device__ __forceinline__ int wait_label(Ctl* ctl) {
     if (label > 0) return label - 1;
     if (label < 0) return -1;
     if ((++spins & 255u) == 0) {
-      if (volatile_status(ctl) != 0) return -1;
+      if (volatile_status(ctl) != 0 || poll_cancel(ctl)) return -1;
       if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
         set_status(ctl, MPCG_ERR_TIMEOUT);
         return -1;
@@ -1297,7 +1309,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
           break;
         }
         if ((++spins & 255u) == 0) {
-          if (volatile_status(ctl) != 0) break;
+          if (volatile_status(ctl) != 0 || poll_cancel(ctl)) break;
           if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
             set_status(ctl, MPCG_ERR_TIMEOUT);
             break;
@@ -1414,10 +1426,14 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
     }
   }
 
+  int cw = 0;  // the cancel word as block 0's thread 0 read it during the last pass
   while (ok) {
     if (lead) {
       int dec = kGoOn, snap_slot = -1;
-      if (isnan(rr)) {
+      if (lead0 && cw != 0) {  // the caller cancelled; the other blocks stop at their next wait
+        dec = kFailed;
+        set_status(ctl, MPCG_ERR_CANCELLED);
+      } else if (isnan(rr)) {
         dec = kFailed;
         if (lead0) set_status(ctl, MPCG_ERR_NAN);
       } else {
@@ -1476,6 +1492,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
       if (dec == kFailed) ok = false;
       break;
     }
+
+    if (lead0) cw = cancel_word(ctl);  // consumed at the next loop head: latency hidden
 
     // ---- P1: q = A d_k with d_k = r_k + beta_k d_{k-1} formed on the fly ----
     const float* dold = parity ? a.db : a.da;

@@ -54,6 +54,7 @@ struct Ctl {
   unsigned long long t_start, t_prep, t_features, t_fp32, t_fp64, t_end;
   int bfs_starts;  // 2BFS runs for l~ (the repeated 2BFS of Sec. 6; 1 = the single run)
   double rz;       // r^T z of the preconditioned single-precision stage (carried to Continue)
+  const volatile int* cancel;  // the caller's cancel word (option `cancel`), or null
 };
 
 // ---------------------------------------------------------------------------------------
@@ -133,6 +134,19 @@ __device__ __forceinline__ int volatile_status(const Ctl* c) {
   return *reinterpret_cast<const volatile int*>(&c->status);
 }
 
+// Cancellation: the caller's cancel word, when set, ends the call's work with
+// MPCG_ERR_CANCELLED (first error wins).  Read in the periodic checks of the
+// bounded waits and, through cancel_word, at the head of every CG iteration.
+__device__ __forceinline__ int cancel_word(const Ctl* c) {
+  const volatile int* w = c->cancel;
+  return w ? *w : 0;
+}
+__device__ __forceinline__ bool poll_cancel(Ctl* c) {
+  if (cancel_word(c) == 0) return false;
+  set_status(c, MPCG_ERR_CANCELLED);
+  return true;
+}
+
 // Streaming (read-once-per-sweep) loads for the matrix: evict-first in L1/L2.
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
@@ -159,11 +173,16 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, int slot, unsigned long l
       const unsigned long long t0 = globaltimer();
       unsigned spins = 0;
       while (ld_acquire(&ctl->bar[slot]) < target) {
-        if ((++spins & 1023u) == 0 &&
-            globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
-          set_status(ctl, MPCG_ERR_TIMEOUT);
-          ok = 0;
-          break;
+        if ((++spins & 1023u) == 0) {
+          if (volatile_status(ctl) != 0 || poll_cancel(ctl)) {  // another block failed
+            ok = 0;
+            break;
+          }
+          if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
+            set_status(ctl, MPCG_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
         }
       }
     }

@@ -99,6 +99,7 @@ __global__ void k_init(Ctl* c, int n, int nnz, int nslices, int wcap, mpcg_optio
   c->x32_src = -1;
   c->bfs_starts = o.bfs_starts > 1 ? o.bfs_starts : 1;
   c->rz = 0.0;
+  c->cancel = reinterpret_cast<const volatile int*>(o.cancel);
 }
 
 // Jacobi preconditioner M = diag(A) (the PCG form of Sec. 5), one thread per

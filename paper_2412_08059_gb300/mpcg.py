@@ -28,6 +28,7 @@ ERR_NAN = -4
 ERR_NOT_CONVERGED = -5
 ERR_TIMEOUT = -6
 ERR_CUDA = -7
+ERR_CANCELLED = -8
 PHASE_NEW, PHASE_STAGE1, PHASE_STAGE2, PHASE_STAGE2_RUN, PHASE_DONE = 0, 1, 2, 3, 4
 KNN_MAX_SAMPLE = 65536
 KNN_MAX_K = 64
@@ -56,7 +57,8 @@ class Options(C.Structure):
                 ("fp64_only", C.c_int32), ("grid_blocks", C.c_int32), ("timeout_ms", C.c_int32),
                 ("stage1_only", C.c_int32), ("team_rows", C.c_int32),
                 ("serve_split", C.c_int32), ("bfs_starts", C.c_int32),
-                ("precond", C.c_int32), ("stop_true_residual", C.c_int32)]
+                ("precond", C.c_int32), ("stop_true_residual", C.c_int32),
+                ("cancel", C.c_void_p)]
 
 
 class Result(C.Structure):
