@@ -39,6 +39,8 @@
 // k_cg64 (double-precision stage), k_promote and k_spmv.
 #include <math.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace mpcg {
@@ -160,6 +162,25 @@ __device__ __forceinline__ double block_d(double p, CShared<NC>& S) {
   return r;
 }
 
+// The waiting part of a grid barrier (thread 0): poll the arrival counter
+// until it reaches target; bounded in device time; gives up when another
+// block has recorded an error or the caller's cancel word is set.  Kept out
+// of line so that its registers do not weigh on the CG loops.
+__device__ __noinline__ int cgrid_wait(Ctl* ctl, int slot, unsigned long long target) {
+  const unsigned long long t0 = globaltimer();
+  unsigned spins = 0;
+  while (ld_acquire(&ctl->bar[slot]) < target) {
+    if ((++spins & 1023u) == 0) {
+      if (volatile_status(ctl) != 0 || poll_cancel(ctl)) return 0;
+      if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
+        set_status(ctl, MPCG_ERR_TIMEOUT);
+        return 0;
+      }
+    }
+  }
+  return 1;
+}
+
 // Grid barrier among the consumer groups of all blocks; bounded; also stops
 // when another block has recorded an error.
 template <int NC>
@@ -171,23 +192,7 @@ __device__ __forceinline__ bool cgrid_barrier(Ctl* ctl, int slot, unsigned long 
     const unsigned long long target = round * (unsigned long long)gridDim.x;
     red_release_add(&ctl->bar[slot], 1ull);
     int ok = 1;
-    if (ld_acquire(&ctl->bar[slot]) < target) {
-      const unsigned long long t0 = globaltimer();
-      unsigned spins = 0;
-      while (ld_acquire(&ctl->bar[slot]) < target) {
-        if ((++spins & 1023u) == 0) {
-          if (volatile_status(ctl) != 0 || poll_cancel(ctl)) {
-            ok = 0;
-            break;
-          }
-          if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
-            set_status(ctl, MPCG_ERR_TIMEOUT);
-            ok = 0;
-            break;
-          }
-        }
-      }
-    }
+    if (ld_acquire(&ctl->bar[slot]) < target) ok = cgrid_wait(ctl, slot, target);
     *s_ok = ok;
   }
   cbar<NC>();
@@ -225,8 +230,12 @@ struct Ring {
   volatile int* stop;
   int E0, E1;                   // element range of the block
   unsigned nch;                 // chunks per pass
+  int c16;                      // columns are int16 offsets from the row (Ctl::col16)
   __device__ __forceinline__ const int32_t* cols(int s) const {
     return reinterpret_cast<const int32_t*>(base + (size_t)s * stage_bytes<T>());
+  }
+  __device__ __forceinline__ const int16_t* cols16(int s) const {
+    return reinterpret_cast<const int16_t*>(base + (size_t)s * stage_bytes<T>());
   }
   __device__ __forceinline__ const T* vals(int s) const {
     return reinterpret_cast<const T*>(base + (size_t)s * stage_bytes<T>() + kCH * sizeof(int32_t));
@@ -252,9 +261,13 @@ __device__ void ring_producer(const CgArgs& a, Ring<T>& R) {
     const unsigned c = g % R.nch;
     const int e = R.E0 + (int)(c << kLogCH);
     const int cnt = min(kCH, R.E1 - e);
-    mbar_arrive_expect_tx(&R.full[st], (uint32_t)cnt * (uint32_t)(sizeof(int32_t) + sizeof(T)));
-    bulk_g2s(const_cast<int32_t*>(R.cols(st)), a.scol + e, (uint32_t)cnt * sizeof(int32_t),
-             &R.full[st], pol);
+    // int16 offsets: 2 bytes a column (element offsets and counts are
+    // multiples of 32, so the copies stay 16-byte aligned)
+    const uint32_t cb = R.c16 ? 2u : 4u;
+    const void* csrc = R.c16 ? (const void*)(reinterpret_cast<const int16_t*>(a.scol) + e)
+                             : (const void*)(a.scol + e);
+    mbar_arrive_expect_tx(&R.full[st], (uint32_t)cnt * (cb + (uint32_t)sizeof(T)));
+    bulk_g2s(const_cast<int32_t*>(R.cols(st)), csrc, (uint32_t)cnt * cb, &R.full[st], pol);
     bulk_g2s(const_cast<T*>(R.vals(st)), sv + e, (uint32_t)cnt * sizeof(T), &R.full[st], pol);
     issued[st] = g;
   }
@@ -306,28 +319,31 @@ __device__ __forceinline__ void slice_chunks(int r0, int w, unsigned& lo, unsign
 
 // Load the (column, value) pairs of one slice row from the ring.  A slice
 // spans at most two chunks: the stage of its first chunk and the next one.
-template <typename T>
-__device__ __forceinline__ void ring_load(const Ring<T>& R, const Cursor& C, int r0, int w,
-                                          int lane, int (&c)[kFastW], T (&v)[kFastW]) {
+// C16: the ring holds int16 offsets from the row index i.
+template <typename T, bool C16>
+__device__ __forceinline__ void ring_load_t(const Ring<T>& R, const Cursor& C, int r0, int w,
+                                            int lane, int i, int (&c)[kFastW], T (&v)[kFastW]) {
+  using CT = typename std::conditional<C16, int16_t, int32_t>::type;
   const unsigned g0 = C.pass_base + ((unsigned)r0 >> kLogCH);
   const int st0 = (int)(g0 % Ring<T>::S);
   const int st1 = st0 + 1 == Ring<T>::S ? 0 : st0 + 1;
   const int off0 = (r0 & (kCH - 1)) + lane;
-  const int32_t* c0p = R.cols(st0);
+  const int base = C16 ? i : 0;
+  const CT* c0p = reinterpret_cast<const CT*>(R.cols(st0));
   const T* v0p = R.vals(st0);
   if ((r0 & (kCH - 1)) + kSlice * kFastW <= kCH) {  // the slice lies in one chunk
-    const int32_t* cp = c0p + off0;
+    const CT* cp = c0p + off0;
     const T* vp = v0p + off0;
 #pragma unroll
     for (int k = 0; k < kFastW; ++k) {
       if (k < w) {
-        c[k] = cp[kSlice * k];
+        c[k] = base + (int)cp[kSlice * k];
         v[k] = vp[kSlice * k];
       }
     }
     return;
   }
-  const int32_t* c1p = R.cols(st1);
+  const CT* c1p = reinterpret_cast<const CT*>(R.cols(st1));
   const T* v1p = R.vals(st1);
 #pragma unroll
   for (int k = 0; k < kFastW; ++k) {
@@ -335,10 +351,16 @@ __device__ __forceinline__ void ring_load(const Ring<T>& R, const Cursor& C, int
       const int off = off0 + kSlice * k;
       const bool second = off >= kCH;
       const int o = second ? off - kCH : off;
-      c[k] = second ? c1p[o] : c0p[o];
+      c[k] = base + (int)(second ? c1p[o] : c0p[o]);
       v[k] = second ? v1p[o] : v0p[o];
     }
   }
+}
+template <typename T>
+__device__ __forceinline__ void ring_load(const Ring<T>& R, const Cursor& C, int r0, int w,
+                                          int lane, int i, int (&c)[kFastW], T (&v)[kFastW]) {
+  if (R.c16) ring_load_t<T, true>(R, C, r0, w, lane, i, c, v);
+  else ring_load_t<T, false>(R, C, r0, w, lane, i, c, v);
 }
 
 // Row sum of one slice row, generic width, from the ring (plus the tail of an
@@ -352,7 +374,8 @@ __device__ __forceinline__ T ring_row_generic(const CgArgs& a, const Ring<T>& R,
     const int rr = r0 + kSlice * k + lane;
     const int st = (int)((C.pass_base + ((unsigned)rr >> kLogCH)) % Ring<T>::S);
     const int off = rr & (kCH - 1);
-    acc = fma(R.vals(st)[off], G(R.cols(st)[off]), acc);
+    const int cc = R.c16 ? i + (int)R.cols16(st)[off] : R.cols(st)[off];
+    acc = fma(R.vals(st)[off], G(cc), acc);
   }
   if ((wf & kOverflowBit) && i < a.n) {
     const int e1 = a.rp[i + 1];
@@ -397,8 +420,8 @@ __device__ __forceinline__ bool ring_spmv(const CgArgs& a, Ring<T>& R, Cursor& C
       if (ok) {
         int c0[kFastW], c1[kFastW];
         T v0[kFastW], v1[kFastW];
-        ring_load(R, C, r00, w0, lane, c0, v0);
-        ring_load(R, C, r01, w1, lane, c1, v1);
+        ring_load(R, C, r00, w0, lane, i0, c0, v0);
+        ring_load(R, C, r01, w1, lane, i1, c1, v1);
 #pragma unroll
         for (int k = 0; k < kFastW; ++k) {
           if (k < w0) acc0 = fma(v0[k], G(c0[k]), acc0);
@@ -426,7 +449,7 @@ __device__ __forceinline__ bool ring_spmv(const CgArgs& a, Ring<T>& R, Cursor& C
         if (fast_w(wf)) {
           int c[kFastW];
           T v[kFastW];
-          ring_load(R, C, r0, w, lane, c, v);
+          ring_load(R, C, r0, w, lane, i, c, v);
 #pragma unroll
           for (int k = 0; k < kFastW; ++k)
             if (k < w) acc = fma(v[k], G(c[k]), acc);
@@ -457,6 +480,7 @@ __device__ __forceinline__ void ring_setup(const CgArgs& a, char* smem, Ring<T>&
   R.E0 = a.slice_ptr[S0];
   R.E1 = a.slice_ptr[S1];
   R.nch = (unsigned)((R.E1 - R.E0 + kCH - 1) >> kLogCH);
+  R.c16 = a.ctl->col16;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&R.full[s], 1);
@@ -1638,8 +1662,13 @@ __device__ __forceinline__ T spmv_row_direct(const CgArgs& a, int s, int i, cons
   const int w = (int)(wf & ~kOverflowBit);
   const int p = a.slice_ptr[s] + (i & 31);
   const T* sv = svals<T>(a);
+  const int16_t* sc16 = reinterpret_cast<const int16_t*>(a.scol);
+  const bool c16 = a.ctl->col16 != 0;
   T acc = (T)0;
-  for (int k = 0; k < w; ++k) acc = fma(sv[p + kSlice * k], x[a.scol[p + kSlice * k]], acc);
+  for (int k = 0; k < w; ++k) {
+    const int e = p + kSlice * k;
+    acc = fma(sv[e], x[c16 ? i + (int)sc16[e] : a.scol[e]], acc);
+  }
   if (wf & kOverflowBit)
     for (int e = a.rp[i] + w; e < a.rp[i + 1]; ++e) acc = fma((T)a.val[e], x[a.col[e]], acc);
   return acc;

@@ -55,6 +55,10 @@ struct Ctl {
   int bfs_starts;  // 2BFS runs for l~ (the repeated 2BFS of Sec. 6; 1 = the single run)
   double rz;       // r^T z of the preconditioned single-precision stage (carried to Continue)
   const volatile int* cancel;  // the caller's cancel word (option `cancel`), or null
+  // Column format of the sliced layout: 1 = int16 offsets (column - row), set
+  // by the fill when every stored entry's offset fits; 0 = int32 columns.
+  int col16;
+  int colwide;  // some stored entry's offset does not fit in int16
 };
 
 // ---------------------------------------------------------------------------------------
@@ -65,7 +69,7 @@ struct Ws {
   double* partials;      // [4][kMaxGrid]
   uint32_t* slice_w;     // width | overflow flag
   int32_t* slice_ptr;    // [nslices + 1] element offsets
-  int32_t* scol;         // sliced column indices
+  int32_t* scol;         // sliced column indices (int32), or int16 offsets (Ctl::col16)
   float* sv32;           // sliced values, single
   double* sv64;          // sliced values, double
   float *b32, *x32, *r32, *d32a, *d32b, *q32;

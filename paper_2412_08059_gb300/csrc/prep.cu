@@ -139,14 +139,18 @@ cudaError_t launch_jacobi(const Launch& L) {
 }
 
 // One thread per row (padded to whole slices): checks the CSR rules, writes
-// b~ = float32(b), and the width and overflow flag of every slice.
+// b~ = float32(b), and the width and overflow flag of every slice.  Also
+// notes whether some entry kept in the sliced arrays (the first wcap of its
+// row) lies more than 32767 columns from the diagonal: the fill then stores
+// int32 columns, otherwise int16 offsets (a quarter of the FP32 stage's
+// matrix bytes less, a sixth of the FP64 stage's).
 __global__ void k_rows(Ctl* c, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                        const double* __restrict__ b, float* __restrict__ b32,
                        uint32_t* __restrict__ slice_w, int n, int nnz, int nslices, int wcap) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = i >> 5;
   if (s >= nslices) return;  // whole warps exit together
-  int len = 0, ok = 1;
+  int len = 0, ok = 1, wide = 0;
   if (i < n) {
     int a = rp[i], e = rp[i + 1];
     if (a < 0 || e < a || e > nnz) {
@@ -157,6 +161,7 @@ __global__ void k_rows(Ctl* c, const int32_t* __restrict__ rp, const int32_t* __
       for (int k = a; k < e; ++k) {
         int cc = col[k];
         if (cc < 0 || cc >= n || cc <= prev) { ok = 0; break; }
+        if (k - a < wcap && (cc - i > 32767 || i - cc > 32768)) wide = 1;
         prev = cc;
       }
     }
@@ -172,6 +177,7 @@ __global__ void k_rows(Ctl* c, const int32_t* __restrict__ rp, const int32_t* __
   int wmax = __reduce_max_sync(0xffffffffu, w);
   int any_ovf = __any_sync(0xffffffffu, len > wcap);
   if ((threadIdx.x & 31) == 0) slice_w[s] = (uint32_t)wmax | (any_ovf ? kOverflowBit : 0u);
+  if (__any_sync(0xffffffffu, wide) && (threadIdx.x & 31) == 0) atomicExch(&c->colwide, 1);
 }
 
 // Exclusive scan of 32 * width over the slices: one block, tiles of
@@ -222,8 +228,12 @@ __global__ void k_scan(const uint32_t* __restrict__ slice_w, int32_t* __restrict
 
 // Fill the sliced arrays: entry k of row i of slice s sits at
 // slice_ptr[s] + 32 k + (i mod 32), in the row's stored order.  Rows shorter
-// than the slice width are padded with value 0 and their own column.
-__global__ void k_fill(const Ctl* c, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+// than the slice width are padded with value 0 and their own column; the
+// rows past n that fill the last slice, with value 0 and column n - 1 (0 in
+// the int32 form).  Columns are int16 offsets from the row (Ctl::col16) when
+// k_rows found that every one fits, int32 otherwise; the same entries are
+// summed in the same order either way.
+__global__ void k_fill(Ctl* c, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                        const double* __restrict__ val, const uint32_t* __restrict__ slice_w,
                        const int32_t* __restrict__ slice_ptr, int32_t* __restrict__ scol,
                        float* __restrict__ sv32, double* __restrict__ sv64, int n, int nslices) {
@@ -231,6 +241,9 @@ __global__ void k_fill(const Ctl* c, const int32_t* __restrict__ rp, const int32
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = i >> 5, lane = i & 31;
   if (s >= nslices) return;
+  const bool c16 = c->colwide == 0;
+  if (i == 0) c->col16 = c16 ? 1 : 0;
+  int16_t* scol16 = reinterpret_cast<int16_t*>(scol);
   const int w = (int)(slice_w[s] & ~kOverflowBit);
   const int base = slice_ptr[s] + lane;
   int a = 0, len = 0;
@@ -240,16 +253,16 @@ __global__ void k_fill(const Ctl* c, const int32_t* __restrict__ rp, const int32
   }
   for (int k = 0; k < w; ++k) {
     const int e = base + kSlice * k;
+    double v = 0.0;
+    int cc = i < n ? i : (c16 ? n - 1 : 0);
     if (k < len) {
-      const double v = val[a + k];
-      scol[e] = col[a + k];
-      sv64[e] = v;
-      sv32[e] = (float)v;
-    } else {
-      scol[e] = i < n ? i : 0;
-      sv64[e] = 0.0;
-      sv32[e] = 0.0f;
+      v = val[a + k];
+      cc = col[a + k];
     }
+    if (c16) scol16[e] = (int16_t)(cc - i);
+    else scol[e] = cc;
+    sv64[e] = v;
+    sv32[e] = (float)v;
   }
 }
 

@@ -299,3 +299,36 @@ def test_algorithm_ii_classes_outside_two_to_seven(mp, classes):
     xo, ro = oracle.solve(A, b, S=(feat, cls))
     assert r["cls"] == ro["cls"] and r["eps1"] == ro["eps1"] and r["pdiam"] == ro["pdiam"]
     parity(r, ro, x.cpu().numpy(), xo)
+
+
+def _coupled_band(n, D, sigma=0.1):
+    """Tridiagonal SPD matrix plus a symmetric coupling at column offset +-D:
+    4 + sigma on the diagonal, -1 off it (strictly diagonally dominant)."""
+    i = np.concatenate([np.arange(n - 1), np.arange(n - D)])
+    j = np.concatenate([np.arange(1, n), np.arange(D, n)])
+    return synth.from_edges(n, i, j, -np.ones(i.size), np.full(n, 4.0 + sigma), f"band+{D}")
+
+
+@pytest.mark.parametrize("D", [32767, 32768])
+def test_column_offset_format_boundary(mp, D):
+    """The sliced layout stores int16 column offsets (column - row) when every
+    kept entry's offset fits, int32 columns otherwise.  Offsets of +-32767 fit,
+    +32768 does not: on either side the SpMV (single and double) is bit-exact
+    against the oracle and Algorithm I takes the oracle's N1 and N2, the first
+    slices' short rows and the last slice's padding rows included."""
+    n = 70001
+    A = _coupled_band(n, D)
+    dA = mp.DeviceCSR.from_host(A)
+    rng = np.random.default_rng(5)
+    x64 = rng.standard_normal(n)
+    x32 = rng.standard_normal(n).astype(np.float32)
+    y64 = mp.spmv(dA, torch.from_numpy(x64).cuda()).cpu().numpy()
+    y32 = mp.spmv(dA, torch.from_numpy(x32).cuda()).cpu().numpy()
+    assert np.array_equal(y64, oracle.spmv64(A, x64))
+    assert np.array_equal(y32, oracle.spmv32(A, x32))
+    _, b = synth.rhs(A, seed=6)
+    x, r = mp.solve(dA, torch.from_numpy(b).cuda(), eps1=1e-5)
+    xo, ro = oracle.solve(A, b, eps1=1e-5)
+    assert r["status"] == ro["status"] == 0
+    assert r["n1"] == ro["n1"] and close_count(r["n2"], ro["n2"])
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-6 * np.linalg.norm(xo)
