@@ -64,11 +64,11 @@ struct WarpGroupSync {
     int ok = 1;
     if ((threadIdx.x & 31) == 0) {
       const unsigned long long target = round * (unsigned long long)gridDim.x;
-      red_release_add(&ctl->bar[slot], 1ull);
-      if (ld_acquire(&ctl->bar[slot]) < target) {
+      red_release_add(&ctl->bar[slot].v, 1ull);
+      if (ld_acquire(&ctl->bar[slot].v) < target) {
         const unsigned long long t0 = globaltimer();
         unsigned spins = 0;
-        while (ld_acquire(&ctl->bar[slot]) < target) {
+        while (ld_acquire(&ctl->bar[slot].v) < target) {
           if ((++spins & 1023u) == 0) {
             if (volatile_status(ctl) != 0 || poll_cancel(ctl)) {
               ok = 0;

@@ -169,7 +169,7 @@ __device__ __forceinline__ double block_d(double p, CShared<NC>& S) {
 __device__ __noinline__ int cgrid_wait(Ctl* ctl, int slot, unsigned long long target) {
   const unsigned long long t0 = globaltimer();
   unsigned spins = 0;
-  while (ld_acquire(&ctl->bar[slot]) < target) {
+  while (ld_acquire(&ctl->bar[slot].v) < target) {
     if ((++spins & 1023u) == 0) {
       if (volatile_status(ctl) != 0 || poll_cancel(ctl)) return 0;
       if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
@@ -190,9 +190,9 @@ __device__ __forceinline__ bool cgrid_barrier(Ctl* ctl, int slot, unsigned long 
   round += 1;
   if (threadIdx.x == 0) {
     const unsigned long long target = round * (unsigned long long)gridDim.x;
-    red_release_add(&ctl->bar[slot], 1ull);
+    red_release_add(&ctl->bar[slot].v, 1ull);
     int ok = 1;
-    if (ld_acquire(&ctl->bar[slot]) < target) ok = cgrid_wait(ctl, slot, target);
+    if (ld_acquire(&ctl->bar[slot].v) < target) ok = cgrid_wait(ctl, slot, target);
     *s_ok = ok;
   }
   cbar<NC>();

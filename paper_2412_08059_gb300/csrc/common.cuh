@@ -12,15 +12,22 @@ namespace mpcg {
 constexpr int kSlice = 32;          // rows per slice of the sliced layout (one warp)
 constexpr int kCgThreads = 512;     // threads per block of the persistent kernels
 constexpr int kMaxGrid = 2048;      // upper bound on persistent grid blocks
-constexpr int kBarSlots = 32;       // barrier counters per control block
+constexpr int kBarSlots = 8;        // barrier counters per control block
 constexpr uint32_t kOverflowBit = 0x80000000u;
 
 // ---------------------------------------------------------------------------------------
 // Control block: all state of one solve that lives on the device.  Zeroed by
 // the host (cudaMemsetAsync) at the start of every call, then initialised.
 // ---------------------------------------------------------------------------------------
+// A grid-barrier arrival counter alone in a 128-byte line: the blocks that
+// arrive at and poll one barrier do not contend with those of another (the
+// fused stage 1 runs two barriers at once, the CG's and the 2BFS's).
+struct alignas(128) BarSlot {
+  unsigned long long v;
+};
+
 struct Ctl {
-  unsigned long long bar[kBarSlots];  // monotone grid-barrier arrival counters
+  BarSlot bar[kBarSlots];             // monotone grid-barrier arrival counters
   int status;                         // first error wins (atomicCAS from 0)
   int trivial;                        // b == 0: x = 0 and nothing else runs
   int warn_eps1;
@@ -43,11 +50,12 @@ struct Ctl {
   double res32, res64, true_rel;
   // features and kNN
   int pdiam, far_t, reached, ncomp, connected;
-  unsigned long long key;
+  // the 2BFS's atomically updated counters, in a line of their own
+  alignas(128) unsigned long long key;
   int qsize[3];
   int qsizeB[3];   // frontier counters of the second, speculative search
   int ccflag[2];
-  int cls;
+  alignas(128) int cls;
   int eps1_ready;  // fused stage 1: 0 pending, t + 1 when the kNN chose t, -1 on failure
   int x32_src;     // stage-1 result: -1 = x32, s >= 0 = snapshot slot s
   // device clock marks (ns)
@@ -171,12 +179,12 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, int slot, unsigned long l
   round += 1;
   if (threadIdx.x == 0) {
     const unsigned long long target = round * (unsigned long long)gridDim.x;
-    red_release_add(&ctl->bar[slot], 1ull);
+    red_release_add(&ctl->bar[slot].v, 1ull);
     int ok = 1;
-    if (ld_acquire(&ctl->bar[slot]) < target) {
+    if (ld_acquire(&ctl->bar[slot].v) < target) {
       const unsigned long long t0 = globaltimer();
       unsigned spins = 0;
-      while (ld_acquire(&ctl->bar[slot]) < target) {
+      while (ld_acquire(&ctl->bar[slot].v) < target) {
         if ((++spins & 1023u) == 0) {
           if (volatile_status(ctl) != 0 || poll_cancel(ctl)) {  // another block failed
             ok = 0;
