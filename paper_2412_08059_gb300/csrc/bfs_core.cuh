@@ -47,6 +47,8 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 
 // Whole blocks, every thread of the grid: the library's grid barrier.
 struct GridSync {
+  static constexpr bool kWholeBlock = true;  // every thread of every block is in the group
+  static constexpr bool kNarrow = true;      // narrow levels run by one warp
   Ctl* ctl;
   int slot;
   unsigned long long round;
@@ -55,6 +57,8 @@ struct GridSync {
 
 // One warp per block: lane 0 arrives on the counter and polls (bounded).
 struct WarpGroupSync {
+  static constexpr bool kWholeBlock = false;  // one warp of every block is in the group
+  static constexpr bool kNarrow = true;       // narrow levels run by one warp
   Ctl* ctl;
   int slot;
   unsigned long long round;
@@ -205,6 +209,240 @@ __device__ bool bfs_run(const BfsGraph& g, int32_t* dist, int sources, int src, 
   return true;
 }
 
+// ---- one-warp mode of the dual search (narrow frontiers) ----
+// A level whose two frontiers together hold at most kNarrowItems vertices is
+// run by one warp of the group (tid < 32) alone: no group barrier, the
+// frontier in shared memory, row pointers and columns through the read-only
+// cache (a narrow frontier on a banded ordering reuses them level after
+// level).  As nothing else writes the distance arrays meanwhile, a claim is
+// a read of the candidate's distance, a shared-memory set that settles
+// candidates reached twice in the level, and a plain store (levels with a
+// row wider than kNarrowHashDeg claim by compare-and-swap instead).  The warp also writes every claimed vertex to the group's queue of
+// the next level, so that when a frontier grows past kNarrowItems it hands the
+// search back at that level with nothing to copy.  The rest of the group waits
+// on the control block's mode word: one lane of one warp a block polls it with
+// pauses (the one-warp levels are latency-bound and must not share the memory
+// system with a crowd of pollers), and in a whole-block group passes it on
+// through shared memory.
+constexpr int kNarrowItems = 64;
+constexpr int kNarrowHash = 2048;  // shared-memory set of the level's claims (load <= 1/2)
+constexpr int kNarrowHashDeg = 16; // levels with a wider row claim by compare-and-swap
+enum { kNmResume = 1, kNmDone = 2 };
+
+// Whether the mode word ends the wait of the group left at level L: the
+// search finished, or was handed back at a level after L (an earlier
+// hand-back, at L or before, may still be in the word); -1 = a failed wait.
+__device__ __forceinline__ bool nm_ends(int m, int L) {
+  return m == -1 || (m & 3) == kNmDone || ((m & 3) == kNmResume && (m >> 2) > L);
+}
+
+template <bool kBlk>
+__device__ int nm_wait(Ctl* ctl, int L, volatile int* s_mode) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool poller = !kBlk || warp == (blockIdx.x == 0 ? 1 : 0);
+  int m = 0;
+  if (lane == 0) {
+    const unsigned long long t0 = globaltimer();
+    unsigned spins = 0;
+    for (;;) {
+      if (poller) {
+        m = *reinterpret_cast<volatile int*>(&ctl->nmode);
+        if (nm_ends(m, L)) break;
+        __nanosleep(1000);
+        if ((++spins & 15u) == 0) {
+          if (volatile_status(ctl) != 0 || poll_cancel(ctl)) {
+            m = -1;
+            break;
+          }
+          if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns) {
+            set_status(ctl, MPCG_ERR_TIMEOUT);
+            m = -1;
+            break;
+          }
+        }
+      } else {  // the block's poller relays the word (and a failure) in shared memory
+        m = *s_mode;
+        if (nm_ends(m, L)) break;
+        __nanosleep(500);
+        if (globaltimer() - t0 > (unsigned long long)ctl->timeout_ns + 100000000ull) {
+          m = -1;  // the poller's own limit passed long ago (it records the status)
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (kBlk && poller) *s_mode = m;
+  }
+  m = __shfl_sync(0xffffffffu, m, 0);
+  __syncwarp();
+  return m;
+}
+
+// The one warp's levels, from level L whose frontiers (sizes sa, sb) are in
+// the group's queues.  Updates la, lb, reached (search A's vertices) for the
+// levels after L that it completes.  Returns the level at which the group
+// resumes (its frontiers in the queues and counters), or -1 when both
+// searches have ended.
+static __device__ int narrow_levels(const BfsGraph& g, int32_t* dA, int32_t* dB, int L, int sa, int sb,
+                             int& la, int& lb, long long& reached, int (*s_cur)[kNarrowItems],
+                             int (*s_nxt)[kNarrowItems], int* s_hash) {
+  Ctl* ctl = g.ctl;
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < kNarrowHash; i += 32) s_hash[i] = -1;
+  {
+    const int32_t* inA = (L & 1) ? g.fq1 : g.fq0;
+    const int32_t* inB = (L & 1) ? g.fq3 : g.fq2;
+    for (int i = lane; i < sa; i += 32) s_cur[0][i] = __ldcg(inA + i);
+    for (int i = lane; i < sb; i += 32) s_cur[1][i] = __ldcg(inB + i);
+  }
+  __syncwarp();
+  int nA = sa, nB = sb, cur = L;
+  for (;;) {
+    int32_t* outA = (cur & 1) ? g.fq0 : g.fq1;
+    int32_t* outB = (cur & 1) ? g.fq2 : g.fq3;
+    // two frontier items per lane: i = lane, lane + 32 over A's items then B's
+    int u[2], e0[2], deg[2];
+    bool isB[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      isB[h] = i >= nA;
+      u[h] = -1;
+      e0[h] = 0;
+      deg[h] = 0;
+      if (i < nA + nB) u[h] = isB[h] ? s_cur[1][i - nA] : s_cur[0][i];
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (u[h] >= 0) {
+        e0[h] = __ldg(g.rp + u[h]);
+        deg[h] = __ldg(g.rp + u[h] + 1) - e0[h];
+      }
+    }
+    const int maxdeg = __reduce_max_sync(0xffffffffu, max(deg[0], deg[1]));
+    const bool hashed = maxdeg <= kNarrowHashDeg;
+    int totA = 0, totB = 0;
+    for (int k0 = 0; k0 < maxdeg; k0 += 8) {
+      int w[2][8];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[h][j] = (k0 + j < deg[h]) ? __ldg(g.col + e0[h] + k0 + j) : -1;
+      bool push[2][8];
+      if (hashed) {
+        // Only this warp writes the distances now: read them, and settle
+        // duplicates among the level's unvisited candidates in the set.
+        int dv[2][8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int32_t* dist = isB[h] ? dB : dA;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            dv[h][j] = (w[h][j] >= 0 && w[h][j] != u[h]) ? __ldcg(dist + w[h][j]) : 0;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int32_t* dist = isB[h] ? dB : dA;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            push[h][j] = false;
+            if (dv[h][j] == -1) {
+              const int key = 2 * w[h][j] + (isB[h] ? 1 : 0);
+              unsigned slot = ((unsigned)key * 2654435761u) & (kNarrowHash - 1);
+              bool settled = false;
+              // at most 64 items x 16 columns enter a set of 2048 slots, so a
+              // free slot is near; the bound only guards the loop
+              for (int probe = 0; probe < kNarrowHash && !settled; ++probe) {
+                const int old = atomicCAS(&s_hash[slot], -1, key);
+                if (old == -1) {
+                  push[h][j] = true;
+                  dist[w[h][j]] = cur + 1;
+                  settled = true;
+                } else if (old == key) {
+                  settled = true;
+                }
+                slot = (slot + 1) & (kNarrowHash - 1);
+              }
+              if (!settled) push[h][j] = atomicCAS(&dist[w[h][j]], -1, cur + 1) == -1;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int32_t* dist = isB[h] ? dB : dA;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            push[h][j] = w[h][j] >= 0 && w[h][j] != u[h] && atomicCAS(&dist[w[h][j]], -1, cur + 1) == -1;
+        }
+      }
+      int mA = 0, mB = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int mine = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mine += push[h][j] ? 1 : 0;
+        if (isB[h]) mB += mine;
+        else mA += mine;
+      }
+      int incA = mA, incB = mB;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int ta = __shfl_up_sync(0xffffffffu, incA, o);
+        const int tb = __shfl_up_sync(0xffffffffu, incB, o);
+        if (lane >= o) {
+          incA += ta;
+          incB += tb;
+        }
+      }
+      int posA = totA + incA - mA, posB = totB + incB - mB;
+      totA += __shfl_sync(0xffffffffu, incA, 31);
+      totB += __shfl_sync(0xffffffffu, incB, 31);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (push[h][j]) {
+            if (isB[h]) {
+              outB[posB] = w[h][j];
+              if (posB < kNarrowItems) s_nxt[1][posB] = w[h][j];
+              ++posB;
+            } else {
+              outA[posA] = w[h][j];
+              if (posA < kNarrowItems) s_nxt[0][posA] = w[h][j];
+              ++posA;
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (hashed) {  // empty the set for the next level
+      for (int i = lane; i < kNarrowHash; i += 32) s_hash[i] = -1;
+      __syncwarp();
+    }
+    ++cur;
+    if (totA == 0 && totB == 0) return -1;
+    if (totA + totB > kNarrowItems) {  // hand back: the group runs level cur from the queues
+      if (lane == 0) {
+        ctl->qsize[cur % 3] = totA;
+        ctl->qsizeB[cur % 3] = totB;
+        ctl->qsize[(cur + 1) % 3] = 0;
+        ctl->qsizeB[(cur + 1) % 3] = 0;
+      }
+      return cur;
+    }
+    reached += totA;
+    if (totA) la = cur;
+    if (totB) lb = cur;
+    nA = totA;
+    nB = totB;
+    int (*t)[kNarrowItems] = s_cur;
+    s_cur = s_nxt;
+    s_nxt = t;
+  }
+}
+
 // Two breadth-first searches advanced together, one barrier per level: A
 // from srcA into dA (queues fq0/fq1, counters qsize), B from srcB into dB
 // (queues fq2/fq3, counters qsizeB).  Each search is exactly the BFS that
@@ -227,6 +465,7 @@ __device__ bool bfs_dual(const BfsGraph& g, int32_t* dA, int32_t* dB, int srcA, 
       ctl->qsize[k] = 0;
       ctl->qsizeB[k] = 0;
     }
+    ctl->nmode = 0;
   }
   if (!sync()) return false;
   if (tid == 0) {
@@ -247,6 +486,45 @@ __device__ bool bfs_dual(const BfsGraph& g, int32_t* dA, int32_t* dB, int srcA, 
     reached += sa;
     if (sa) la = level;
     if (sb) lb = level;
+    if constexpr (Sync::kNarrow) {
+    if (sa + sb <= kNarrowItems) {
+      // ---- narrow frontiers: one warp runs the next levels alone ----
+      __shared__ int s_nbuf[4][kNarrowItems];  // the warp's current and next frontiers
+      __shared__ int s_hash[kNarrowHash];      // the warp's set of a level's claims
+      __shared__ volatile int s_nmode;         // whole-block groups: the block's copy of the mode word
+      if constexpr (Sync::kWholeBlock) {
+        if (threadIdx.x == 0) s_nmode = 0;
+        __syncthreads();  // every thread of the block is here (same level, same decision)
+      }
+      int resume;
+      if (tid < 32) {
+        resume = narrow_levels(g, dA, dB, level, sa, sb, la, lb, reached,
+                               reinterpret_cast<int (*)[kNarrowItems]>(&s_nbuf[0][0]),
+                               reinterpret_cast<int (*)[kNarrowItems]>(&s_nbuf[2][0]), s_hash);
+        if (lane == 0) {
+          ctl->nla = la;
+          ctl->nlb = lb;
+          ctl->nreached = reached;
+          __threadfence();
+          atomicExch(&ctl->nmode, resume < 0 ? kNmDone : ((resume << 2) | kNmResume));
+        }
+        __syncwarp();
+      } else {
+        const int m = nm_wait<Sync::kWholeBlock>(ctl, level, &s_nmode);
+        if (m == -1) return false;
+        la = *reinterpret_cast<volatile int*>(&ctl->nla);
+        lb = *reinterpret_cast<volatile int*>(&ctl->nlb);
+        reached = *reinterpret_cast<volatile long long*>(&ctl->nreached);
+        resume = (m & 3) == kNmDone ? -1 : (m >> 2);
+      }
+      if (resume < 0) break;
+      // resume: the loop's head reads the level's sizes from the counters
+      // and adds them to the state (the published state stops before it);
+      // the frontiers are larger than kNarrowItems, so the group runs it
+      level = resume;
+      continue;
+    }
+    }
     if (tid == 0) {
       ctl->qsize[(level + 2) % 3] = 0;
       ctl->qsizeB[(level + 2) % 3] = 0;

@@ -63,6 +63,11 @@ struct Ctl {
   int bfs_starts;  // 2BFS runs for l~ (the repeated 2BFS of Sec. 6; 1 = the single run)
   double rz;       // r^T z of the preconditioned single-precision stage (carried to Continue)
   const volatile int* cancel;  // the caller's cancel word (option `cancel`), or null
+  // One-warp mode of the dual 2BFS (bfs_core.cuh): mode word and the state
+  // that a hand-back or the end publishes to the rest of the group
+  alignas(128) int nmode;
+  int nla, nlb;
+  long long nreached;
   // Column format of the sliced layout: 1 = int16 offsets (column - row), set
   // by the fill when every stored entry's offset fits; 0 = int32 columns.
   int col16;
