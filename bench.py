@@ -314,71 +314,64 @@ class Clocks:
 # ------------------------------------------------------------------------------------------
 # CPU oracle timing (bounded sample, one core)
 # ------------------------------------------------------------------------------------------
-def oracle_costs(size, iters=10):
-    """Live per-iteration costs of the oracle on the sigma = 0 system."""
+SAMPLE_FILE = os.path.join(ROOT, "paper_2412_08059_gb300", "data", "sample_lap3d_training.json")
+
+
+def load_sample_file(path=SAMPLE_FILE):
+    """The committed kNN sample of the 3-D family (raw features and labels),
+    read as plain JSON (no library code runs)."""
+    import numpy as np
+    with open(path) as f:
+        d = json.load(f)
+    return np.array(d["feat"], dtype=np.float64), np.array(d["cls"], dtype=np.int8)
+
+
+def oracle_solves(size, names, feat, cls):
+    """Whole Algorithm II solves of the named 128^3 systems by the CPU oracle
+    (one core), each timed on its own.  Returns [(name, seconds, result)]."""
     import oracle
     import synth
     oracle.build()
-    A = synth.laplacian_3d(size)
-    _, b = synth.rhs(A, 1)
-    t0 = time.perf_counter()
-    oracle.pseudo_diameter(A)
-    t_2bfs = time.perf_counter() - t0
-
-    def timed(fn, k):
+    S = oracle.sample(feat, cls)
+    out = []
+    for name, A, _, b in synth.lap3d_workload(size, seed=1):
+        if name not in names:
+            continue
         t = time.perf_counter()
-        fn(A, b, 0.0, max_it=k)
-        return time.perf_counter() - t
-    base32 = timed(oracle.cg32, 0)
-    t32 = (timed(oracle.cg32, iters) - base32) / iters
-    base64 = timed(oracle.cg64, 0)
-    t64 = (timed(oracle.cg64, iters) - base64) / iters
-    return {"t_2bfs": t_2bfs, "t_setup32": base32, "t_setup64": base64, "t_it32": t32,
-            "t_it64": t64, "sample_s": t_2bfs + base32 + base64 + (t32 + t64) * iters + base32
-            + base64}
-
-
-def oracle_rate(costs, size):
-    """Solves/s of the oracle's mixed method at its best eps1 per system (scaled from
-    the bounded sample by the oracle's own iteration counts)."""
-    path = os.path.join(ROOT, "oracle", "data", f"lap3d{size}_counts.json")
-    with open(path) as f:
-        counts = json.load(f)
-    total = 0.0
-    for s in counts["systems"]:
-        best = min(costs["t_setup32"] + costs["t_setup64"] + v["n1"] * costs["t_it32"]
-                   + v["n2"] * costs["t_it64"] for v in s["sweep"].values())
-        total += costs["t_2bfs"] + best
-    nsys = len(counts["systems"])
-    return nsys / total, total / nsys
+        _, r = oracle.solve(A, b, S=S)
+        out.append((name, time.perf_counter() - t, r))
+    return out
 
 
 def reference_arm(args, rank):
+    """The CPU oracle on this workload: one whole Algorithm II solve of each of
+    the six systems, one system a step, each step timed (a step takes seconds
+    to tens of seconds on one core, so --steps is not followed: the arm always
+    runs the six systems once, after one untimed solve of the cheapest)."""
     if rank != 0:
         return
     cfg = workload_config(args.size)
-    vals, walls = [], []
-    for step in range(args.warmup + args.steps):
-        t = time.perf_counter()
-        costs = oracle_costs(args.size, iters=5)
-        rate, per_solve = oracle_rate(costs, args.size)
-        if step >= args.warmup:
-            vals.append(rate)
-            walls.append(time.perf_counter() - t)
-    value = statistics.mean(vals)
-    sample = ("per step: 2BFS + 5 FP32 + 5 FP64 oracle iterations on the sigma=0 128^3 system "
-              "(%.1f s wall); scaled to whole solves by the oracle's own (N1, N2) at its best "
-              "eps1 per system (oracle/data/lap3d%d_counts.json)" % (statistics.mean(walls),
-                                                                    args.size))
+    feat, cls = load_sample_file()
+    oracle_solves(args.size, ("sigma1",), feat, cls)  # warm-up, untimed
+    names = [v[0] for v in __import__("synth").LAP3D_VARIANTS]
+    runs = oracle_solves(args.size, names, feat, cls)
+    total = sum(t for _, t, _ in runs)
+    value = len(runs) / total
+    sample = ("whole Algorithm II solves by the CPU oracle, one of each of the six systems a step "
+              "(%d timed steps, %.1f s in all; --steps %d is not followed), kNN sample "
+              "paper_2412_08059_gb300/data/sample_lap3d_training.json" % (len(runs), total,
+                                                                          args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * cfg["systems"] / value, "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": len(runs), "warmup": 1,
+            "ms_per_step": 1000.0 * total / len(runs), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+                    "d2h_bytes_per_step": 0},
+            "per_system": [{"name": nm, "seconds": round(t, 3), "n1": r["n1"], "n2": r["n2"],
+                            "cls": r["cls"], "status": r["status"]} for nm, t, r in runs]}
     print(json.dumps(line), flush=True)
 
 
@@ -925,15 +918,16 @@ def native_arm(args, rank, world, local_rank):
     # ---- CPU oracle baseline (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        iters = 400  # about 10 s of one core
-        costs = oracle_costs(args.size, iters=iters)
-        rate, per_solve = oracle_rate(costs, args.size)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": ("2BFS + %d FP32 + %d FP64 oracle iterations on the sigma=0 128^3 system "
-                          "(%.1f s of CPU); scaled to whole solves by the oracle's own (N1, N2) at "
-                          "its best eps1 per system" % (iters, iters, costs["sample_s"])),
-               "per_iteration_ms": {"fp32": round(costs["t_it32"] * 1e3, 2),
-                                    "fp64": round(costs["t_it64"] * 1e3, 2)},
+        # whole Algorithm II solves of the two cheapest systems, with the sample
+        # the GPU steps used (about 10-15 s of one core)
+        runs = oracle_solves(args.size, ("sigma1", "sigma1e-2"), feat, cls)
+        total = sum(t for _, t, _ in runs)
+        cpu = {"value": len(runs) / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": ("whole Algorithm II solves by the CPU oracle of two of the six systems "
+                          "(sigma = 1 and 1e-2, the two shortest; %.1f s of CPU), with the GPU "
+                          "steps' kNN sample; the six-system rate is the reference arm's "
+                          "(--impl reference)" % total),
+               "per_system_s": {nm: round(t, 3) for nm, t, _ in runs},
                "host_cores_available": os.cpu_count()}
 
     batch = None
