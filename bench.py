@@ -565,9 +565,10 @@ def serve_section(args, dev):
                     done_t[i] = t_now
                     live.remove((i, slot))
         makespan = time.perf_counter() - t0
+        launches = srv.launches_per_step()
         srv.close()
         res = [mpcg.read_results(r)[0] for r in ress]
-        return done_t, adm_t, makespan, steps, res
+        return done_t, adm_t, makespan, steps, res, launches
 
     def run_fifo(opts, arrivals):
         ws = torch.empty(max(mpcg.workspace_bytes(A.n, A.nnz) for A in mats), dtype=torch.uint8,
@@ -586,14 +587,14 @@ def serve_section(args, dev):
 
     o_mixed = mpcg.options(team_rows=team_rows)
     o_fp64 = mpcg.options(fp64_only=1, team_rows=team_rows)
-    run_server(o_mixed, np.zeros(R))  # warm-up
-    _, _, burst, _, _ = run_server(o_fp64, np.zeros(R))
+    _, _, burst_mixed, _, _, _ = run_server(o_mixed, np.zeros(R))  # also the warm-up
+    _, _, burst, _, _, _ = run_server(o_fp64, np.zeros(R))
     capacity = R / burst  # saturated pure-FP64 serving throughput
     rate = 0.8 * capacity
     arrivals = np.cumsum(rng.exponential(1.0 / rate, R))
     arrivals -= arrivals[0]
 
-    def stats(done_t, adm_t, makespan, steps=None, res=None):
+    def stats(done_t, adm_t, makespan, steps=None, res=None, launches=0):
         lat = (done_t - arrivals) * 1e3
         out = {"solves_per_s": R / makespan, "latency_ms_p50": float(np.percentile(lat, 50)),
                "latency_ms_p99": float(np.percentile(lat, 99)), "latency_ms_mean": float(lat.mean())}
@@ -601,16 +602,16 @@ def serve_section(args, dev):
             out["queue_wait_ms_mean"] = float(((adm_t - arrivals) * 1e3).mean())
         if steps is not None:
             out["steps"] = steps
-            out["gpu_launches"] = 2 * steps  # the step kernel and the abort check after it
+            out["gpu_launches"] = launches * steps  # table staging, step kernel, abort check
         if res is not None:
             out["failed"] = int(sum(r["status"] < 0 for r in res))
             out["max_true_rel_resid_over_eps2"] = float(max(r["true_rel_resid"] / e for r, e in zip(res, req_e)))
         return out
 
-    d, a, mk, st, res = run_server(o_mixed, arrivals)
-    mixed = stats(d, a, mk, st, res)
-    d, a, mk, st, res = run_server(o_fp64, arrivals)
-    fp64 = stats(d, a, mk, st, res)
+    d, a, mk, st, res, nl = run_server(o_mixed, arrivals)
+    mixed = stats(d, a, mk, st, res, nl)
+    d, a, mk, st, res, nl = run_server(o_fp64, arrivals)
+    fp64 = stats(d, a, mk, st, res, nl)
     d, mk = run_fifo(o_mixed, arrivals)
     fifo = stats(d, None, mk)
     return {"workload": f"{R} requests, Poisson arrivals at 80% of the saturated FP64 throughput "
@@ -619,6 +620,7 @@ def serve_section(args, dev):
             "sum_n_resident": int(sum(A.n for A in mats)), "max_iters_per_step": max_iters,
             "autotuned_team_rows": team_rows,
             "saturated_fp64_solves_per_s": capacity,
+            "saturated_mixed_solves_per_s": R / burst_mixed,
             "continuous_batching_mixed": mixed, "continuous_batching_fp64": fp64,
             "one_at_a_time_mixed": fifo}
 

@@ -18,10 +18,10 @@
  *   - Every array argument is DEVICE memory owned by the caller unless the
  *     parameter says otherwise.  The library never allocates device memory:
  *     it carves the caller's workspace `ws` (size from mpcg_workspace_bytes).
- *   - Calls are stream-ordered on `stream`.  The single-system calls never
- *     synchronise the host; mpcg_solve_batch and mpcg_batch_step copy their
- *     descriptor tables from pageable host memory, which by CUDA's rule
- *     waits for earlier work on the stream; mpcg_batch_tune synchronises.
+ *   - Calls are stream-ordered on `stream` and never synchronise the host,
+ *     except mpcg_batch_tune, which times batches.  The descriptor tables of
+ *     mpcg_solve_batch and mpcg_batch_step travel inside kernel parameters,
+ *     so the host buffers they are built in are free when the call returns.
  *     The workspace, the outputs and the inputs must stay valid until the
  *     stream reaches the end of the call's work.  Two calls that share a
  *     workspace must not overlap on the GPU.
@@ -319,11 +319,16 @@ int32_t mpcg_server_admit(mpcg_server_t* srv, const mpcg_csr_t* A, const double*
  * system by at most max_iters iterations per stage, then copies the phase
  * of every slot (int32[max_slots], MPCG_PHASE_*) to slot_phase (host memory,
  * pinned for an asynchronous copy; may be NULL), valid after the stream has
- * synchronised.  Entries of slots that are not admitted are meaningless.
- * The table copy is from host memory and may wait for earlier work on the
- * stream. */
+ * synchronised (a pageable slot_phase makes that copy, and so the call,
+ * wait for the step).  Entries of slots that are not admitted are
+ * meaningless. */
 int32_t mpcg_batch_step(mpcg_server_t* srv, int32_t max_iters, int32_t* slot_phase,
                         mpcg_stream_t stream);
+
+/* Kernel launches that one mpcg_batch_step makes while a system is admitted:
+ * the table staging launches, the step kernel (two with serve_split) and the
+ * abort check.  -1 for a NULL handle.  Host only. */
+int32_t mpcg_batch_step_launches(const mpcg_server_t* srv);
 
 /* Free the slot and the pool block of an admitted system (after its phase
  * is MPCG_PHASE_DONE, or to cancel it between steps). */

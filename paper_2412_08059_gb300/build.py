@@ -9,8 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmpcg.so")
-SOURCES = ("prep.cu", "cg.cu", "bfs.cu", "knn.cu", "api.cu", "noalloc.cu", "batch.cu", "serve.cu")
-HEADERS = ("common.cuh", "internal.h", "bfs_core.cuh", "bfs_block.cuh", "knn_core.cuh", "team_core.cuh")
+SOURCES = ("prep.cu", "cg.cu", "bfs.cu", "knn.cu", "api.cu", "noalloc.cu", "batch.cu", "serve.cu", "stage.cu")
+HEADERS = ("common.cuh", "internal.h", "bfs_core.cuh", "bfs_block.cuh", "knn_core.cuh", "team_core.cuh", "stage.cuh")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

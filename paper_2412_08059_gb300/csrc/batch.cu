@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "stage.cuh"
 #include "team_core.cuh"
 
 namespace mpcg {
@@ -346,6 +347,19 @@ size_t batch_header_bytes(int nsys) {
          a256(sizeof(int) * (size_t)nsys) + 4 * a256(sizeof(int) * kMaxGrid);
 }
 
+// Every record starts as MPCG_ERR_TIMEOUT: a system that the launch leaves
+// unfinished after a team barrier timed out (the launch aborts) reports that
+// instead of the record's earlier contents.
+__global__ void k_pre_records(mpcg_result_t* res, int nsys) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsys) return;
+  mpcg_result_t r;
+  memset(&r, 0, sizeof(r));
+  r.status = MPCG_ERR_TIMEOUT;
+  r.cls = -1;
+  res[i] = r;
+}
+
 int batch_grid(int requested, int smem) {
   return persistent_grid((const void*)k_batch<1>, kBatchThreads, requested, (size_t)smem);
 }
@@ -444,20 +458,9 @@ extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const dou
     sys_off += a256(carve(d, nullptr, nullptr));
   }
   cudaStream_t st = (cudaStream_t)stream;
-  if (cudaMemcpyAsync(dev, blob.data(), hdr, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return MPCG_ERR_CUDA;
-  // Every record starts as MPCG_ERR_TIMEOUT: a system that the launch leaves
-  // unfinished after a team barrier timed out (the launch aborts) reports
-  // that instead of the record's earlier contents.
-  std::vector<mpcg_result_t> pre((size_t)nsys);
-  memset(pre.data(), 0, sizeof(mpcg_result_t) * (size_t)nsys);
-  for (auto& r : pre) {
-    r.status = MPCG_ERR_TIMEOUT;
-    r.cls = -1;
-  }
-  if (cudaMemcpyAsync(res, pre.data(), sizeof(mpcg_result_t) * (size_t)nsys, cudaMemcpyDefault,
-                      st) != cudaSuccess)
-    return MPCG_ERR_CUDA;
+  if (stage_to_device(dev, blob.data(), hdr, st) != cudaSuccess) return MPCG_ERR_CUDA;
+  k_pre_records<<<(nsys + 255) / 256, 256, 0, st>>>(res, nsys);
+  if (cudaGetLastError() != cudaSuccess) return MPCG_ERR_CUDA;
   BatchArgs a{};
   a.h = Hd;
   a.sys = Syd;

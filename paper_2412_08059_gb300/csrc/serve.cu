@@ -21,6 +21,7 @@
 #include <map>
 #include <vector>
 
+#include "stage.cuh"
 #include "team_core.cuh"
 
 namespace mpcg {
@@ -216,7 +217,7 @@ struct mpcg_server {
   char* dev;              // workspace base (device)
   int max_slots;
   size_t pool_off, pool_bytes;
-  std::vector<char> mirror;  // host copy of the tables region
+  std::vector<char> mirror;  // host copy of the tables region, staged each step
   BatchSys* sys_h;           // inside mirror
   int* phase_d;
   std::vector<int> active;       // 1 if admitted and not retired
@@ -355,6 +356,13 @@ extern "C" int32_t mpcg_server_retire(mpcg_server_t* s, int32_t slot) {
   return MPCG_OK;
 }
 
+extern "C" int32_t mpcg_batch_step_launches(const mpcg_server_t* s) {
+  if (!s) return -1;
+  const int stage = (int)((s->mirror.size() + kStageChunk - 1) / kStageChunk);
+  const bool split = s->o.serve_split && !s->o.fp64_only;
+  return stage + (split ? 2 : 1) + 1;
+}
+
 extern "C" int32_t mpcg_batch_step(mpcg_server_t* s, int32_t max_iters, int32_t* slot_phase,
                                    mpcg_stream_t stream) {
   if (!s || max_iters <= 0) return MPCG_ERR_INVALID_ARG;
@@ -402,8 +410,7 @@ extern "C" int32_t mpcg_batch_step(mpcg_server_t* s, int32_t max_iters, int32_t*
     a.o = s->o;
     a.auto_eps1 = s->auto_eps1;
     a.knn = s->knn;
-    if (cudaMemcpyAsync(s->dev, m, s->mirror.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
-      return MPCG_ERR_CUDA;
+    if (stage_to_device(s->dev, m, s->mirror.size(), st) != cudaSuccess) return MPCG_ERR_CUDA;
     ServeArgs sa{};
     sa.phase = s->phase_d;
     sa.budget = max_iters;

@@ -88,7 +88,7 @@ SYMBOLS = ("mpcg_options_default", "mpcg_status_string", "mpcg_workspace_bytes",
            "mpcg_choose_eps1", "mpcg_solve", "mpcg_batch_workspace_bytes", "mpcg_solve_batch",
            "mpcg_spmv", "mpcg_bfs", "mpcg_pseudo_diameter", "mpcg_solve_static",
            "mpcg_server_workspace_bytes", "mpcg_server_create", "mpcg_server_destroy",
-           "mpcg_server_admit", "mpcg_batch_step", "mpcg_server_retire", "mpcg_batch_tune",
+           "mpcg_server_admit", "mpcg_batch_step", "mpcg_batch_step_launches", "mpcg_server_retire", "mpcg_batch_tune",
            "mpcg_knn_batch")
 
 
@@ -144,6 +144,8 @@ def load(path: str = LIB_PATH):
                                         C.POINTER(I32)]
         L.mpcg_batch_step.restype = I32
         L.mpcg_batch_step.argtypes = [P, I32, P, P]
+        L.mpcg_batch_step_launches.restype = I32
+        L.mpcg_batch_step_launches.argtypes = [P]
         L.mpcg_server_retire.restype = I32
         L.mpcg_server_retire.argtypes = [P, I32]
         L.mpcg_solve_static.restype = I32
@@ -414,6 +416,10 @@ class Server:
         st = load().mpcg_batch_step(self.h, int(max_iters), C.c_void_p(self.phase.data_ptr()),
                                     _stream(stream))
         _check(st, "mpcg_batch_step")
+
+    def launches_per_step(self) -> int:
+        """Kernel launches of one step while a system is admitted."""
+        return int(load().mpcg_batch_step_launches(self.h))
 
     def retire(self, slot: int) -> None:
         _check(load().mpcg_server_retire(self.h, int(slot)), "mpcg_server_retire")

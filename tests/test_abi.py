@@ -51,6 +51,7 @@ def test_host_only_entry_points(lib_path):
     wb = mpcg.workspace_bytes(n, nnz)
     # sliced arrays (<= 32 * wcap per slice, 16 B per entry) + vectors: < 1 GB at 128^3
     assert 16 * nnz < wb < 1_000_000_000
+    assert mpcg.load().mpcg_batch_step_launches(None) == -1
 
 
 def test_oracle_and_library_share_no_code():

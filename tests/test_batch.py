@@ -226,3 +226,30 @@ def test_batch_abort_reports_timeout_not_stale_records(mp):
             parity(r, ro, x.cpu().numpy(), xo)
     rs = run()  # same workspace, default limit
     assert all(r["status"] >= 0 and r["true_rel_resid"] <= 1e-10 for r in rs)
+
+
+def test_batch_call_does_not_wait_for_earlier_stream_work(mp):
+    """The descriptor tables travel inside kernel parameters: the call
+    returns while a long kernel still runs ahead of it on the stream, and the
+    batch still sees its tables (results equal the oracle's)."""
+    import time
+    mats = mixed_systems()[:6] + [synth.laplacian_2d(10 + i % 5, 9) for i in range(200)]
+    bs = [synth.rhs(A, seed=500 + i)[1] for i, A in enumerate(mats)]
+    dmats = [mp.DeviceCSR.from_host(A) for A in mats]
+    dbs = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in bs]
+    xs = [torch.full((A.n,), np.nan, dtype=torch.float64, device="cuda") for A in mats]
+    ws = torch.empty(mp.batch_workspace_bytes(dmats), dtype=torch.uint8, device="cuda")
+    res = mp.result_buffer(len(mats))
+    o = mp.options(eps1=1e-5)
+    torch.cuda.synchronize()
+    torch.cuda._sleep(1_000_000_000)  # about half a second of device time
+    t0 = time.perf_counter()
+    mp.solve_batch_async(dmats, dbs, xs, o, ws, res, None)
+    t_call = time.perf_counter() - t0
+    assert not torch.cuda.current_stream().query()  # the sleep is still running
+    torch.cuda.synchronize()
+    assert t_call < 0.2, t_call
+    rs = mp.read_results(res, len(mats))
+    for k in [0, 3, 5, 6, 205]:
+        xo, ro = oracle.solve(mats[k], bs[k], eps1=1e-5)
+        parity(rs[k], ro, xs[k].cpu().numpy(), xo)

@@ -197,3 +197,44 @@ def test_serve_abort_ends_the_system_as_timed_out(mp):
         assert m["status"] == ro["status"] and m["cls"] == ro["cls"]
         assert close_count(m["n1"], ro["n1"]) and close_count(m["n2"], ro["n2"])
         assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+def test_serve_step_does_not_wait_for_earlier_stream_work(mp):
+    """A step stages its slot tables inside kernel parameters and copies the
+    phases to pinned memory: it returns while earlier work still runs."""
+    import time
+    reqs = requests(mp)[:4]
+    o = mp.options(eps1=1e-4)
+    pool = sum(mp.workspace_bytes(r.A.n, r.A.nnz) for r in reqs) + (1 << 20)
+    srv = mp.Server(64, pool, o, None)
+    for r in reqs:
+        r.slot = srv.admit(r.dA, r.db, r.x, r.eps2, r.res)
+        assert r.slot is not None
+    torch.cuda.synchronize()
+    torch.cuda._sleep(1_000_000_000)  # about half a second of device time
+    t0 = time.perf_counter()
+    srv.step(20)
+    t_call = time.perf_counter() - t0
+    assert not torch.cuda.current_stream().query()
+    torch.cuda.synchronize()
+    assert t_call < 0.2, t_call
+    assert srv.launches_per_step() >= 3
+    live = list(reqs)
+    for _ in range(100000):  # finish the admitted requests
+        ph = srv.phase.numpy()
+        for r in list(live):
+            if ph[r.slot] == mp.PHASE_DONE:
+                srv.retire(r.slot)
+                live.remove(r)
+        if not live:
+            break
+        srv.step(20)
+        torch.cuda.synchronize()
+    assert not live
+    for r in reqs:
+        x, res = r.result(mp)
+        xo, ro = oracle.solve(r.A, r.b, eps1=1e-4)
+        assert res["status"] == ro["status"]
+        assert close_count(res["n1"], ro["n1"]) and close_count(res["n2"], ro["n2"])
+        assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
+    srv.close()
