@@ -67,6 +67,15 @@ def parse():
                     help="run the paper's evaluation protocol (Sec. 12) at this fraction of its "
                          "general-sample sizes (0: skip)")
     ap.add_argument("--paper-eval-splits", type=int, default=100)
+    ap.add_argument("--paper-eval-acc32", action="store_true",
+                    help="evaluation protocol with the single-precision inner products summed in "
+                         "float (option acc32)")
+    ap.add_argument("--paper-eval-absolute", action="store_true",
+                    help="evaluation protocol with the absolute stop test ||r|| <= eps of Sec. 3 "
+                         "(option tol_relative = 0)")
+    ap.add_argument("--kappa-study-only", type=int, default=0, metavar="SYSTEMS",
+                    help="run only the efficiency-vs-pseudo-diameter study by kappa class "
+                         "(Sec. 7, Tables 1-3 analogue) on this many Laplacians")
     ap.add_argument("--diameter-sweep-only", action="store_true",
                     help="run only the diameter sweep (thin grids, random 8-regular graph)")
     ap.add_argument("--paper-eval-only", action="store_true",
@@ -216,10 +225,28 @@ def paper_eval_section(args):
     from paper_2412_08059_gb300 import evaluate
     t = time.time()
     res = evaluate.run(scale=args.paper_eval, splits=args.paper_eval_splits,
-                       log=lambda m: print(m, file=sys.stderr, flush=True))
+                       log=lambda m: print(m, file=sys.stderr, flush=True),
+                       acc32=int(args.paper_eval_acc32),
+                       tol_relative=0 if args.paper_eval_absolute else 1)
     return {"scale_of_paper_sample_sizes": args.paper_eval, "splits": args.paper_eval_splits,
+            "single_precision_sums": "float (acc32)" if args.paper_eval_acc32 else "double",
+            "stop_test": "absolute ||r|| <= eps" if args.paper_eval_absolute
+                         else "relative ||r||/||b|| <= eps",
             "features": "(m, l~, v), weighted kNN", "seconds": round(time.time() - t, 1),
             "samples": res}
+
+
+def kappa_study_section(args):
+    """Tables 1-3 analogue (Sec. 7): E with the optimal eps1 (Eq. 12) against
+    the mean pseudo-diameter, by condition-number class, on seeded 2-D and 3-D
+    Laplacians whose kappa has a closed form (evaluate.laplacian_sample)."""
+    from paper_2412_08059_gb300 import evaluate
+    res = evaluate.kappa_study(args.kappa_study_only,
+                               log=lambda m: print(m, file=sys.stderr, flush=True))
+    res["workload"] = (f"{args.kappa_study_only} Laplacians, 2-D (70 %) and 3-D, n log-uniform "
+                       "[1e3, 2.6e5], aspect 1..256, coupling 1 or 1e-2, shift 0 or "
+                       "log-uniform [1e-5, 3]; eps2 = 1e-10; eps1 = 1e-2..1e-7")
+    return res
 
 
 def workload_config(size):
@@ -658,6 +685,10 @@ def native_arm(args, rank, world, local_rank):
     if args.diameter_sweep_only:
         if rank == 0:
             print(json.dumps({"diameter_sweep": diameter_sweep_section(dev)}), flush=True)
+        return
+    if args.kappa_study_only:
+        if rank == 0:
+            print(json.dumps({"kappa_study": kappa_study_section(args)}), flush=True)
         return
     if args.paper_eval_only:
         if rank == 0:

@@ -157,6 +157,14 @@ typedef struct {
                                 partial iterate).  A set word also cancels later calls that
                                 pass it.  The batched solve and the server do not poll it
                                 (the server cancels a system by retiring it between steps) */
+  int32_t acc32;             /* 1: every inner product of the single-precision stage (r^T r,
+                                d^T q, ||b~||) is summed in float: each thread sums its rows in
+                                order, then a butterfly over the warp's lanes, the warps of a
+                                block in index order, and the blocks in index order, every
+                                add rounded to float.  0 (default): the same tree carried in
+                                float-float and the blocks summed in double, the reading of
+                                Sec. 9, Remark 3 (norms of the single-precision stage computed
+                                in double).  The FP64 stage is the same either way */
 } mpcg_options_t;
 
 /* Result record, written by the device at the end of the call's work into

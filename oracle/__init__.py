@@ -62,7 +62,7 @@ class Opts(C.Structure):
                 ("max_it_fp32", C.c_int32), ("max_it_fp64", C.c_int32),
                 ("max_true_restarts", C.c_int32), ("feat_mask", C.c_uint32),
                 ("bfs_starts", C.c_int32), ("precond", C.c_int32),
-                ("stop_true_residual", C.c_int32)]
+                ("stop_true_residual", C.c_int32), ("acc32", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -89,10 +89,13 @@ def lib():
             L.orc_dot64.restype = C.c_double
             L.orc_dot32.argtypes = [C.c_int32, P, P]
             L.orc_dot32.restype = C.c_double
+            L.orc_dot32_f.argtypes = [C.c_int32, P, P]
+            L.orc_dot32_f.restype = C.c_double
             L.orc_cg64.argtypes = [C.POINTER(Csr), P, P, C.c_double, C.c_int32, C.c_int32,
                                    C.c_int32, C.c_int32, C.POINTER(C.c_int32), P]
             L.orc_cg64.restype = C.c_int32
-            L.orc_cg32.argtypes = L.orc_cg64.argtypes
+            L.orc_cg32.argtypes = [C.POINTER(Csr), P, P, C.c_double, C.c_int32, C.c_int32,
+                                   C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32), P]
             L.orc_cg32.restype = C.c_int32
             L.orc_bfs.argtypes = [C.POINTER(Csr), C.c_int32, P]
             L.orc_bfs.restype = C.c_int32
@@ -188,10 +191,13 @@ def spmv32(A, x):
     return y
 
 
-def dot32(a, b):
+def dot32(a, b, acc32=0):
+    """Inner product of two float vectors: summed in double, or with acc32=1
+    summed in float in index order."""
     a = np.ascontiguousarray(a, dtype=np.float32)
     b = np.ascontiguousarray(b, dtype=np.float32)
-    return lib().orc_dot32(a.size, _ptr(a), _ptr(b))
+    f = lib().orc_dot32_f if acc32 else lib().orc_dot32
+    return f(a.size, _ptr(a), _ptr(b))
 
 
 def dot64(a, b):
@@ -218,9 +224,11 @@ def cg64(A, b, eps, x0=None, tol_relative=1, max_it=None, history=False, precond
     return out + (hist[: it.value + 1],) if history else out
 
 
-def cg32(A, b, eps, tol_relative=1, max_it=None, history=False, precond=0, true_res=0):
+def cg32(A, b, eps, tol_relative=1, max_it=None, history=False, precond=0, true_res=0,
+         acc32=0):
     """Plain FP32 CG on float32(A), float32(b) from 0 (precond=1: Jacobi PCG;
-    true_res=1: stop on ||b~ - A~ x~||).  Returns (x32, iters, status[, hist])."""
+    true_res=1: stop on ||b~ - A~ x~||; acc32=1: inner products summed in
+    float).  Returns (x32, iters, status[, hist])."""
     h = csr(A)
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(h.n, dtype=np.float32)
@@ -228,7 +236,7 @@ def cg32(A, b, eps, tol_relative=1, max_it=None, history=False, precond=0, true_
     it = C.c_int32(0)
     hist = np.full(max_it + 1, np.nan) if history else None
     st = lib().orc_cg32(C.byref(h.s), _ptr(b), _ptr(x), eps, tol_relative, max_it,
-                        int(precond), int(true_res), C.byref(it),
+                        int(precond), int(true_res), int(acc32), C.byref(it),
                         _ptr(hist) if history else None)
     out = (x, it.value, st)
     return out + (hist[: it.value + 1],) if history else out

@@ -57,6 +57,18 @@ double orc_dot32(int32_t n, const float* a, const float* b) {
   return s;
 }
 
+/* The other reading of the single-precision stage's inner products: both
+ * the products and the running sum rounded to float, in index order.  The
+ * float result is returned widened (exactly) to double. */
+double orc_dot32_f(int32_t n, const float* a, const float* b) {
+  float s = 0.0f;
+  for (int32_t i = 0; i < n; ++i) {
+    const float p = a[i] * b[i];
+    s = s + p;
+  }
+  return (double)s;
+}
+
 /* Stop measure of the CG loop test (Sec. 3): ||r||, or ||r||/||b|| when the
  * relative reading is selected.  r is the recursively updated residual. */
 static double stop_measure(double rr, double bnorm, int32_t rel) {
@@ -77,12 +89,20 @@ typedef struct {
   const float* dinv;
   float* z;
   double rz;
+  int acc32;  /* inner products summed in float (orc_dot32_f) instead of double */
 } cg32_t;
+
+/* Inner product of the single-precision stage in the selected reading. */
+static double sdot(const cg32_t* s, const float* a, const float* b) {
+  return s->acc32 ? orc_dot32_f(s->n, a, b) : orc_dot32(s->n, a, b);
+}
 
 enum { IT_OK = 0, IT_BREAKDOWN = 1, IT_NAN = 2 };
 
-static int cg32_alloc(cg32_t* s, const orc_csr* A, const float* v32, const float* dinv) {
+static int cg32_alloc(cg32_t* s, const orc_csr* A, const float* v32, const float* dinv,
+                      int acc32) {
   s->n = A->n;
+  s->acc32 = acc32;
   s->rp = A->row_ptr;
   s->ci = A->col;
   s->v32 = v32;
@@ -110,11 +130,11 @@ static void cg32_start(cg32_t* s, const float* b32) {
   if (s->dinv) {
     for (int32_t i = 0; i < s->n; ++i) s->z[i] = s->dinv[i] * s->r[i];
     for (int32_t i = 0; i < s->n; ++i) s->d[i] = s->z[i];
-    s->rz = orc_dot32(s->n, s->r, s->z);
+    s->rz = sdot(s, s->r, s->z);
   } else {
     for (int32_t i = 0; i < s->n; ++i) s->d[i] = s->r[i];
   }
-  s->rr = orc_dot32(s->n, s->r, s->r);
+  s->rr = sdot(s, s->r, s->r);
 }
 
 /* One CG iteration (the loop body of Sec. 3) in single precision.
@@ -122,18 +142,18 @@ static void cg32_start(cg32_t* s, const float* b32) {
 static int cg32_iter(cg32_t* s) {
   const int32_t n = s->n;
   orc_spmv32(n, s->rp, s->ci, s->v32, s->d, s->q);         /* q = A d      */
-  double dq = orc_dot32(n, s->d, s->q);                      /* d^T A d      */
+  double dq = sdot(s, s->d, s->q);                           /* d^T A d      */
   if (!isfinite(dq)) return IT_NAN;
   if (!(dq > 0.0)) return IT_BREAKDOWN;
   const double num = s->dinv ? s->rz : s->rr;                /* PCG: r^T z   */
   float alpha = (float)(num / dq);                           /* alpha_i      */
   for (int32_t i = 0; i < n; ++i) s->x[i] = fmaf(alpha, s->d[i], s->x[i]);
   for (int32_t i = 0; i < n; ++i) s->r[i] = fmaf(-alpha, s->q[i], s->r[i]);
-  double rr_new = orc_dot32(n, s->r, s->r);
+  double rr_new = sdot(s, s->r, s->r);
   if (!isfinite(rr_new)) return IT_NAN;
   if (s->dinv) {                                             /* z = M^-1 r   */
     for (int32_t i = 0; i < n; ++i) s->z[i] = s->dinv[i] * s->r[i];
-    double rz_new = orc_dot32(n, s->r, s->z);
+    double rz_new = sdot(s, s->r, s->z);
     if (!isfinite(rz_new)) return IT_NAN;
     float beta = (float)(rz_new / s->rz);
     for (int32_t i = 0; i < n; ++i) s->d[i] = fmaf(beta, s->d[i], s->z[i]);
@@ -236,7 +256,7 @@ static double true_rr32(const cg32_t* s, const float* b32) {
   if (!t) return NAN;
   orc_spmv32(s->n, s->rp, s->ci, s->v32, s->x, t);
   for (int32_t i = 0; i < s->n; ++i) t[i] = b32[i] - t[i];
-  const double rr = orc_dot32(s->n, t, t);
+  const double rr = sdot(s, t, t);
   free(t);
   return rr;
 }
@@ -323,7 +343,7 @@ int32_t orc_cg64(const orc_csr* A, const double* b, double* x, double eps,
 
 int32_t orc_cg32(const orc_csr* A, const double* b, float* x, double eps,
                  int32_t tol_relative, int32_t max_it, int32_t precond, int32_t true_res,
-                 int32_t* iters, double* res_hist) {
+                 int32_t acc32, int32_t* iters, double* res_hist) {
   *iters = 0;
   if (!csr_ok(A)) return ORC_ERR_INVALID_ARG;
   const int32_t n = A->n;
@@ -337,9 +357,9 @@ int32_t orc_cg32(const orc_csr* A, const double* b, float* x, double eps,
     for (int32_t i = 0; i < n; ++i) b32[i] = (float)b[i];
   }
   int ok = v32 && b32 && (!precond || (dinv && jacobi_dinv(A, NULL, dinv))) &&
-           cg32_alloc(&s, A, v32, dinv);
+           cg32_alloc(&s, A, v32, dinv, acc32);
   if (ok) {
-    double bnorm = sqrt(orc_dot32(n, b32, b32));
+    double bnorm = sqrt(sdot(&s, b32, b32));
     cg32_start(&s, b32);
     for (;;) {
       const double trr = true_res ? true_rr32(&s, b32) : s.rr;
@@ -565,6 +585,7 @@ orc_opts orc_opts_default(void) {
   o.bfs_starts = 1;
   o.precond = 0;
   o.stop_true_residual = 0;
+  o.acc32 = 0;
   return o;
 }
 
@@ -628,8 +649,8 @@ int32_t orc_features(const orc_csr* A, const double* b, const orc_opts* o,
   }
   for (int32_t e = 0; e < A->nnz; ++e) v32[e] = (float)A->val[e];
   for (int32_t i = 0; i < n; ++i) b32[i] = (float)b[i];
-  if (!cg32_alloc(&s, A, v32, dinv)) { free(v32); free(b32); free(dinv); return ORC_ERR_INVALID_ARG; }
-  double bnorm32 = sqrt(orc_dot32(n, b32, b32));
+  if (!cg32_alloc(&s, A, v32, dinv, o->acc32)) { free(v32); free(b32); free(dinv); return ORC_ERR_INVALID_ARG; }
+  double bnorm32 = sqrt(sdot(&s, b32, b32));
   cg32_start(&s, b32);
   int32_t n1 = 0, broke = 0;
   double v = 0.0;
@@ -683,11 +704,11 @@ int32_t orc_solve(const orc_csr* A, const double* b, double* x,
   }
   for (int32_t e = 0; e < A->nnz; ++e) v32[e] = (float)A->val[e];
   for (int32_t i = 0; i < n; ++i) b32[i] = (float)b[i];
-  if (!cg32_alloc(&s, A, v32, dinv32)) {
+  if (!cg32_alloc(&s, A, v32, dinv32, o->acc32)) {
     free(v32); free(b32); free(dinv32); free(dinv64);
     return res->status = ORC_ERR_INVALID_ARG;
   }
-  double bnorm32 = sqrt(orc_dot32(n, b32, b32));
+  double bnorm32 = sqrt(sdot(&s, b32, b32));
   int32_t status = ORC_OK;
   int warn_eps1 = 0, warn_restart = 0, broke = 0;
   int32_t n1 = 0, n2 = 0;

@@ -73,6 +73,9 @@ typedef struct {
                                  as printed), and a stage that has stagnated (recursive r
                                  1e3 times below it) ends as at its cap; 0: on the recursive r
                                  (default) */
+  int32_t acc32;        /* 1: every inner product of the single-precision stage is summed
+                           in float, sequentially (orc_dot32_f); 0: in double (default,
+                           the reading of Sec. 9, Remark 3) */
 } orc_opts;
 
 typedef struct {
@@ -99,6 +102,7 @@ void orc_spmv32(int32_t n, const int32_t* row_ptr, const int32_t* col,
                 const float* val32, const float* x, float* y);
 double orc_dot64(int32_t n, const double* a, const double* b);
 double orc_dot32(int32_t n, const float* a, const float* b);
+double orc_dot32_f(int32_t n, const float* a, const float* b);
 
 /* ---- plain CG in one precision from x0 (Sec. 3) ----
  * Runs while the stop measure exceeds eps and it < max_it.  x is in/out.
@@ -113,7 +117,7 @@ int32_t orc_cg64(const orc_csr* A, const double* b, double* x, double eps,
                  int32_t* iters, double* res_hist);
 int32_t orc_cg32(const orc_csr* A, const double* b, float* x, double eps,
                  int32_t tol_relative, int32_t max_it, int32_t precond, int32_t true_res,
-                 int32_t* iters, double* res_hist);
+                 int32_t acc32, int32_t* iters, double* res_hist);
 
 /* ---- sparsity-graph features (Sec. 6) ---- */
 int32_t orc_bfs(const orc_csr* A, int32_t src, int32_t* dist);  /* returns #reached */

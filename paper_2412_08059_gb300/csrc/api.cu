@@ -26,6 +26,7 @@ bool options_ok(const mpcg_options_t* o) {
   if (o->bfs_starts < 0) return false;
   if (o->precond != 0 && o->precond != 1) return false;
   if (o->stop_true_residual != 0 && o->stop_true_residual != 1) return false;
+  if (o->acc32 != 0 && o->acc32 != 1) return false;
   return true;
 }
 
@@ -105,6 +106,7 @@ mpcg_options_t mpcg_options_default(void) {
   o.bfs_starts = 1;
   o.precond = 0;
   o.stop_true_residual = 0;
+  o.acc32 = 0;
   return o;
 }
 

@@ -128,9 +128,9 @@ struct CShared {
 // Block partial of float-float sums, valid in thread 0 (float ops only until
 // the final conversion).
 template <int NC>
-__device__ __forceinline__ double block_ff(FF v, CShared<NC>& S) {
+__device__ __forceinline__ double block_ff(FF v, CShared<NC>& S, bool f32) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = ff_warp_sum(v);
+  v = ff_warp_sum(v, f32);
   if (lane == 0) {
     S.ffp[2 * warp] = v.hi;
     S.ffp[2 * warp + 1] = v.lo;
@@ -139,7 +139,7 @@ __device__ __forceinline__ double block_ff(FF v, CShared<NC>& S) {
   double r = 0.0;
   if (warp == 0) {
     FF t = lane < NC ? FF{S.ffp[2 * lane], S.ffp[2 * lane + 1]} : FF{0.f, 0.f};
-    t = ff_warp_sum(t);
+    t = ff_warp_sum(t, f32);
     r = (double)t.hi + (double)t.lo;
   }
   return r;
@@ -205,15 +205,21 @@ __device__ __forceinline__ bool cgrid_barrier(Ctl* ctl, int slot, unsigned long 
 template <int NC>
 __device__ __forceinline__ double cgrid_total(double block_part, double* partials, int& red,
                                               Ctl* ctl, int slot, unsigned long long& round,
-                                              CShared<NC>& S, bool& ok) {
+                                              CShared<NC>& S, bool& ok, bool f32 = false) {
   double* buf = partials + (red & 1) * kMaxGrid;
   ++red;
   if (threadIdx.x == 0) buf[blockIdx.x] = block_part;
   ok = cgrid_barrier<NC>(ctl, slot, round, &S.ok);
   double s = 0.0;
   if (threadIdx.x < 32) {
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) s += buf[i];
-    s = warp_sum(s);
+    if (f32) {  // option acc32: the blocks' float partials summed in float
+      float sf = 0.0f;
+      for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) sf = __fadd_rn(sf, (float)buf[i]);
+      s = (double)warp_sum_f(sf);
+    } else {
+      for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) s += buf[i];
+      s = warp_sum(s);
+    }
   }
   return s;
 }
@@ -516,7 +522,7 @@ __device__ __forceinline__ void warp_rows(int S0, int S1, int n, int& R0, int& R
 // two groups of four in flight.
 // x += alpha d, r -= alpha q, r^T r for four rows whose operands are loaded.
 __device__ __forceinline__ void upd32(const CgArgs& a, int i, float4 d4, float4 q4, float4 x4,
-                                      float4 r4, float alpha, FF& prr) {
+                                      float4 r4, float alpha, FF& prr, bool f32) {
   x4.x = __fmaf_rn(alpha, d4.x, x4.x);
   x4.y = __fmaf_rn(alpha, d4.y, x4.y);
   x4.z = __fmaf_rn(alpha, d4.z, x4.z);
@@ -527,10 +533,10 @@ __device__ __forceinline__ void upd32(const CgArgs& a, int i, float4 d4, float4 
   r4.w = __fmaf_rn(-alpha, q4.w, r4.w);
   *reinterpret_cast<float4*>(a.x32 + i) = x4;
   *reinterpret_cast<float4*>(a.r32 + i) = r4;
-  ff_add_prod(prr, r4.x, r4.x);
-  ff_add_prod(prr, r4.y, r4.y);
-  ff_add_prod(prr, r4.z, r4.z);
-  ff_add_prod(prr, r4.w, r4.w);
+  ff_add_prod(prr, r4.x, r4.x, f32);
+  ff_add_prod(prr, r4.y, r4.y, f32);
+  ff_add_prod(prr, r4.z, r4.z, f32);
+  ff_add_prod(prr, r4.w, r4.w, f32);
 }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -539,7 +545,7 @@ __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast
 // both groups is loaded before the first store (stores to x and r could
 // alias later loads, so the compiler would not reorder them).
 __device__ __forceinline__ void p2_32(const CgArgs& a, int R0, int R1, int lane, const float* d,
-                                      float alpha, FF& prr) {
+                                      float alpha, FF& prr, bool f32) {
   for (int base = R0 + 4 * lane; base < R1; base += 8 * kSlice) {
     const int b2 = base + 4 * kSlice;
     if (b2 + 4 <= R1) {
@@ -547,18 +553,18 @@ __device__ __forceinline__ void p2_32(const CgArgs& a, int R0, int R1, int lane,
       const float4 x4 = ld4(a.x32 + base), r4 = ld4(a.r32 + base);
       const float4 e4 = ld4(d + b2), s4 = ld4(a.q32 + b2);
       const float4 y4 = ld4(a.x32 + b2), t4 = ld4(a.r32 + b2);
-      upd32(a, base, d4, q4, x4, r4, alpha, prr);
-      upd32(a, b2, e4, s4, y4, t4, alpha, prr);
+      upd32(a, base, d4, q4, x4, r4, alpha, prr, f32);
+      upd32(a, b2, e4, s4, y4, t4, alpha, prr, f32);
     } else {
       for (int g = base; g < R1 && g <= b2; g += 4 * kSlice) {
         if (g + 4 <= R1) {
-          upd32(a, g, ld4(d + g), ld4(a.q32 + g), ld4(a.x32 + g), ld4(a.r32 + g), alpha, prr);
+          upd32(a, g, ld4(d + g), ld4(a.q32 + g), ld4(a.x32 + g), ld4(a.r32 + g), alpha, prr, f32);
         } else {
           for (int i = g; i < R1; ++i) {
             a.x32[i] = __fmaf_rn(alpha, d[i], a.x32[i]);
             const float ri = __fmaf_rn(-alpha, a.q32[i], a.r32[i]);
             a.r32[i] = ri;
-            ff_add_prod(prr, ri, ri);
+            ff_add_prod(prr, ri, ri, f32);
           }
         }
       }
@@ -569,7 +575,7 @@ __device__ __forceinline__ void p2_32(const CgArgs& a, int R0, int R1, int lane,
 // Preconditioned form: also z = dinv r (stored; the next P1 forms d from it)
 // and r^T z.  Four rows per lane, every operand loaded before the stores.
 __device__ __forceinline__ void p2_32_pc(const CgArgs& a, int R0, int R1, int lane, const float* d,
-                                         float alpha, FF& prr, FF& prz) {
+                                         float alpha, FF& prr, FF& prz, bool f32) {
   for (int base = R0 + 4 * lane; base < R1; base += 4 * kSlice) {
     if (base + 4 <= R1) {
       const float4 d4 = ld4(d + base), q4 = ld4(a.q32 + base), m4 = ld4(a.dinv32 + base);
@@ -589,14 +595,14 @@ __device__ __forceinline__ void p2_32_pc(const CgArgs& a, int R0, int R1, int la
       *reinterpret_cast<float4*>(a.x32 + base) = x4;
       *reinterpret_cast<float4*>(a.r32 + base) = r4;
       *reinterpret_cast<float4*>(a.z32 + base) = z4;
-      ff_add_prod(prr, r4.x, r4.x);
-      ff_add_prod(prr, r4.y, r4.y);
-      ff_add_prod(prr, r4.z, r4.z);
-      ff_add_prod(prr, r4.w, r4.w);
-      ff_add_prod(prz, r4.x, z4.x);
-      ff_add_prod(prz, r4.y, z4.y);
-      ff_add_prod(prz, r4.z, z4.z);
-      ff_add_prod(prz, r4.w, z4.w);
+      ff_add_prod(prr, r4.x, r4.x, f32);
+      ff_add_prod(prr, r4.y, r4.y, f32);
+      ff_add_prod(prr, r4.z, r4.z, f32);
+      ff_add_prod(prr, r4.w, r4.w, f32);
+      ff_add_prod(prz, r4.x, z4.x, f32);
+      ff_add_prod(prz, r4.y, z4.y, f32);
+      ff_add_prod(prz, r4.z, z4.z, f32);
+      ff_add_prod(prz, r4.w, z4.w, f32);
     } else {
       for (int i = base; i < R1; ++i) {
         a.x32[i] = __fmaf_rn(alpha, d[i], a.x32[i]);
@@ -604,8 +610,8 @@ __device__ __forceinline__ void p2_32_pc(const CgArgs& a, int R0, int R1, int la
         const float zi = __fmul_rn(a.dinv32[i], ri);
         a.r32[i] = ri;
         a.z32[i] = zi;
-        ff_add_prod(prr, ri, ri);
-        ff_add_prod(prz, ri, zi);
+        ff_add_prod(prr, ri, ri, f32);
+        ff_add_prod(prz, ri, zi, f32);
       }
     }
   }
@@ -655,6 +661,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
   warp_rows<NC>(S0, S1, a.n, R0, R1);
   const int n = a.n;
   const int rel = ctl->tol_relative;
+  const bool f32 = ctl->acc32 != 0;  // inner products summed in float (option acc32)
   unsigned long long round = 0;
   int red = 0;
   bool ok = true;
@@ -671,15 +678,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
       a.x32[i] = 0.0f;
       a.r32[i] = bi;
       a.da[i] = 0.0f;  // d_{-1}
-      ff_add_prod(acc, bi, bi);
+      ff_add_prod(acc, bi, bi, f32);
       if constexpr (kPc) {
         const float zi = __fmul_rn(a.dinv32[i], bi);
         a.z32[i] = zi;
-        ff_add_prod(accz, bi, zi);
+        ff_add_prod(accz, bi, zi, f32);
       }
     }
-    const double tot = cgrid_total(block_ff(acc, S), a.partials, red, ctl, a.slot, round, S, ok);
-    if constexpr (kPc) rz = cgrid_total(block_ff(accz, S), a.partials, red, ctl, a.slot, round, S, ok);
+    const double tot = cgrid_total(block_ff(acc, S, f32), a.partials, red, ctl, a.slot, round, S, ok, f32);
+    if constexpr (kPc) rz = cgrid_total(block_ff(accz, S, f32), a.partials, red, ctl, a.slot, round, S, ok, f32);
     if (lead) {
       S.rr = tot;
       S.val = sqrt(tot);  // ||b~|| = ||r0||
@@ -722,11 +729,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
       auto Rt = [&](int i, float acc) {
         if (i < n) {
           const float t = __fsub_rn(bv[i], acc);
-          ff_add_prod(pt, t, t);
+          ff_add_prod(pt, t, t, f32);
         }
       };
       if (!ring_spmv<NC, float>(a, R, C, S0, S1, Gx, Rt)) set_status(ctl, MPCG_ERR_TIMEOUT);
-      trr = cgrid_total(block_ff(pt, S), a.partials, red, ctl, a.slot, round, S, ok);
+      trr = cgrid_total(block_ff(pt, S, f32), a.partials, red, ctl, a.slot, round, S, ok, f32);
       if (!ok) break;
     }
     if (lead) {
@@ -764,13 +771,13 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
         const float di = __fmaf_rn(bt, dold[i], r[i]);
         dnew[i] = di;
         q[i] = acc;
-        ff_add_prod(pdq, di, acc);
+        ff_add_prod(pdq, di, acc, f32);
       }
     };
     const bool pass_ok = ring_spmv<NC, float>(a, R, C, S0, S1, G, Rw);
     if (!pass_ok) set_status(ctl, MPCG_ERR_TIMEOUT);
     {
-      const double dq = cgrid_total(block_ff(pdq, S), a.partials, red, ctl, a.slot, round, S, ok);
+      const double dq = cgrid_total(block_ff(pdq, S, f32), a.partials, red, ctl, a.slot, round, S, ok, f32);
       if (lead) {
         int dec = kGo;
         if (!isfinite(dq)) dec = kNan;
@@ -791,13 +798,13 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg32(CgArgs a) {
 
     // ---- P2: x += alpha d_k, r -= alpha q, r^T r (kPc: also z = dinv r, r^T z) ----
     FF prr{0.f, 0.f}, prz{0.f, 0.f};
-    if constexpr (kPc) p2_32_pc(a, R0, R1, lane, dnew, alpha, prr, prz);
-    else p2_32(a, R0, R1, lane, dnew, alpha, prr);
+    if constexpr (kPc) p2_32_pc(a, R0, R1, lane, dnew, alpha, prr, prz, f32);
+    else p2_32(a, R0, R1, lane, dnew, alpha, prr, f32);
     {
-      const double rrn = cgrid_total(block_ff(prr, S), a.partials, red, ctl, a.slot, round, S, ok);
+      const double rrn = cgrid_total(block_ff(prr, S, f32), a.partials, red, ctl, a.slot, round, S, ok, f32);
       double rzn = 0.0;
       if constexpr (kPc)
-        rzn = cgrid_total(block_ff(prz, S), a.partials, red, ctl, a.slot, round, S, ok);
+        rzn = cgrid_total(block_ff(prz, S, f32), a.partials, red, ctl, a.slot, round, S, ok, f32);
       if (lead) {
         int dec = kGo;
         if (!isfinite(rrn) || (kPc && !isfinite(rzn))) {
@@ -1378,6 +1385,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
   warp_rows<NC>(S0, S1, a.n, R0, R1);
   const int n = a.n;
   const int rel = ctl->tol_relative;
+  const bool f32 = ctl->acc32 != 0;  // inner products summed in float (option acc32)
   const int k0 = ctl->k0, max1 = ctl->max1;
   const double eps2 = ctl->eps2;
   unsigned long long round = 0;
@@ -1403,15 +1411,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
     a.x32[i] = 0.0f;
     a.r32[i] = bi;
     a.da[i] = 0.0f;
-    ff_add_prod(acc, bi, bi);
+    ff_add_prod(acc, bi, bi, f32);
   }
   double rr, bnorm;
   unsigned cmask = 0u;  // thread 0
   {
     double* buf = a.partials + (red & 1) * kMaxGrid;
-    const double bp = block_ff(acc, S);  // all consumer warps past the mask
+    const double bp = block_ff(acc, S, f32);  // all consumer warps past the mask
     if (lead0) buf[gridDim.x] = (double)s_cmask;
-    const double tot = cgrid_total(bp, a.partials, red, ctl, a.slot, round, S, ok);
+    const double tot = cgrid_total(bp, a.partials, red, ctl, a.slot, round, S, ok, f32);
     if (lead) {
       cmask = (unsigned)buf[gridDim.x];
       S.rr = tot;
@@ -1532,12 +1540,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
         const float di = __fmaf_rn(bt, dold[i], r[i]);
         dnew[i] = di;
         q[i] = accv;
-        ff_add_prod(pdq, di, accv);
+        ff_add_prod(pdq, di, accv, f32);
       }
     };
     if (!ring_spmv<NC, float>(a, R, C, S0, S1, G, Rw)) set_status(ctl, MPCG_ERR_TIMEOUT);
     {
-      const double dq = cgrid_total(block_ff(pdq, S), a.partials, red, ctl, a.slot, round, S, ok);
+      const double dq = cgrid_total(block_ff(pdq, S, f32), a.partials, red, ctl, a.slot, round, S, ok, f32);
       if (lead) {
         int d2 = kGoOn;
         if (!isfinite(dq)) {
@@ -1568,12 +1576,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
     int label_now = 0;
     if (lead0) label_now = cls >= 0 ? cls + 1 : *reinterpret_cast<volatile int*>(&ctl->eps1_ready);
     FF prr{0.f, 0.f};
-    p2_32(a, R0, R1, lane, dnew, alpha, prr);
+    p2_32(a, R0, R1, lane, dnew, alpha, prr, f32);
     {
       double* buf = a.partials + (red & 1) * kMaxGrid;
-      const double bp = block_ff(prr, S);
+      const double bp = block_ff(prr, S, f32);
       if (lead0) buf[gridDim.x] = (double)label_now;
-      const double rrn = cgrid_total(bp, a.partials, red, ctl, a.slot, round, S, ok);
+      const double rrn = cgrid_total(bp, a.partials, red, ctl, a.slot, round, S, ok, f32);
       if (lead) {
         const int label = (int)buf[gridDim.x];
         int d3 = kGoOn;

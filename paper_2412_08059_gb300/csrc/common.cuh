@@ -35,6 +35,7 @@ struct Ctl {
   // problem and options
   int n, nnz, nslices, wcap;
   int k0, max1, max2, max_restarts, tol_relative;
+  int acc32;  // single-precision inner products summed in float (option acc32)
   double eps1, eps2;
   long long timeout_ns;
   // norms
@@ -283,7 +284,13 @@ struct FF {
   float hi, lo;
 };
 
-__device__ __forceinline__ void ff_add_prod(FF& s, float a, float b) {
+// With `f32` (option acc32) the compensation is left out: the product and
+// every add round to float, in the same order and the same tree.
+__device__ __forceinline__ void ff_add_prod(FF& s, float a, float b, bool f32) {
+  if (f32) {
+    s.hi = __fadd_rn(s.hi, __fmul_rn(a, b));
+    return;
+  }
   float p = a * b;
   float e = __fmaf_rn(a, b, -p);             // a*b = p + e exactly
   float t = s.hi + p;                         // two-sum(s.hi, p)
@@ -293,7 +300,8 @@ __device__ __forceinline__ void ff_add_prod(FF& s, float a, float b) {
   s.lo += err + e;
 }
 
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
+__device__ __forceinline__ FF ff_add(FF a, FF b, bool f32) {
+  if (f32) return FF{__fadd_rn(a.hi, b.hi), 0.f};
   float t = a.hi + b.hi;
   float bp = t - a.hi;
   float err = (a.hi - (t - bp)) + (b.hi - bp);
@@ -303,14 +311,22 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   return {hi, lo};
 }
 
-__device__ __forceinline__ FF ff_warp_sum(FF v) {
+__device__ __forceinline__ FF ff_warp_sum(FF v, bool f32) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     FF w;
     w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
     w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-    v = ff_add(v, w);
+    v = ff_add(v, w, f32);
   }
+  return v;
+}
+
+// Butterfly sum of one float per lane, every add rounded to float (all lanes
+// end with the same value: a + b and b + a round alike).
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 

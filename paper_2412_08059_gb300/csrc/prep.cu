@@ -91,6 +91,7 @@ __global__ void k_init(Ctl* c, int n, int nnz, int nslices, int wcap, mpcg_optio
   c->max2 = m2 > 0x7fffffffll ? 0x7fffffff : (int)m2;
   c->max_restarts = o.max_true_restarts > 0 ? o.max_true_restarts : 0;
   c->tol_relative = o.tol_relative ? 1 : 0;
+  c->acc32 = o.acc32 ? 1 : 0;
   c->eps1 = o.eps1;
   c->eps2 = o.eps2;
   c->timeout_ns = (long long)(o.timeout_ms > 0 ? o.timeout_ms : 20000) * 1000000ll;

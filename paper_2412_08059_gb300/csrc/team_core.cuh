@@ -179,9 +179,10 @@ static __device__ bool team_sum_d(Team& t, double v, double* partials, int& red,
 }
 
 // Same for float-float partial sums (single-precision stage).
-static __device__ bool team_sum_ff(Team& t, FF v, double* partials, int& red, double& out) {
+static __device__ bool team_sum_ff(Team& t, FF v, double* partials, int& red, double& out,
+                                   bool f32) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = ff_warp_sum(v);
+  v = ff_warp_sum(v, f32);
   if (lane == 0) {
     t.S->ffp[2 * warp] = v.hi;
     t.S->ffp[2 * warp + 1] = v.lo;
@@ -191,7 +192,7 @@ static __device__ bool team_sum_ff(Team& t, FF v, double* partials, int& red, do
   ++red;
   if (threadIdx.x < 32) {
     FF s = lane < kBatchWarps ? FF{t.S->ffp[2 * lane], t.S->ffp[2 * lane + 1]} : FF{0.f, 0.f};
-    s = ff_warp_sum(s);
+    s = ff_warp_sum(s, f32);
     const double bs = (double)s.hi + (double)s.lo;
     if (threadIdx.x == 0) {
       if (t.size == 1) t.S->val[0] = bs;
@@ -202,8 +203,14 @@ static __device__ bool team_sum_ff(Team& t, FF v, double* partials, int& red, do
     if (!team_sync(t)) return false;
     if (threadIdx.x < 32) {
       double s = 0.0;
-      for (int i = lane; i < t.size; i += 32) s += buf[i];
-      s = warp_sum(s);
+      if (f32) {  // option acc32: the blocks' float partials summed in float
+        float sf = 0.0f;
+        for (int i = lane; i < t.size; i += 32) sf = __fadd_rn(sf, (float)buf[i]);
+        s = (double)warp_sum_f(sf);
+      } else {
+        for (int i = lane; i < t.size; i += 32) s += buf[i];
+        s = warp_sum(s);
+      }
       if (threadIdx.x == 0) t.S->val[0] = s;
     }
   }
@@ -240,6 +247,7 @@ static __device__ void sys_init(const Team& t, const BatchSys& s, const BatchArg
     c->max2 = m2 > 0x7fffffffll ? 0x7fffffff : (int)m2;
     c->max_restarts = o.max_true_restarts > 0 ? o.max_true_restarts : 0;
     c->tol_relative = o.tol_relative ? 1 : 0;
+    c->acc32 = o.acc32 ? 1 : 0;
     c->eps1 = o.fp64_only ? 0.0 : (a.auto_eps1 ? -1.0 : o.eps1);
     c->eps2 = s.eps2;
     c->timeout_ns = (long long)(o.timeout_ms > 0 ? o.timeout_ms : 20000) * 1000000ll;
@@ -634,6 +642,7 @@ static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, 
   const int lane = threadIdx.x & 31;
   const int gw = team_warp(t), W = team_warps(t);
   const int n = s.n, rel = ctl->tol_relative;
+  const bool f32 = ctl->acc32 != 0;  // inner products summed in float (option acc32)
   const bool lead = threadIdx.x == 0, lead0 = lead && t.rank == 0;
   if (mode == kCgContinue && ctl->broke32) {  // stage 1 already ended in the k0 phase
     if (lead0) {
@@ -657,11 +666,11 @@ static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, 
         x[i] = 0.0f;
         r[i] = bi;
         s.w.d32a[i] = 0.0f;  // d_{-1}
-        ff_add_prod(acc, bi, bi);
+        ff_add_prod(acc, bi, bi, f32);
       }
     }
     double tot;
-    if (!team_sum_ff(t, acc, s.w.partials, red, tot)) return false;
+    if (!team_sum_ff(t, acc, s.w.partials, red, tot, f32)) return false;
     rr = tot;
     if (lead) t.S->val[1] = sqrt(tot);
     __syncthreads();
@@ -718,11 +727,11 @@ static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, 
             const float di = __fmaf_rn(bt, own.x, own.y);
             dnew[i] = di;
             q[i] = acc;
-            ff_add_prod(pdq, di, acc);
+            ff_add_prod(pdq, di, acc, f32);
           }
         });
     double dq;
-    if (!team_sum_ff(t, pdq, s.w.partials, red, dq)) return false;
+    if (!team_sum_ff(t, pdq, s.w.partials, red, dq, f32)) return false;
     dec = kBGo;
     if (!isfinite(dq)) dec = kBNan;
     else if (!(dq > 0.0)) dec = kBBroke;
@@ -743,10 +752,10 @@ static __device__ bool sys_cg32(Team& t, const BatchSys& s, int mode, int& red, 
           x[i] = __fmaf_rn(alpha, v.x, v.y);
           const float ri = __fmaf_rn(-alpha, v.z, v.w);
           r[i] = ri;
-          ff_add_prod(prr, ri, ri);
+          ff_add_prod(prr, ri, ri, f32);
         });
     double rrn;
-    if (!team_sum_ff(t, prr, s.w.partials, red, rrn)) return false;
+    if (!team_sum_ff(t, prr, s.w.partials, red, rrn, f32)) return false;
     if (!isfinite(rrn)) {
       if (lead0) set_status(ctl, MPCG_ERR_NAN);
       break;

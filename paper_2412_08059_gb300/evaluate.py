@@ -87,9 +87,15 @@ def general_sample(family: str, n: int, per: int | None = None, seed: int = 0) -
 
 
 def build(desc: dict):
-    """The matrix of a descriptor (synth generators of the three families)."""
+    """The matrix of a descriptor (synth generators of the three families, and
+    the Laplacians of the condition-number study)."""
     import synth
     f = desc["family"]
+    if f == "lap2d":
+        return synth.laplacian_2d(desc["nx"], desc["ny"], sigma=desc["sigma"], cy=desc["c"])
+    if f == "lap3d":
+        return synth.laplacian_3d(desc["nx"], desc["ny"], desc["nz"], eps=desc["c"],
+                                  sigma=desc["sigma"])
     if f == "xstar":
         return synth.extended_star(desc["lc"], desc["nc"], desc["mu"], extra=None, seed=desc["seed"])
     if f == "random":
@@ -104,10 +110,13 @@ def _batch_results(dmats, dbs, xs, ws, res, opts, sample):
 
 
 def sweep_records(descs: list[dict], device="cuda", eps2: float = 1e-10, k0: int = 10,
-                  team_rows: int = 0) -> dict:
+                  team_rows: int = 0, acc32: int = 0, tol_relative: int = 1) -> dict:
     """Step 2 for every descriptor, as batched solves on the GPU: one batch of
     Algorithm II for the features, one of Algorithm I per candidate eps1 and
-    one pure-FP64 batch.  b = A x* with x* ~ U[-1, 1] (seeded per matrix)."""
+    one pure-FP64 batch.  b = A x* with x* ~ U[-1, 1] (seeded per matrix).
+    acc32 = 1 sums the single-precision stage's inner products in float, and
+    tol_relative = 0 stops on ||r|| <= eps as Sec. 3 prints it (the options of
+    the same names)."""
     import synth
     t0 = time.time()
     mats = [build(d) for d in descs]
@@ -122,8 +131,9 @@ def sweep_records(descs: list[dict], device="cuda", eps2: float = 1e-10, k0: int
     t1 = time.time()
     # features (any sample: the label of this run is not used)
     dummy = mpcg.DeviceSample(np.ones((1, 4)), np.array([2], np.int8), device=device)
-    rf = _batch_results(dmats, dbs, xs, ws, res, mpcg.options(k0=k0, eps2=eps2, team_rows=team_rows),
-                        dummy)
+    rf = _batch_results(dmats, dbs, xs, ws, res,
+                        mpcg.options(k0=k0, eps2=eps2, team_rows=team_rows, acc32=acc32,
+                                     tol_relative=tol_relative), dummy)
     feat = np.array([[A.n, A.nnz, r["pdiam"], r["v"]] for A, r in zip(mats, rf)], dtype=np.float64)
     n1 = np.zeros((N, len(CLASSES)), np.int64)
     n2 = np.zeros((N, len(CLASSES)), np.int64)
@@ -132,12 +142,14 @@ def sweep_records(descs: list[dict], device="cuda", eps2: float = 1e-10, k0: int
     for j, t in enumerate(CLASSES):
         rr = _batch_results(dmats, dbs, xs, ws, res,
                             mpcg.options(eps1=float(f"1e-{t}"), eps2=eps2, k0=k0,
-                                         team_rows=team_rows), None)
+                                         team_rows=team_rows, acc32=acc32,
+                                         tol_relative=tol_relative), None)
         for i, r in enumerate(rr):
             n1[i, j], n2[i, j], st[i, j] = r["n1"], r["n2"], r["status"]
             ms32[i] += (r["t_fp32_ns"] - r["t_features_ns"]) / 1e6
     rd = _batch_results(dmats, dbs, xs, ws, res,
-                        mpcg.options(fp64_only=1, eps2=eps2, team_rows=team_rows), None)
+                        mpcg.options(fp64_only=1, eps2=eps2, team_rows=team_rows,
+                                     tol_relative=tol_relative), None)
     ndp = np.array([r["n2"] for r in rd], np.int64)
     st_dp = np.array([r["status"] for r in rd], np.int64)
     # t_sp from the single-precision stages of the Algorithm I runs; t_dp from
@@ -213,16 +225,18 @@ def protocol(rec: dict, classify, n: int, ks=(1, 5, 10, 15, 20), splits: int = 1
 
 
 def run(families=("xstar", "random", "banded"), scale: float = 1.0, splits: int = 100,
-        ks=(1, 5, 10, 15, 20), device="cuda", seed: int = 0, log=None) -> dict:
+        ks=(1, 5, 10, 15, 20), device="cuda", seed: int = 0, log=None, acc32: int = 0,
+        tol_relative: int = 1) -> dict:
     """The whole protocol: every family and size, `scale` times the paper's
-    matrices per parameter set (at least one)."""
+    matrices per parameter set (at least one); acc32 and tol_relative as in
+    sweep_records."""
     classify = gpu_classifier(device)
     out = {}
     for fam in families:
         for n in FAMILY_SIZES[fam]:
             per = max(1, int(round(PAPER_PER[fam] * scale)))
             descs = general_sample(fam, n, per, seed=seed + n)
-            rec = sweep_records(descs, device)
+            rec = sweep_records(descs, device, acc32=acc32, tol_relative=tol_relative)
             t = time.time()
             r = protocol(rec, classify, n, ks, splits, seed)
             r["seconds_generate"] = round(rec["seconds_generate"], 1)
@@ -237,3 +251,155 @@ def run(families=("xstar", "random", "banded"), scale: float = 1.0, splits: int 
             del rec
             torch.cuda.empty_cache()
     return out
+
+
+# Efficiency against the pseudo-diameter by condition-number class (Sec. 7,
+# Tables 1-3) on Laplacians whose condition number has a closed form.
+# ------------------------------------------------------------------------------
+
+# The four classes of Sec. 7: kappa <= 10, 10 < kappa <= 100, 100 < kappa <= 1000,
+# kappa > 1000 (upper bounds, inclusive).
+KAPPA_BOUNDS = (10.0, 100.0, 1000.0)
+KAPPA_NAMES = ("kappa<=10", "10<kappa<=100", "100<kappa<=1000", "kappa>1000")
+
+
+def _tridiag_extremes(m: int) -> tuple[float, float]:
+    """Smallest and largest eigenvalue of tridiag(-1, 2, -1) of order m:
+    4 sin^2(k pi / (2 (m + 1))) for k = 1 and k = m."""
+    return (4.0 * math.sin(math.pi / (2 * (m + 1))) ** 2,
+            4.0 * math.sin(m * math.pi / (2 * (m + 1))) ** 2)
+
+
+def kappa_closed_form(desc: dict) -> float:
+    """Spectral condition number of a Laplacian descriptor.  The matrices are
+    Kronecker sums of tridiag(-1, 2, -1) (weights 1, c) plus sigma I, so the
+    extreme eigenvalues are sums of the factors' extreme eigenvalues."""
+    if desc["family"] == "lap2d":
+        dims, w = (desc["nx"], desc["ny"]), (1.0, desc["c"])
+    elif desc["family"] == "lap3d":
+        dims, w = (desc["nx"], desc["ny"], desc["nz"]), (1.0, 1.0, desc["c"])
+    else:
+        raise KeyError(desc["family"])
+    lo = desc["sigma"] + sum(wk * _tridiag_extremes(m)[0] for m, wk in zip(dims, w))
+    hi = desc["sigma"] + sum(wk * _tridiag_extremes(m)[1] for m, wk in zip(dims, w))
+    return hi / lo
+
+
+def grid_diameter(desc: dict) -> int:
+    """Graph diameter of the grid: the sum over the axes of (points - 1)."""
+    dims = [desc["nx"], desc["ny"]] + ([desc["nz"]] if desc["family"] == "lap3d" else [])
+    return int(sum(m - 1 for m in dims))
+
+
+def laplacian_sample(count: int, seed: int = 0, n_lo: float = 1e3, n_hi: float = 2.6e5) -> list[dict]:
+    """Seeded 2-D (70 %) and 3-D 5/7-point Dirichlet Laplacians, n log-uniform
+    in [n_lo, n_hi] before the grid sides are rounded.  The shape sets the diameter and, through its shortest
+    side, the smallest eigenvalue, so the two vary apart: 2-D aspect ratios
+    log-uniform in [1, 256], 3-D grids with the z side 1 to 64 times shorter.
+    Coupling c (y in 2-D, z in 3-D) is 1, or 1e-2 in a quarter of the
+    matrices; the shift sigma is 0 in a quarter, else log-uniform in
+    [1e-5, 3], which moves kappa across the four classes."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(count):
+        n = math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))
+        c = 1.0 if rng.random() < 0.75 else 1e-2
+        sigma = 0.0 if rng.random() < 0.25 else float(10.0 ** rng.uniform(-5.0, math.log10(3.0)))
+        if rng.random() < 0.7:
+            a = math.exp(rng.uniform(0.0, math.log(256.0)))
+            nx = max(2, int(round(math.sqrt(n * a))))
+            ny = max(2, int(round(n / nx)))
+            d = {"family": "lap2d", "nx": nx, "ny": ny}
+        else:
+            a = math.exp(rng.uniform(0.0, math.log(64.0)))
+            nx = max(2, int(round((n * a) ** (1.0 / 3.0))))
+            nz = max(2, int(round(n / (nx * nx))))
+            d = {"family": "lap3d", "nx": nx, "ny": nx, "nz": nz}
+        d.update(c=c, sigma=sigma, seed=seed * 1_000_003 + j)
+        out.append(d)
+    return out
+
+
+def kappa_class(kappa: np.ndarray) -> np.ndarray:
+    """Index 0..3 of the Sec. 7 class of each condition number."""
+    return np.searchsorted(np.asarray(KAPPA_BOUNDS), np.asarray(kappa, float), side="left")
+
+
+def optimal_efficiency(n1: np.ndarray, n2: np.ndarray, ndp: np.ndarray, omega) -> np.ndarray:
+    """E(A) of Eq. (12) at the optimal eps1: Eq. (4) minimised over the
+    candidates (ties to the smallest t), per matrix (rows of n1, n2)."""
+    w = np.broadcast_to(np.asarray(omega, float).reshape(-1, 1) if np.ndim(omega) else omega,
+                        n1.shape)
+    cost = w * n1 + n2
+    best = cost[np.arange(cost.shape[0]), np.argmin(cost, axis=1)]
+    return (1.0 - best / ndp) * 100.0
+
+
+def kappa_table(kappa, pdiam, E) -> list[dict]:
+    """One row per condition-number class, as in Tables 1-3: the mean E, the
+    mean pseudo-diameter and the count; then the mean pseudo-diameter and
+    count of the matrices below the class's mean E, and of those at or above
+    it (the two groups partition the class).  Empty classes give None."""
+    kappa, pdiam, E = (np.asarray(v, float) for v in (kappa, pdiam, E))
+    cls = kappa_class(kappa)
+    rows = []
+    for c, name in enumerate(KAPPA_NAMES):
+        sel = cls == c
+        N = int(sel.sum())
+        if N == 0:
+            rows.append({"kappa": name, "N": 0, "ME": None, "Ml": None, "worse": None,
+                         "better": None})
+            continue
+        e, l = E[sel], pdiam[sel]
+        me = float(e.mean())
+        lo, hi = e < me, e >= me
+        grp = lambda m: {"Ml": float(l[m].mean()) if m.any() else None, "N": int(m.sum())}
+        rows.append({"kappa": name, "N": N, "ME": me, "Ml": float(l.mean()),
+                     "worse": grp(lo), "better": grp(hi)})
+    return rows
+
+
+def kappa_study(count: int = 2400, seed: int = 0, device="cuda", chunk: int = 600,
+                eps2: float = 1e-10, log=None) -> dict:
+    """The Tables 1-3 analogue on laplacian_sample(count): GPU sweeps (chunks
+    of `chunk` systems per batch), then kappa_table for omega = 1/3 and the
+    matrix's measured omega.  Systems with a failed solve are left out and
+    counted; the GPU pseudo-diameter is checked against the grid diameter."""
+    descs = laplacian_sample(count, seed)
+    kap, pd, n1, n2, ndp, om = [], [], [], [], [], []
+    failed = pd_mismatch = 0
+    t0 = time.time()
+    for s in range(0, count, chunk):
+        part = descs[s:s + chunk]
+        rec = sweep_records(part, device, eps2=eps2)
+        ok = (rec["status"] >= 0).all(axis=1) & (rec["status_dp"] >= 0)
+        failed += int((~ok).sum())
+        for i, d in enumerate(part):
+            if not ok[i]:
+                continue
+            kap.append(kappa_closed_form(d))
+            pd.append(float(rec["feat"][i, 2]))
+            pd_mismatch += int(rec["feat"][i, 2] != grid_diameter(d))
+            n1.append(rec["n1"][i])
+            n2.append(rec["n2"][i])
+            ndp.append(rec["n_dp"][i])
+            om.append(rec["omega"][i])
+        if log:
+            log(f"kappa study: {min(s + chunk, count)}/{count} systems, {time.time() - t0:.0f} s")
+        del rec
+        torch.cuda.empty_cache()
+    kap, pd, om = np.array(kap), np.array(pd), np.array(om)
+    n1, n2, ndp = np.array(n1), np.array(n2), np.array(ndp, float)
+    E13 = optimal_efficiency(n1, n2, ndp, 1.0 / 3.0)
+    Em = optimal_efficiency(n1, n2, ndp, om)
+    cls = kappa_class(kap)
+    corr = {}
+    for c, name in enumerate(KAPPA_NAMES):
+        sel = cls == c
+        if sel.sum() >= 3 and np.std(pd[sel]) > 0 and np.std(E13[sel]) > 0:
+            corr[name] = float(np.corrcoef(np.log(pd[sel]), E13[sel])[0, 1])
+    return {"systems": count, "used": int(kap.size), "failed": failed,
+            "pdiam_not_grid_diameter": pd_mismatch, "omega_measured_mean": float(om.mean()),
+            "table_omega_1_3": kappa_table(kap, pd, E13),
+            "table_omega_measured": kappa_table(kap, pd, Em),
+            "corr_E_log_pdiam_omega_1_3": corr, "seconds": round(time.time() - t0, 1)}

@@ -58,7 +58,7 @@ class Options(C.Structure):
                 ("stage1_only", C.c_int32), ("team_rows", C.c_int32),
                 ("serve_split", C.c_int32), ("bfs_starts", C.c_int32),
                 ("precond", C.c_int32), ("stop_true_residual", C.c_int32),
-                ("cancel", C.c_void_p)]
+                ("cancel", C.c_void_p), ("acc32", C.c_int32)]
 
 
 class Result(C.Structure):

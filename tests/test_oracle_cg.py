@@ -498,3 +498,98 @@ def test_true_residual_restart_with_none_allowed_at_5e16():
     x, r = oracle.solve(A, b, eps1=1e-4, eps2=5e-16, max_true_restarts=0)
     assert r["status"] == oracle.ERR_NOT_CONVERGED and r["restarts"] == 0
     assert r["true_rel_resid"] > 5e-16
+
+
+# ---- the other reading of Sec. 9, Remark 3: single-precision sums (option acc32) ----
+
+def test_float_sum_dot_exact_cases():
+    """Cases whose float result follows from the rounding rule alone:
+    1e8 + 1 rounds back to 1e8 (ulp 8), and 2^24 + 1 ties to the even 2^24."""
+    one = np.ones(3, np.float32)
+    a = np.float32([1e8, 1.0, -1e8])
+    assert oracle.dot32(a, one, acc32=1) == 0.0
+    assert oracle.dot32(a, one) == 1.0
+    b = np.float32([2.0 ** 24, 1.0, 1.0])
+    assert oracle.dot32(b, one, acc32=1) == 2.0 ** 24
+    assert oracle.dot32(b, one) == 2.0 ** 24 + 2.0
+    # the products round to float too: (1 + 2^-12)^2 = 1 + 2^-11 + 2^-24 -> 1 + 2^-11
+    c = np.float32([1.0 + 2.0 ** -12])
+    assert oracle.dot32(c, c, acc32=1) == 1.0 + 2.0 ** -11
+    assert oracle.dot32(c, c) == (1.0 + 2.0 ** -12) ** 2
+
+
+def test_float_sum_dot_is_the_sequential_float_sum():
+    """numpy's accumulate is a sequential float32 running sum; the error of the
+    float sum stays inside gamma_n sum |a_i b_i| and is far above the double
+    sum's."""
+    rng = np.random.default_rng(5)
+    a = rng.uniform(-1, 1, 20000).astype(np.float32)
+    b = rng.uniform(-1, 1, 20000).astype(np.float32)
+    want = np.add.accumulate((a * b).astype(np.float32), dtype=np.float32)[-1]
+    assert oracle.dot32(a, b, acc32=1) == float(want)
+    exact = math.fsum(float(x) * float(y) for x, y in zip(a, b))
+    u, n = 2.0 ** -24, a.size
+    bound = n * u / (1 - n * u) * float(np.sum(np.abs(a.astype(np.float64) * b)))
+    err32 = abs(oracle.dot32(a, b, acc32=1) - exact)
+    assert 0 < err32 <= bound
+    assert abs(oracle.dot32(a, b) - exact) < 1e-3 * err32
+
+
+def test_float_sum_cg32_keeps_the_cg_invariants():
+    """With float sums the FP32 CG still exhausts a 3-eigenvalue Krylov space
+    in 3 steps (to the float rounding floor), solves a small SPD system like a
+    dense solve to float accuracy, and its first stop measure is the float
+    ||b~|| relative to itself."""
+    A = star_laplacian(400, 1.0)
+    b = np.random.default_rng(1).uniform(-1, 1, 400)
+    _, it, st, h = oracle.cg32(A, b, 0.0, max_it=3, history=True, acc32=1)
+    assert h.size == 4 and h[2] > 1e-3 and h[3] < 1e-4
+    A2, M = random_spd(24, 50.0, 3)
+    b2 = np.random.default_rng(4).uniform(-1, 1, 24)
+    x, it, st = oracle.cg32(A2, b2, 1e-6, acc32=1)
+    assert st == oracle.OK
+    xs = scipy.linalg.solve(M, b2, assume_a="pos")
+    assert np.linalg.norm(x - xs) <= 1e-4 * np.linalg.norm(xs)
+
+
+def test_float_sum_reading_changes_stage_one_and_both_reach_eps2():
+    """Algorithm I with either reading meets eps2; the float sums change the
+    single-precision iteration count of a 128x128 Laplacian at eps1 = 1e-6 by
+    a few iterations at most, and the FP64 stage is the same computation."""
+    A = synth.laplacian_2d(128, 128)
+    _, b = synth.rhs(A, 3)
+    _, r0 = oracle.solve(A, b, eps1=1e-6)
+    _, r1 = oracle.solve(A, b, eps1=1e-6, acc32=1)
+    assert r0["status"] == r1["status"] == oracle.OK
+    assert r0["true_rel_resid"] <= 1e-10 and r1["true_rel_resid"] <= 1e-10
+    assert abs(r0["n1"] - r1["n1"]) <= max(3, 0.05 * r0["n1"])
+    x32, it32, _ = oracle.cg32(A, b, 1e-6, acc32=1)
+    assert it32 == r1["n1"]
+
+
+def absorbing_diagonal(m=4000):
+    """diag(2, 1, ..., 1) with b = (2^12, 2^-13, ..., 2^-13).  Every float sum
+    of b^T b (and of b^T A b) equals its large term, in any order: the small
+    terms add up to m 2^-26 < 1, below half an ulp of 2^24.  The double sums
+    keep them exactly.  One CG step from 0 has alpha = 1/2 in float under both
+    readings and leaves r_1 = (0, 2^-14, ...), whose r^T r = m 2^-28 is exact
+    in any order; so v of Eq. (13) with k0 = 1 has a closed form per reading."""
+    n = m + 1
+    A = synth.from_edges(n, np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0),
+                         np.concatenate([[2.0], np.ones(m)]), "absorbing_diag")
+    b = np.concatenate([[2.0 ** 12], np.full(m, 2.0 ** -13)])
+    rr1 = m * 2.0 ** -28
+    v_double = math.sqrt(rr1) / math.sqrt(2.0 ** 24 + m * 2.0 ** -26)
+    v_float = math.sqrt(rr1) / math.sqrt(2.0 ** 24)
+    return A, b, v_double, v_float
+
+
+def test_float_sum_reading_on_the_absorbing_diagonal():
+    # (the oracle's per-component 2BFS is quadratic on n isolated vertices: keep m small)
+    A, b, v_double, v_float = absorbing_diagonal()
+    assert v_double != v_float
+    feat0, k0d, st0 = oracle.features(A, b, k0=1)
+    feat1, k0d1, st1 = oracle.features(A, b, k0=1, acc32=1)
+    assert st0 == st1 == oracle.OK and k0d == k0d1 == 1
+    assert feat0[3] == v_double
+    assert feat1[3] == v_float
