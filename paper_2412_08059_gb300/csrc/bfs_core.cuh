@@ -49,6 +49,7 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 struct GridSync {
   static constexpr bool kWholeBlock = true;  // every thread of every block is in the group
   static constexpr bool kNarrow = true;      // narrow levels run by one warp
+  static constexpr bool kHelpers = false;    // no other warps join the levels
   Ctl* ctl;
   int slot;
   unsigned long long round;
@@ -59,6 +60,7 @@ struct GridSync {
 struct WarpGroupSync {
   static constexpr bool kWholeBlock = false;  // one warp of every block is in the group
   static constexpr bool kNarrow = true;       // narrow levels run by one warp
+  static constexpr bool kHelpers = false;     // no other warps join the levels
   Ctl* ctl;
   int slot;
   unsigned long long round;
@@ -92,6 +94,202 @@ struct WarpGroupSync {
     return ok != 0;
   }
 };
+
+// ---- helper warps ----
+// Warps of a block that have nothing else to do (the consumers of the fused
+// single-precision stage once their iterations wait for the label) can join
+// the levels of the one-warp-per-block group.  The group's warp stays the only
+// member of the grid barrier.  Per wide level it publishes the level in
+// shared memory, meets the helpers at a block barrier, every warp of the
+// block takes its share of the block's items, and a second block barrier
+// closes the level before the grid barrier.  Which items a block owns does not
+// change, so blocks with and without helpers mix freely.  The helpers' only
+// unbounded waits are these block barriers, and the group's warp reaches them
+// through bounded waits only: its release (help_release) ends every search.
+struct HelpLevel {
+  const int32_t* inA;
+  const int32_t* inB;
+  int32_t* outA;
+  int32_t* outB;
+  int32_t* dA;
+  int32_t* dB;
+  int* cntA;
+  int* cntB;
+  int sa, sb, level, cmd;  // cmd: 0 = run the level, 1 = leave
+};
+
+enum { kHelpNone = 0, kHelpJoined = 1, kHelpClosed = 2 };
+constexpr int kHelpBarStart = 2;  // block barrier ids (1 is the consumers' own)
+constexpr int kHelpBarEnd = 3;
+
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+struct WarpGroupHelped : WarpGroupSync {
+  static constexpr bool kHelpers = true;
+  volatile int* hstate;  // kHelpNone / kHelpJoined (set by the helpers) / kHelpClosed
+  HelpLevel* hl;
+  int nhelp;             // helper warps of the block
+};
+
+// One level of the dual search over the items [0, sa + sb) of the two
+// frontiers (A's first): the warp whose chunk base is `wbase` takes the item
+// pairs first_pair, first_pair + pair_step, ... of its chunk sequence (two
+// items per lane, T apart, so that their loads and claims are in flight
+// together).  A single search is the case sb = 0.
+__device__ __forceinline__ void dual_level_items(const BfsGraph& g, const int32_t* inA,
+                                                 const int32_t* inB, int32_t* outA, int32_t* outB,
+                                                 int32_t* dA, int32_t* dB, int* cntA, int* cntB,
+                                                 int sa, int sb, int level, int wbase, int T,
+                                                 int first_pair, int pair_step) {
+  const int lane = threadIdx.x & 31;
+  const int total = sa + sb;
+  for (int base = wbase + first_pair * 2 * T; base < total; base += pair_step * 2 * T) {
+    int u[2], e0[2], deg[2];
+    bool isB[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int idx = base + h * T + lane;
+      isB[h] = idx >= sa;
+      u[h] = -1;
+      if (idx < total) u[h] = isB[h] ? inB[idx - sa] : inA[idx];
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      e0[h] = 0;
+      deg[h] = 0;
+      if (u[h] >= 0) {
+        e0[h] = g.rp[u[h]];
+        deg[h] = g.rp[u[h] + 1] - e0[h];
+      }
+    }
+    const int maxdeg = __reduce_max_sync(0xffffffffu, max(deg[0], deg[1]));
+    for (int k0 = 0; k0 < maxdeg; k0 += 8) {
+      int w[2][8];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[h][j] = (k0 + j < deg[h]) ? g.col[e0[h] + k0 + j] : -1;
+      bool push[2][8];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int32_t* dist = isB[h] ? dB : dA;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          push[h][j] =
+              w[h][j] >= 0 && w[h][j] != u[h] && atomicCAS(&dist[w[h][j]], -1, level + 1) == -1;
+      }
+      int mA = 0, mB = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int mine = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mine += push[h][j] ? 1 : 0;
+        if (isB[h]) mB += mine;
+        else mA += mine;
+      }
+      // separate warp scans for the pushes into A's and into B's queue
+      int incA = mA, incB = mB;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int ta = __shfl_up_sync(0xffffffffu, incA, o);
+        const int tb = __shfl_up_sync(0xffffffffu, incB, o);
+        if (lane >= o) {
+          incA += ta;
+          incB += tb;
+        }
+      }
+      const int totA = __shfl_sync(0xffffffffu, incA, 31);
+      const int totB = __shfl_sync(0xffffffffu, incB, 31);
+      int bA = 0, bB = 0;
+      if (lane == 0) {
+        if (totA > 0) bA = atomicAdd(cntA, totA);
+        if (totB > 0) bB = atomicAdd(cntB, totB);
+      }
+      bA = __shfl_sync(0xffffffffu, bA, 0);
+      bB = __shfl_sync(0xffffffffu, bB, 0);
+      int posA = bA + incA - mA, posB = bB + incB - mB;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (push[h][j]) {
+            if (isB[h]) outB[posB++] = w[h][j];
+            else outA[posA++] = w[h][j];
+          }
+        }
+      }
+    }
+  }
+}
+
+// The group's warp at the start of a wide level: when helpers have joined,
+// publish the level and meet them.  Returns the warps of the block on it.
+template <class Sync>
+__device__ __forceinline__ int help_begin(Sync& s, const HelpLevel& L) {
+  if constexpr (Sync::kHelpers) {
+    int st = 0;
+    if ((threadIdx.x & 31) == 0) st = *s.hstate;
+    st = __shfl_sync(0xffffffffu, st, 0);
+    if (st != kHelpJoined) return 1;
+    if ((threadIdx.x & 31) == 0) {
+      *s.hl = L;
+      __threadfence();  // the other blocks' queue entries, acquired at the grid barrier
+    }
+    __syncwarp();
+    named_bar(kHelpBarStart, (s.nhelp + 1) * 32);
+    return s.nhelp + 1;
+  } else {
+    return 1;
+  }
+}
+
+// The group's warp at the end of a level run with helpers: wait for their
+// claims and pushes before the grid barrier publishes them.
+template <class Sync>
+__device__ __forceinline__ void help_end(Sync& s, int warps) {
+  if constexpr (Sync::kHelpers) {
+    if (warps > 1) {
+      named_bar(kHelpBarEnd, (s.nhelp + 1) * 32);
+      if ((threadIdx.x & 31) == 0) __threadfence();
+      __syncwarp();
+    }
+  }
+}
+
+// The group's warp once its searches are over (on every path): no helper
+// joins any more, and helpers that have joined are sent away.
+template <class Sync>
+__device__ void help_release(Sync& s) {
+  if constexpr (Sync::kHelpers) {
+    int old = 0;
+    if ((threadIdx.x & 31) == 0) old = atomicCAS(const_cast<int*>(s.hstate), kHelpNone, kHelpClosed);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old == kHelpJoined) {
+      if ((threadIdx.x & 31) == 0) {
+        s.hl->cmd = 1;
+        *s.hstate = kHelpClosed;
+      }
+      __syncwarp();
+      named_bar(kHelpBarStart, (s.nhelp + 1) * 32);
+    }
+  }
+}
+
+// A helper warp (warp index gw >= 1 among the block's nhelp + 1) in the
+// levels of the block's group until the release.
+static __device__ __noinline__ void bfs_help(const BfsGraph g, const HelpLevel* hl, int nhelp, int gw) {
+  const int wbase = blockIdx.x * 32, T = gridDim.x * 32;
+  for (;;) {
+    named_bar(kHelpBarStart, (nhelp + 1) * 32);
+    const volatile HelpLevel* v = hl;
+    if (v->cmd) break;
+    dual_level_items(g, v->inA, v->inB, v->outA, v->outB, v->dA, v->dB, v->cntA, v->cntB, v->sa,
+                     v->sb, v->level, wbase, T, gw, nhelp + 1);
+    named_bar(kHelpBarEnd, (nhelp + 1) * 32);
+  }
+}
 
 // One BFS over the group.  Writes dist (all n entries), and by role: the
 // farthest-vertex key and the reached count (first), per-component keys
@@ -144,6 +342,13 @@ __device__ bool bfs_run(const BfsGraph& g, int32_t* dist, int sources, int src, 
     reached += size;
     if (tid == 0) ctl->qsize[(level + 2) % 3] = 0;
     int* cnt = &ctl->qsize[(level + 1) % 3];
+    if constexpr (Sync::kHelpers) {  // the dual level body with an empty second search
+      const HelpLevel L{in, in, out, out, dist, dist, cnt, cnt, size, 0, level, 0};
+      const int warps = help_begin(sync, L);
+      dual_level_items(g, in, in, out, out, dist, dist, cnt, cnt, size, 0, level, wbase, T, 0,
+                       warps);
+      help_end(sync, warps);
+    } else {
     for (int base = wbase; base < size; base += T) {
       const int idx = base + lane;
       int u = -1, e0 = 0, deg = 0;
@@ -180,6 +385,7 @@ __device__ bool bfs_run(const BfsGraph& g, int32_t* dist, int sources, int src, 
             if (push[j]) out[pos++] = w[j];
         }
       }
+    }
     }
     ++level;
     if (!sync()) return false;
@@ -535,85 +741,14 @@ __device__ bool bfs_dual(const BfsGraph& g, int32_t* dA, int32_t* dB, int srcA, 
     int32_t* outB = (level & 1) ? g.fq2 : g.fq3;
     int* cntA = &ctl->qsize[(level + 1) % 3];
     int* cntB = &ctl->qsizeB[(level + 1) % 3];
-    const int total = sa + sb;
-    // Each lane takes two frontier vertices per round (items base + lane and
-    // base + T + lane), so that their loads and claims are in flight together.
-    for (int base = wbase; base < total; base += 2 * T) {  // warp-uniform bound
-      int u[2], e0[2], deg[2];
-      bool isB[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int idx = base + h * T + lane;
-        isB[h] = idx >= sa;
-        u[h] = -1;
-        if (idx < total) u[h] = isB[h] ? inB[idx - sa] : inA[idx];
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        e0[h] = 0;
-        deg[h] = 0;
-        if (u[h] >= 0) {
-          e0[h] = g.rp[u[h]];
-          deg[h] = g.rp[u[h] + 1] - e0[h];
-        }
-      }
-      const int maxdeg = __reduce_max_sync(0xffffffffu, max(deg[0], deg[1]));
-      for (int k0 = 0; k0 < maxdeg; k0 += 8) {
-        int w[2][8];
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) w[h][j] = (k0 + j < deg[h]) ? g.col[e0[h] + k0 + j] : -1;
-        bool push[2][8];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          int32_t* dist = isB[h] ? dB : dA;
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            push[h][j] =
-                w[h][j] >= 0 && w[h][j] != u[h] && atomicCAS(&dist[w[h][j]], -1, level + 1) == -1;
-        }
-        int mA = 0, mB = 0;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          int mine = 0;
-#pragma unroll
-          for (int j = 0; j < 8; ++j) mine += push[h][j] ? 1 : 0;
-          if (isB[h]) mB += mine;
-          else mA += mine;
-        }
-        // separate warp scans for the pushes into A's and into B's queue
-        int incA = mA, incB = mB;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int ta = __shfl_up_sync(0xffffffffu, incA, o);
-          const int tb = __shfl_up_sync(0xffffffffu, incB, o);
-          if (lane >= o) {
-            incA += ta;
-            incB += tb;
-          }
-        }
-        const int totA = __shfl_sync(0xffffffffu, incA, 31);
-        const int totB = __shfl_sync(0xffffffffu, incB, 31);
-        int bA = 0, bB = 0;
-        if (lane == 0) {
-          if (totA > 0) bA = atomicAdd(cntA, totA);
-          if (totB > 0) bB = atomicAdd(cntB, totB);
-        }
-        bA = __shfl_sync(0xffffffffu, bA, 0);
-        bB = __shfl_sync(0xffffffffu, bB, 0);
-        int posA = bA + incA - mA, posB = bB + incB - mB;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            if (push[h][j]) {
-              if (isB[h]) outB[posB++] = w[h][j];
-              else outA[posA++] = w[h][j];
-            }
-          }
-        }
-      }
+    if constexpr (Sync::kHelpers) {
+      const HelpLevel L{inA, inB, outA, outB, dA, dB, cntA, cntB, sa, sb, level, 0};
+      const int warps = help_begin(sync, L);
+      dual_level_items(g, inA, inB, outA, outB, dA, dB, cntA, cntB, sa, sb, level, wbase, T, 0,
+                       warps);
+      help_end(sync, warps);
+    } else {
+      dual_level_items(g, inA, inB, outA, outB, dA, dB, cntA, cntB, sa, sb, level, wbase, T, 0, 1);
     }
     ++level;
     if (!sync()) return false;

@@ -1301,6 +1301,18 @@ __device__ __forceinline__ int wait_label(Ctl* ctl) {
   }
 }
 
+// The feature warp's 2BFS (out of line: its registers are its own).  The
+// block's consumers join its levels once stage 1 waits for nothing but the
+// label (help_begin); the release ends their part on every path.
+__device__ __noinline__ bool stage1_pdiam(const BfsGraph g, int32_t* d1, int32_t* d2, Ctl* ctl,
+                                          int slot, int* hstate, HelpLevel* hl, int nhelp) {
+  WarpGroupHelped sync{{ctl, slot, 0ull}, hstate, hl, nhelp};
+  const bool ok = pseudo_diameter_run(g, d1, d2, blockIdx.x * 32 + (threadIdx.x & 31),
+                                      gridDim.x * 32, sync);
+  help_release(sync);
+  return ok;
+}
+
 __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
   constexpr int NC = kNC1;
   extern __shared__ __align__(128) char smem[];
@@ -1308,12 +1320,16 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
   __shared__ volatile int s_k0_ready;
   __shared__ double s_v;
   __shared__ unsigned s_cmask;
+  __shared__ int s_help;       // the consumers' part in the 2BFS (kHelpNone / Joined / Closed)
+  __shared__ HelpLevel s_hl;   // the level the feature warp publishes to them
   const CgArgs& a = sa.a;
   Ctl* ctl = a.ctl;
   if (volatile_status(ctl) != 0 || ctl->trivial) return;
   if (threadIdx.x == 0) {
     s_k0_ready = 0;
     s_cmask = 0u;
+    s_help = kHelpNone;
+    s_hl.cmd = 0;
   }
   Ring<float> R;
   int S0, S1;
@@ -1325,9 +1341,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
   }
   if (warp == NC) {
     // ---- feature warp: 2BFS over the grid's feature warps ----
-    WarpGroupSync sync{ctl, sa.bfs_slot, 0ull};
-    const bool ok = pseudo_diameter_run(sa.g, sa.d1, sa.d2, blockIdx.x * 32 + lane,
-                                        gridDim.x * 32, sync);
+    const bool ok = stage1_pdiam(sa.g, sa.d1, sa.d2, ctl, sa.bfs_slot, &s_help, &s_hl, NC);
     if (blockIdx.x != 0) return;
     // ---- block 0: wait for v from this block's consumers, then the kNN ----
     int have_v = 0;
@@ -1445,7 +1459,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
     nt[t] = -1;
     res_at[t] = 0.0;
   }
-  enum { kGoOn = 0, kEnd = 1, kFailed = 2, kBrokeDown = 3 };
+  enum { kGoOn = 0, kEnd = 1, kFailed = 2, kBrokeDown = 3, kEndForLabel = 4 };
   int broke = 0;
   // thread 0: stop thresholds of eps2 (slot 16) and of every candidate
   // eps1 = 10^-t (slots 0..15), kept in shared memory
@@ -1459,6 +1473,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
   }
 
   int cw = 0;  // the cancel word as block 0's thread 0 read it during the last pass
+  bool help = false;  // stage 1 is over and waits for the label only
   while (ok) {
     if (lead) {
       int dec = kGoOn, snap_slot = -1;
@@ -1494,7 +1509,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
             }
             if (nt[t] < 0) all = false;
           }
-          if (cls < 0 && (all || it >= max1 || (fresh && nslots >= kSnapSlots))) {
+          if (cls < 0 && (all || it >= max1)) {
+            // Stage 1 ends here whatever the label (every present class is
+            // met, or the cap): the loop ends, and the consumers help the
+            // 2BFS before thread 0 waits for the label.
+            dec = kEndForLabel;
+          } else if (cls < 0 && fresh && nslots >= kSnapSlots) {
             cls = wait_label(ctl);
             if (cls < 0) dec = kFailed;
           }
@@ -1522,6 +1542,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
     }
     if (dec != kGoOn) {
       if (dec == kFailed) ok = false;
+      if (dec == kEndForLabel) help = true;
       break;
     }
 
@@ -1614,6 +1635,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
     ++it;
   }
 
+  if (ok && help) {  // the consumers join the 2BFS levels unless the search has ended
+    if (lead) S.aux = atomicCAS(&s_help, kHelpNone, kHelpJoined);
+    cbar<NC>();
+    if (S.aux == kHelpNone) bfs_help(sa.g, &s_hl, NC, warp + 1);
+  }
   if (lead) {
     if (ok && broke && in_k0 && lead0) {  // breakdown in the k0 phase: v over completed ratios
       ctl->k0_done = k0done;

@@ -141,6 +141,7 @@ static __device__ bool team_sync(Team& t) {
 struct TeamSyncFn {
   static constexpr bool kWholeBlock = true;
   static constexpr bool kNarrow = false;  // team searches keep every level on the team
+  static constexpr bool kHelpers = false;
   Team* t;
   __device__ bool operator()() { return team_sync(*t); }
 };
