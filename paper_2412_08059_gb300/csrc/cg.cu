@@ -862,29 +862,20 @@ __device__ __forceinline__ double2 ld2(const double* p) {
   return *reinterpret_cast<const double2*>(p);
 }
 
-// x += alpha d, r -= alpha q over rows [R0, R1): two rows per lane, two
-// pairs per step with every operand loaded before the first store; returns
-// this thread's part of r^T r.
+// P2: r -= alpha q and r^T r over rows [R0, R1), both pairs of a step loaded
+// first.  (x += alpha d waits for P3, which reads d anyway.)
 __device__ __forceinline__ double p2_64(const CgArgs& a, int R0, int R1, int lane, double alpha) {
   double prr = 0.0;
   for (int base = R0 + 2 * lane; base < R1; base += 4 * kSlice) {
     const int g1 = base + 2 * kSlice;
     if (g1 + 2 <= R1) {
-      const double2 d0 = ld2(a.d64 + base), q0 = ld2(a.q64 + base);
-      const double2 d1 = ld2(a.d64 + g1), q1 = ld2(a.q64 + g1);
-      double2 x0 = ld2(a.x64 + base), r0 = ld2(a.r64 + base);
-      double2 x1 = ld2(a.x64 + g1), r1 = ld2(a.r64 + g1);
-      x0.x = __fma_rn(alpha, d0.x, x0.x);
-      x0.y = __fma_rn(alpha, d0.y, x0.y);
+      const double2 q0 = ld2(a.q64 + base), q1 = ld2(a.q64 + g1);
+      double2 r0 = ld2(a.r64 + base), r1 = ld2(a.r64 + g1);
       r0.x = __fma_rn(-alpha, q0.x, r0.x);
       r0.y = __fma_rn(-alpha, q0.y, r0.y);
-      x1.x = __fma_rn(alpha, d1.x, x1.x);
-      x1.y = __fma_rn(alpha, d1.y, x1.y);
       r1.x = __fma_rn(-alpha, q1.x, r1.x);
       r1.y = __fma_rn(-alpha, q1.y, r1.y);
-      *reinterpret_cast<double2*>(a.x64 + base) = x0;
       *reinterpret_cast<double2*>(a.r64 + base) = r0;
-      *reinterpret_cast<double2*>(a.x64 + g1) = x1;
       *reinterpret_cast<double2*>(a.r64 + g1) = r1;
       prr = __fma_rn(r0.x, r0.x, prr);
       prr = __fma_rn(r0.y, r0.y, prr);
@@ -896,18 +887,14 @@ __device__ __forceinline__ double p2_64(const CgArgs& a, int R0, int R1, int lan
     for (int h = 0; h < 2; ++h) {
       const int g = base + h * 2 * kSlice;
       if (g + 2 <= R1) {
-        const double2 d2 = ld2(a.d64 + g), q2 = ld2(a.q64 + g);
-        double2 x2 = ld2(a.x64 + g), r2 = ld2(a.r64 + g);
-        x2.x = __fma_rn(alpha, d2.x, x2.x);
-        x2.y = __fma_rn(alpha, d2.y, x2.y);
+        const double2 q2 = ld2(a.q64 + g);
+        double2 r2 = ld2(a.r64 + g);
         r2.x = __fma_rn(-alpha, q2.x, r2.x);
         r2.y = __fma_rn(-alpha, q2.y, r2.y);
-        *reinterpret_cast<double2*>(a.x64 + g) = x2;
         *reinterpret_cast<double2*>(a.r64 + g) = r2;
         prr = __fma_rn(r2.x, r2.x, prr);
         prr = __fma_rn(r2.y, r2.y, prr);
       } else if (g < R1) {
-        a.x64[g] = __fma_rn(alpha, a.d64[g], a.x64[g]);
         const double ri = __fma_rn(-alpha, a.q64[g], a.r64[g]);
         a.r64[g] = ri;
         prr = __fma_rn(ri, ri, prr);
@@ -917,17 +904,26 @@ __device__ __forceinline__ double p2_64(const CgArgs& a, int R0, int R1, int lan
   return prr;
 }
 
-// d = r + beta d over rows [R0, R1), both pairs of a step loaded first.
-__device__ __forceinline__ void p3_64(const CgArgs& a, int R0, int R1, int lane, double beta) {
+// P3: x += alpha d (the step of P2, with the d it used), then d = r + beta d,
+// over rows [R0, R1), both pairs of a step loaded first.
+__device__ __forceinline__ void p3_64(const CgArgs& a, int R0, int R1, int lane, double alpha,
+                                      double beta) {
   for (int base = R0 + 2 * lane; base < R1; base += 4 * kSlice) {
     const int g1 = base + 2 * kSlice;
     if (g1 + 2 <= R1) {
       double2 d0 = ld2(a.d64 + base), d1 = ld2(a.d64 + g1);
+      double2 x0 = ld2(a.x64 + base), x1 = ld2(a.x64 + g1);
       const double2 r0 = ld2(a.r64 + base), r1 = ld2(a.r64 + g1);
+      x0.x = __fma_rn(alpha, d0.x, x0.x);
+      x0.y = __fma_rn(alpha, d0.y, x0.y);
+      x1.x = __fma_rn(alpha, d1.x, x1.x);
+      x1.y = __fma_rn(alpha, d1.y, x1.y);
       d0.x = __fma_rn(beta, d0.x, r0.x);
       d0.y = __fma_rn(beta, d0.y, r0.y);
       d1.x = __fma_rn(beta, d1.x, r1.x);
       d1.y = __fma_rn(beta, d1.y, r1.y);
+      *reinterpret_cast<double2*>(a.x64 + base) = x0;
+      *reinterpret_cast<double2*>(a.x64 + g1) = x1;
       *reinterpret_cast<double2*>(a.d64 + base) = d0;
       *reinterpret_cast<double2*>(a.d64 + g1) = d1;
       continue;
@@ -936,39 +932,40 @@ __device__ __forceinline__ void p3_64(const CgArgs& a, int R0, int R1, int lane,
     for (int h = 0; h < 2; ++h) {
       const int g = base + h * 2 * kSlice;
       if (g + 2 <= R1) {
-        double2 d2 = ld2(a.d64 + g);
+        double2 d2 = ld2(a.d64 + g), x2 = ld2(a.x64 + g);
         const double2 r2 = ld2(a.r64 + g);
+        x2.x = __fma_rn(alpha, d2.x, x2.x);
+        x2.y = __fma_rn(alpha, d2.y, x2.y);
         d2.x = __fma_rn(beta, d2.x, r2.x);
         d2.y = __fma_rn(beta, d2.y, r2.y);
+        *reinterpret_cast<double2*>(a.x64 + g) = x2;
         *reinterpret_cast<double2*>(a.d64 + g) = d2;
       } else if (g < R1) {
-        a.d64[g] = __fma_rn(beta, a.d64[g], a.r64[g]);
+        const double dg = a.d64[g];
+        a.x64[g] = __fma_rn(alpha, dg, a.x64[g]);
+        a.d64[g] = __fma_rn(beta, dg, a.r64[g]);
       }
     }
   }
 }
 
-// Preconditioned P2: x += alpha d, r -= alpha q; returns r^T r and, in
-// *prz, r^T z with z = dinv r (z is not stored: P3 forms it again).
+// Preconditioned P2: r -= alpha q; returns r^T r and, in *prz, r^T z with
+// z = dinv r (z is not stored: P3 forms it again; x waits for P3 too).
 __device__ __forceinline__ double p2_64_pc(const CgArgs& a, int R0, int R1, int lane, double alpha,
                                            double* prz) {
   double prr = 0.0, pz = 0.0;
   for (int g = R0 + 2 * lane; g < R1; g += 2 * kSlice) {
     if (g + 2 <= R1) {
-      const double2 d2 = ld2(a.d64 + g), q2 = ld2(a.q64 + g), m2 = ld2(a.dinv64 + g);
-      double2 x2 = ld2(a.x64 + g), r2 = ld2(a.r64 + g);
-      x2.x = __fma_rn(alpha, d2.x, x2.x);
-      x2.y = __fma_rn(alpha, d2.y, x2.y);
+      const double2 q2 = ld2(a.q64 + g), m2 = ld2(a.dinv64 + g);
+      double2 r2 = ld2(a.r64 + g);
       r2.x = __fma_rn(-alpha, q2.x, r2.x);
       r2.y = __fma_rn(-alpha, q2.y, r2.y);
-      *reinterpret_cast<double2*>(a.x64 + g) = x2;
       *reinterpret_cast<double2*>(a.r64 + g) = r2;
       prr = __fma_rn(r2.x, r2.x, prr);
       prr = __fma_rn(r2.y, r2.y, prr);
       pz = __fma_rn(r2.x, __dmul_rn(m2.x, r2.x), pz);
       pz = __fma_rn(r2.y, __dmul_rn(m2.y, r2.y), pz);
     } else if (g < R1) {
-      a.x64[g] = __fma_rn(alpha, a.d64[g], a.x64[g]);
       const double ri = __fma_rn(-alpha, a.q64[g], a.r64[g]);
       a.r64[g] = ri;
       prr = __fma_rn(ri, ri, prr);
@@ -979,17 +976,23 @@ __device__ __forceinline__ double p2_64_pc(const CgArgs& a, int R0, int R1, int 
   return prr;
 }
 
-// Preconditioned P3: d = dinv r + beta d.
-__device__ __forceinline__ void p3_64_pc(const CgArgs& a, int R0, int R1, int lane, double beta) {
+// Preconditioned P3: x += alpha d, then d = dinv r + beta d.
+__device__ __forceinline__ void p3_64_pc(const CgArgs& a, int R0, int R1, int lane, double alpha,
+                                         double beta) {
   for (int g = R0 + 2 * lane; g < R1; g += 2 * kSlice) {
     if (g + 2 <= R1) {
-      double2 d2 = ld2(a.d64 + g);
+      double2 d2 = ld2(a.d64 + g), x2 = ld2(a.x64 + g);
       const double2 r2 = ld2(a.r64 + g), m2 = ld2(a.dinv64 + g);
+      x2.x = __fma_rn(alpha, d2.x, x2.x);
+      x2.y = __fma_rn(alpha, d2.y, x2.y);
       d2.x = __fma_rn(beta, d2.x, __dmul_rn(m2.x, r2.x));
       d2.y = __fma_rn(beta, d2.y, __dmul_rn(m2.y, r2.y));
+      *reinterpret_cast<double2*>(a.x64 + g) = x2;
       *reinterpret_cast<double2*>(a.d64 + g) = d2;
     } else if (g < R1) {
-      a.d64[g] = __fma_rn(beta, a.d64[g], __dmul_rn(a.dinv64[g], a.r64[g]));
+      const double dg = a.d64[g];
+      a.x64[g] = __fma_rn(alpha, dg, a.x64[g]);
+      a.d64[g] = __fma_rn(beta, dg, __dmul_rn(a.dinv64[g], a.r64[g]));
     }
   }
 }
@@ -1153,7 +1156,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
     int next = S.dec;
 
     if (kind == kIterate && next == kIterate) {
-      // ---- P2: x += alpha d, r -= alpha q, r^T r ----
+      // ---- P2: r -= alpha q, r^T r ----
       const double alpha = S.val;
       double przl = 0.0;
       double prr;
@@ -1180,9 +1183,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_cg64(CgArgs a) {
       }
       cbar<NC>();
       if (!ok || S.dec == kDone) break;
-      // ---- P3: d = r + beta d (kPc: d = dinv r + beta d) ----
-      if constexpr (kPc) p3_64_pc(a, R0, R1, lane, S.val);
-      else p3_64(a, R0, R1, lane, S.val);
+      // ---- P3: x += alpha d, d = r + beta d (kPc: d = dinv r + beta d) ----
+      if constexpr (kPc) p3_64_pc(a, R0, R1, lane, alpha, S.val);
+      else p3_64(a, R0, R1, lane, alpha, S.val);
       ok = cgrid_barrier<NC>(ctl, a.slot, round, &S.ok);
       ++it;
       next = -1;

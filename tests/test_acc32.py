@@ -169,8 +169,13 @@ def test_algorithm_ii_parity(mp):
         assert r["pdiam"] == ro["pdiam"]
         # v rests on float sums of n squares, which the two sides round in
         # different orders: a relative spread of about sqrt(n) u (measured
-        # 7.6e-6 on the 64000-row system)
-        assert abs(r["v"] - ro["v"]) <= 1e-4 * ro["v"]
+        # 7.6e-6 on the 64000-row system).  On the extended star the first
+        # iterations' norms are dominated by the hub, whose magnitude
+        # swallows the small terms of a float sum: v moves with the order
+        # (the oracle's own two readings give 0.884 and 0.722), so there only
+        # the label is checked, against the kNN on the GPU's own features.
+        if name not in SENSITIVE:
+            assert abs(r["v"] - ro["v"]) <= 1e-4 * ro["v"]
         assert r["cls"] == oracle.knn([A.n, A.nnz, r["pdiam"], r["v"]], (feat, cls))
         if r["cls"] == ro["cls"]:
             parity(r, ro, x.cpu().numpy(), xo, name)
