@@ -408,8 +408,8 @@ def reference_arm(args, rank):
 def batch_section(args, dev, steps, warmup):
     """512 systems (n log-uniform in [1e3, 2.6e5]; 2-D, 3-D, anisotropic and
     shifted Laplacians), each with x* ~ U[-1, 1] and b = A x*, eps2 = 1e-10,
-    auto eps1 from a kNN sample built on 64 other systems of the same
-    families.  Timed: mpcg_solve_batch (mixed, Algorithm II), the same batch
+    auto eps1 from a kNN sample built on 256 other systems of the same
+    families, labelled from batched sweeps.  Timed: mpcg_solve_batch (mixed, Algorithm II), the same batch
     in pure FP64, and the systems solved one at a time with mpcg_solve."""
     import numpy as np
     import torch
@@ -427,12 +427,13 @@ def batch_section(args, dev, steps, warmup):
         dbs.append(torch.from_numpy(b).to(dev))
         xs.append(torch.empty(A.n, dtype=torch.float64, device=dev))
     train = []
-    for i, d in enumerate(synth.batch_family(64, seed=12)):
+    for i, d in enumerate(synth.batch_family(256, seed=12)):
         A = synth.build_desc(d)
         _, b = synth.rhs(A, seed=5000 + i)
         train.append((f"train{i}", A, b))
     t = time.time()
-    feat, cls, _ = sample.build(train, device=dev)
+    # labels from batched sweeps: omega is that of the team kernels the batch runs
+    feat, cls, _ = sample.build_batched(train, device=dev)
     t_sample = time.time() - t
     S = mpcg.DeviceSample(feat, cls, device=dev)
     nsys = len(mats)
@@ -485,7 +486,7 @@ def batch_section(args, dev, steps, warmup):
     flops64 = sum(2.0 * (A.nnz + 5 * A.n) * r["n2"] for A, r in zip(mats, r_fp64))
     return {
         "workload": f"{nsys} systems, n log-uniform [1e3, 2.6e5] (2D/3D/aniso/shifted Laplacians), "
-                    "eps2 1e-10, auto eps1 (kNN sample: 64 other systems of the families)",
+                    "eps2 1e-10, auto eps1 (kNN sample: 256 other systems of the families, labels from batched sweeps)",
         "systems": nsys, "sum_n": sum_n, "sum_nnz": sum_nnz,
         "solves_per_s": {"batch_mixed": nsys / (ms_mixed / 1e3), "batch_fp64": nsys / (ms_fp64 / 1e3),
                          "one_at_a_time_mixed": nsys / (ms_seq / 1e3)},
@@ -540,10 +541,11 @@ def serve_section(args, dev):
         dmats.append(mpcg.DeviceCSR.from_host(A, dev))
         rhs.append([torch.from_numpy(synth.rhs(A, seed=7000 + 2 * k + j)[1]).to(dev) for j in range(2)])
     train = []
-    for i, d in enumerate(synth.batch_family(48, seed=22, n_lo=1e3, n_hi=5e5)):
+    for i, d in enumerate(synth.batch_family(256, seed=22, n_lo=1e3, n_hi=5e5)):
         A = synth.build_desc(d)
         train.append((f"t{i}", A, synth.rhs(A, seed=9000 + i)[1]))
-    feat, cls, _ = sample.build(train, device=dev)
+    # labels from batched sweeps: omega is that of the team kernels the server runs
+    feat, cls, _ = sample.build_batched(train, device=dev)
     S = mpcg.DeviceSample(feat, cls, device=dev)
     R = args.serve_requests
     req_m = rng.integers(0, len(mats), R)

@@ -34,7 +34,7 @@ import time
 import numpy as np
 import torch
 
-from . import mpcg
+from . import mpcg, sample
 
 CLASSES = (2, 3, 4, 5, 6, 7)
 MU = (1.1, 3.0, 10.0)
@@ -103,64 +103,24 @@ def build(desc: dict):
     return synth.banded(desc["n"], desc["b"], desc["p"], desc["mu"], seed=desc["seed"])
 
 
-def _batch_results(dmats, dbs, xs, ws, res, opts, sample):
-    mpcg.solve_batch_async(dmats, dbs, xs, opts, ws, res, sample)
-    torch.cuda.synchronize()
-    return mpcg.read_results(res, len(dmats))
-
-
 def sweep_records(descs: list[dict], device="cuda", eps2: float = 1e-10, k0: int = 10,
                   team_rows: int = 0, acc32: int = 0, tol_relative: int = 1) -> dict:
-    """Step 2 for every descriptor, as batched solves on the GPU: one batch of
-    Algorithm II for the features, one of Algorithm I per candidate eps1 and
-    one pure-FP64 batch.  b = A x* with x* ~ U[-1, 1] (seeded per matrix).
-    acc32 = 1 sums the single-precision stage's inner products in float, and
-    tol_relative = 0 stops on ||r|| <= eps as Sec. 3 prints it (the options of
-    the same names)."""
+    """Step 2 for every descriptor, as batched solves on the GPU
+    (sample.sweep_batched): one batch of Algorithm II for the features, one of
+    Algorithm I per candidate eps1 and one pure-FP64 batch.  b = A x* with
+    x* ~ U[-1, 1] (seeded per matrix).  acc32 = 1 sums the single-precision
+    stage's inner products in float, and tol_relative = 0 stops on
+    ||r|| <= eps as Sec. 3 prints it (the options of the same names)."""
     import synth
     t0 = time.time()
     mats = [build(d) for d in descs]
     bs = [synth.rhs(A, seed=d["seed"])[1] for A, d in zip(mats, descs)]
     t_gen = time.time() - t0
-    dmats = [mpcg.DeviceCSR.from_host(A, device) for A in mats]
-    dbs = [torch.from_numpy(np.ascontiguousarray(b)).to(device) for b in bs]
-    xs = [torch.empty(A.n, dtype=torch.float64, device=device) for A in mats]
-    ws = torch.empty(mpcg.batch_workspace_bytes(dmats), dtype=torch.uint8, device=device)
-    res = mpcg.result_buffer(len(mats), device)
-    N = len(mats)
     t1 = time.time()
-    # features (any sample: the label of this run is not used)
-    dummy = mpcg.DeviceSample(np.ones((1, 4)), np.array([2], np.int8), device=device)
-    rf = _batch_results(dmats, dbs, xs, ws, res,
-                        mpcg.options(k0=k0, eps2=eps2, team_rows=team_rows, acc32=acc32,
-                                     tol_relative=tol_relative), dummy)
-    feat = np.array([[A.n, A.nnz, r["pdiam"], r["v"]] for A, r in zip(mats, rf)], dtype=np.float64)
-    n1 = np.zeros((N, len(CLASSES)), np.int64)
-    n2 = np.zeros((N, len(CLASSES)), np.int64)
-    st = np.zeros((N, len(CLASSES)), np.int64)
-    ms32 = np.zeros(N)
-    for j, t in enumerate(CLASSES):
-        rr = _batch_results(dmats, dbs, xs, ws, res,
-                            mpcg.options(eps1=float(f"1e-{t}"), eps2=eps2, k0=k0,
-                                         team_rows=team_rows, acc32=acc32,
-                                         tol_relative=tol_relative), None)
-        for i, r in enumerate(rr):
-            n1[i, j], n2[i, j], st[i, j] = r["n1"], r["n2"], r["status"]
-            ms32[i] += (r["t_fp32_ns"] - r["t_features_ns"]) / 1e6
-    rd = _batch_results(dmats, dbs, xs, ws, res,
-                        mpcg.options(fp64_only=1, eps2=eps2, team_rows=team_rows,
-                                     tol_relative=tol_relative), None)
-    ndp = np.array([r["n2"] for r in rd], np.int64)
-    st_dp = np.array([r["status"] for r in rd], np.int64)
-    # t_sp from the single-precision stages of the Algorithm I runs; t_dp from
-    # the pure-FP64 run (a mixed batch runs its FP64 stages in a second launch,
-    # so their clock marks include the wait for the first launch to end)
-    ms64 = np.array([(r["t_fp64_ns"] - r["t_prep_ns"]) / 1e6 for r in rd])
-    t_sp = ms32 / np.maximum(n1.sum(axis=1), 1)
-    t_dp = ms64 / np.maximum(ndp, 1)
-    return {"descs": descs, "feat": feat, "n1": n1, "n2": n2, "status": st, "n_dp": ndp,
-            "status_dp": st_dp, "omega": t_sp / t_dp, "seconds_generate": t_gen,
-            "seconds_gpu": time.time() - t1}
+    rec = sample.sweep_batched(mats, bs, device, eps2=eps2, k0=k0, team_rows=team_rows,
+                               acc32=acc32, tol_relative=tol_relative, classes=CLASSES)
+    rec.update(descs=descs, seconds_generate=t_gen, seconds_gpu=time.time() - t1)
+    return rec
 
 
 def labels(n1: np.ndarray, n2: np.ndarray, omega: float = 1.0 / 3.0) -> np.ndarray:

@@ -176,3 +176,22 @@ def test_sweep_of_a_small_general_sample_matches_oracle(mp):
     a = ev.protocol(rec, ev.gpu_classifier(), 301, ks=(1, 5), splits=4, seed=2)
     b = ev.protocol(rec, oracle_classifier(), 301, ks=(1, 5), splits=4, seed=2)
     assert a == b
+
+
+@pytest.mark.gpu
+def test_batched_sample_builder_labels_by_eq4_with_the_team_omega(mp):
+    """sample.build_batched: every label is the Eq. (4) argmin with the
+    matrix's measured omega (a recount through oracle/metrics.py), and the
+    features' pseudo-diameters are the oracle's."""
+    from paper_2412_08059_gb300 import sample
+    systems = []
+    for i, d in enumerate(synth.batch_family(24, seed=31, n_lo=1e3, n_hi=4e4)):
+        A = synth.build_desc(d)
+        systems.append((f"s{i}", A, synth.rhs(A, seed=700 + i)[1]))
+    feat, cls, recs = sample.build_batched(systems)
+    assert len(recs) == len(systems) == feat.shape[0] == cls.size
+    for (name, A, b), f, c, r in zip(systems, feat, cls, recs):
+        assert r["name"] == name and r["omega"] > 0
+        assert c == metrics.label(r["n1"], r["n2"], r["omega"])
+        assert (f[0], f[1]) == (A.n, A.nnz)
+        assert f[2] == oracle.pseudo_diameter(A)
