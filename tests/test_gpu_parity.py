@@ -66,6 +66,39 @@ def disjoint(*mats):
                      np.concatenate(vals))
 
 
+def cycle(n):
+    i = np.arange(n, dtype=np.int64)
+    return synth.from_edges(n, i, (i + 1) % n, -np.ones(n), np.full(n, 2.2), f"cycle_{n}")
+
+
+def caterpillar(spine, legs):
+    """A path of `spine` vertices, each with `legs` leaves (numbered after the spine)."""
+    i = list(range(spine - 1))
+    j = list(range(1, spine))
+    for v in range(spine):
+        for k in range(legs):
+            i.append(v)
+            j.append(spine + v * legs + k)
+    n = spine * (1 + legs)
+    deg = np.bincount(np.concatenate([i, j]), minlength=n).astype(float)
+    return synth.from_edges(n, np.array(i), np.array(j), -np.ones(len(i)), 1.1 * deg, "caterpillar")
+
+
+def lollipop(k, tail):
+    """A clique on k vertices with a path of `tail` vertices hanging off vertex k - 1."""
+    i, j = [], []
+    for a in range(k):
+        for b in range(a + 1, k):
+            i.append(a)
+            j.append(b)
+    for v in range(k - 1, k + tail - 1):
+        i.append(v)
+        j.append(v + 1)
+    n = k + tail
+    deg = np.bincount(np.concatenate([i, j]), minlength=n).astype(float)
+    return synth.from_edges(n, np.array(i), np.array(j), -np.ones(len(i)), 1.1 * deg, "lollipop")
+
+
 GRAPHS = dict(MATRICES)
 GRAPHS.update({
     "path_2000": lambda: synth.path(2000),
@@ -74,6 +107,13 @@ GRAPHS.update({
                               synth.from_edges(1, [], [], np.zeros(0), np.ones(1)),
                               synth.random_regular_laplacian(500, 4, seed=2)),
     "single": lambda: synth.from_edges(1, [], [], np.zeros(0), np.ones(1)),
+    # narrow frontiers of the dual search (one warp, frontier tables): fronts that
+    # meet at one level or at neighbouring levels, leaves off a path, a dense end
+    "cycle_2001": lambda: cycle(2001),
+    "cycle_2000": lambda: cycle(2000),
+    "caterpillar": lambda: caterpillar(700, 3),
+    "lollipop": lambda: lollipop(30, 900),
+    "grid_37x300": lambda: synth.laplacian_2d(37, 300),
 })
 
 
