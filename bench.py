@@ -40,7 +40,7 @@ KERNELS_PER_SOLVE_AUTO = 9    # k_init, k_rows, k_scan, k_fill, k_bnorm_*(2), k_
 KERNELS_PER_SOLVE_FP64 = 8
 # DRAM bytes per FP64 iteration of k_cg64 at 128^3 from one ncu capture (65.92 GB over 307
 # passes of the captured launch); profiles/k_cg64_lap3d128.md.
-K_CG64_DRAM_BYTES_PER_ITER = 65.92e9 / 307
+K_CG64_DRAM_BYTES_PER_ITER = 56.40e9 / 307
 
 
 def parse():
