@@ -224,11 +224,14 @@ __device__ __forceinline__ void dual_level_items(const BfsGraph& g, const int32_
   }
 }
 
-// The group's warp at the start of a wide level: when helpers have joined,
-// publish the level and meet them.  Returns the warps of the block on it.
+// The group's warp at the start of a wide level: when helpers have joined
+// and the level needs more than one round of the group's warps alone (two
+// items a lane), publish the level and meet them.  Returns the warps of the
+// block on it.
 template <class Sync>
 __device__ __forceinline__ int help_begin(Sync& s, const HelpLevel& L) {
   if constexpr (Sync::kHelpers) {
+    if (L.sa + L.sb <= 64 * (int)gridDim.x) return 1;  // one round: more warps cannot shorten it
     int st = 0;
     if ((threadIdx.x & 31) == 0) st = *s.hstate;
     st = __shfl_sync(0xffffffffu, st, 0);
