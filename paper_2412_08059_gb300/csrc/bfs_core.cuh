@@ -236,10 +236,10 @@ __device__ __forceinline__ int help_begin(Sync& s, const HelpLevel& L) {
     if ((threadIdx.x & 31) == 0) st = *s.hstate;
     st = __shfl_sync(0xffffffffu, st, 0);
     if (st != kHelpJoined) return 1;
-    if ((threadIdx.x & 31) == 0) {
-      *s.hl = L;
-      __threadfence();  // the other blocks' queue entries, acquired at the grid barrier
-    }
+    // The other blocks' queue entries, acquired by lane 0 at the grid
+    // barrier, reach the helpers through the block barrier (the same order
+    // as the consumers' own grid barrier: acquire by one thread, then bar.sync).
+    if ((threadIdx.x & 31) == 0) *s.hl = L;
     __syncwarp();
     named_bar(kHelpBarStart, (s.nhelp + 1) * 32);
     return s.nhelp + 1;
@@ -254,8 +254,9 @@ template <class Sync>
 __device__ __forceinline__ void help_end(Sync& s, int warps) {
   if constexpr (Sync::kHelpers) {
     if (warps > 1) {
+      // the helpers' claims and pushes precede the barrier, and lane 0's
+      // release at the grid barrier that follows covers them
       named_bar(kHelpBarEnd, (s.nhelp + 1) * 32);
-      if ((threadIdx.x & 31) == 0) __threadfence();
       __syncwarp();
     }
   }
