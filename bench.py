@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve section")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched-solve section")
     ap.add_argument("--batch-systems", type=int, default=512)
+    ap.add_argument("--batch-eps1-sweep", action="store_true",
+                    help="with the batch section: also time the batch at every fixed eps1 "
+                         "(Algorithm I) and account for its block-time per launch")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving section")
     ap.add_argument("--serve-requests", type=int, default=400)
@@ -439,10 +442,13 @@ def batch_section(args, dev, steps, warmup):
     nsys = len(mats)
     ws = torch.empty(mpcg.batch_workspace_bytes(dmats), dtype=torch.uint8, device=dev)
     res = mpcg.result_buffer(nsys, dev)
-    # autotune the team granularity once, outside the timed region
-    team_rows, tune_ms = mpcg.batch_tune(dmats, dbs, xs, mpcg.options(), ws, res, S)
-    o_mixed = mpcg.options(team_rows=team_rows)
-    o_fp64 = mpcg.options(fp64_only=1, team_rows=team_rows)
+    # autotune every system's team size, each mode on its own, outside the timed region
+    team_rows, tune_ms, rows_mixed = mpcg.batch_tune(dmats, dbs, xs, mpcg.options(), ws, res, S,
+                                                     per_system=True)
+    team_rows64, tune_ms64, rows_fp64 = mpcg.batch_tune(dmats, dbs, xs, mpcg.options(fp64_only=1),
+                                                        ws, res, None, per_system=True)
+    o_mixed = mpcg.options(team_rows=team_rows, team_rows_sys=rows_mixed)
+    o_fp64 = mpcg.options(fp64_only=1, team_rows=team_rows64, team_rows_sys=rows_fp64)
 
     def timed(fn, k, w):
         for _ in range(w):
@@ -473,16 +479,20 @@ def batch_section(args, dev, steps, warmup):
             mpcg.solve_async(dmats[i], dbs[i], xs[i], o_mixed, ws1, res1[i * rsz:(i + 1) * rsz], S)
     ms_seq = timed(seq, 1, 1)
     r_seq = mpcg.read_results(res1, nsys)
+    sweep = batch_eps1_sweep(mpcg, dmats, dbs, xs, ws, res, S, team_rows, timed) \
+        if args.batch_eps1_sweep else None
     bad = [r["status"] for r in r_mixed + r_fp64 + r_seq if r["status"] < 0]
     n1 = np.array([r["n1"] for r in r_mixed])
     n2 = np.array([r["n2"] for r in r_mixed])
     ndp = np.array([r["n2"] for r in r_fp64])
     sum_n = int(sum(A.n for A in mats))
     sum_nnz = int(sum(A.nnz for A in mats))
-    # algorithmic bytes: per iteration the sliced matrix and six vector passes
-    by = lambda A, p: A.nnz * (p + 4) + 4 * (A.n + 1) + 6 * p * A.n
-    bytes_mixed = sum(by(A, 4) * r["n1"] + by(A, 8) * (r["n2"] + 2) for A, r in zip(mats, r_mixed))
-    bytes_fp64 = sum(by(A, 8) * (r["n2"] + 2) for A, r in zip(mats, r_fp64))
+    # algorithmic bytes: per iteration the sliced matrix (a value and a column
+    # of spmv_cols bits per stored entry) and six vector passes
+    by = lambda A, p, r: A.nnz * (p + r["spmv_cols"] // 8) + 4 * (A.n + 1) + 6 * p * A.n
+    bytes_mixed = sum(by(A, 4, r) * r["n1"] + by(A, 8, r) * (r["n2"] + 2)
+                      for A, r in zip(mats, r_mixed))
+    bytes_fp64 = sum(by(A, 8, r) * (r["n2"] + 2) for A, r in zip(mats, r_fp64))
     flops64 = sum(2.0 * (A.nnz + 5 * A.n) * r["n2"] for A, r in zip(mats, r_fp64))
     return {
         "workload": f"{nsys} systems, n log-uniform [1e3, 2.6e5] (2D/3D/aniso/shifted Laplacians), "
@@ -498,14 +508,53 @@ def batch_section(args, dev, steps, warmup):
                                    "fp64": float(ndp.sum() / (ms_fp64 / 1e3))},
         "mean_iters": {"n1": float(n1.mean()), "n2": float(n2.mean()), "n_dp": float(ndp.mean())},
         "eps1_labels": np.bincount([max(0, r["cls"]) for r in r_mixed], minlength=8).tolist(),
+        "spmv_cols_16bit_systems": int(sum(r["spmv_cols"] == 16 for r in r_mixed)),
         "algorithmic_GBps": {"batch_mixed": bytes_mixed / (ms_mixed / 1e3) / 1e9,
                              "batch_fp64": bytes_fp64 / (ms_fp64 / 1e3) / 1e9},
         "fp64_TFLOPs_batch_fp64": flops64 / (ms_fp64 / 1e3) / 1e12,
         "failed_statuses": bad, "sample_seconds": round(t_sample, 1),
         "kernels_per_batch": {"batch_mixed": 2, "batch_fp64": 1},
-        "autotuned_team_rows": team_rows,
-        "tuning_ms": dict(zip(("8192", "16384", "32768", "65536"), [round(x, 1) for x in tune_ms])),
+        "autotuned_team_rows": {"batch_mixed": team_rows, "batch_fp64": team_rows64},
+        "tuning_ms": {m: dict(zip(("8192", "16384", "32768", "65536", "per_system"),
+                                  [round(x, 1) for x in t]))
+                      for m, t in (("batch_mixed", tune_ms), ("batch_fp64", tune_ms64))},
+        "per_system_team_rows": {m: {str(k): int((r == k).sum()) for k in (8192, 16384, 32768, 65536)}
+                                 for m, r in (("batch_mixed", rows_mixed), ("batch_fp64", rows_fp64))},
+        "eps1_sweep": sweep,
     }
+
+
+def batch_eps1_sweep(mpcg, dmats, dbs, xs, ws, res, S, team_rows, timed):
+    """The batch at one team granularity: pure FP64, auto eps1 and every fixed
+    eps1 = 1e-2 .. 1e-7 (Algorithm I).  Per mode: ms per batch, mean N1 and N2,
+    and the block-time of each launch (sum over systems of team blocks x the
+    time the system kept its team busy, from the records' clock marks) over
+    the grid's blocks, against that launch's span: their ratio is the launch's
+    load balance."""
+    import numpy as np
+    import torch
+
+    grid = torch.cuda.get_device_properties(0).multi_processor_count  # one block per SM
+    modes = [("fp64", mpcg.options(fp64_only=1, team_rows=team_rows), None),
+             ("auto", mpcg.options(team_rows=team_rows), S)]
+    modes += [(f"1e-{t}", mpcg.options(eps1=10.0 ** -t, team_rows=team_rows), None) for t in range(2, 8)]
+    out = {}
+    for name, o, s in modes:
+        ms = timed(lambda: mpcg.solve_batch_async(dmats, dbs, xs, o, ws, res, s), 3, 1)
+        rr = mpcg.read_results(res, len(dmats))
+        t0 = min(r["t_start_ns"] for r in rr)
+        b1 = sum(r["team_blocks"] * max(0, r["t_fp32_ns"] - r["t_start_ns"]) for r in rr) / 1e6
+        b2 = sum(r["team_blocks"] * max(0, r["t_end_ns"] - r["t_stage2_ns"]) for r in rr) / 1e6
+        end1 = max(r["t_fp32_ns"] for r in rr) - t0
+        end = max(r["t_end_ns"] for r in rr) - t0
+        out[name] = {"ms": round(ms, 2),
+                     "mean_n1": float(np.mean([r["n1"] for r in rr])),
+                     "mean_n2": float(np.mean([r["n2"] for r in rr])),
+                     "block_ms_over_grid": round((b1 + b2) / grid, 1),
+                     "launch1": None if name == "fp64" else
+                     {"block_ms_over_grid": round(b1 / grid, 1), "span_ms": round(end1 / 1e6, 1)},
+                     "failed": int(sum(r["status"] < 0 for r in rr))}
+    return out
 
 
 # Serving: Poisson arrivals, continuous batching

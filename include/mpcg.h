@@ -165,6 +165,24 @@ typedef struct {
                                 float-float and the blocks summed in double, the reading of
                                 Sec. 9, Remark 3 (norms of the single-precision stage computed
                                 in double).  The FP64 stage is the same either way */
+  int32_t spmv_variant;      /* column format of the sliced SpMV layout (the only access to A
+                                in the CG stages): 0 (default) = chosen per system at set-up:
+                                16-bit offsets from the row when every entry kept in the
+                                slices lies within 32767 columns of its row, 32-bit columns
+                                otherwise; 1 = 32-bit columns always.  The single-system
+                                kernels read the chosen format in both stages; the batched
+                                solve and the server read it in the single-precision SpMV
+                                that stages its pairs in shared memory (the batch's stage 1,
+                                the server's split mode) and 32-bit columns elsewhere.  Both
+                                formats sum the same entries in the same order, so x and every
+                                count are bit-identical; 16-bit offsets move 6 instead of 8
+                                bytes a stored entry in single precision, 10 instead of 12 in
+                                double */
+  const int32_t* team_rows_sys; /* batched solve only: NULL (default), or a host array of one
+                                entry per system of the call, each that system's target rows
+                                per block (its team size, as team_rows sets it for all; an
+                                entry <= 0 takes team_rows).  mpcg_batch_tune writes one.  Read
+                                during the call only */
 } mpcg_options_t;
 
 /* Result record, written by the device at the end of the call's work into
@@ -187,6 +205,13 @@ typedef struct {
    * stage 2; result written; end of the set-up (demotion, sliced layout,
    * ||b||). */
   uint64_t t_start_ns, t_features_ns, t_fp32_ns, t_fp64_ns, t_end_ns, t_prep_ns;
+  uint64_t t_stage2_ns;      /* start of the double-precision stage (the batched solve starts
+                                it in its second launch; elsewhere the end of stage 1) */
+  int32_t spmv_cols;         /* bits of a stored column that the single-precision SpMV read:
+                                16 (offsets from the row) or 32 (option spmv_variant); 0 if the
+                                set-up did not build the layout */
+  int32_t team_blocks;       /* batched solve and server: blocks of the team that solved the
+                                system (its tile shape); 0 in the single-system calls */
 } mpcg_result_t;
 
 mpcg_options_t mpcg_options_default(void);
@@ -261,21 +286,34 @@ int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const double* const*
                          const mpcg_options_t* opts, void* ws, size_t ws_bytes,
                          mpcg_result_t* res, mpcg_stream_t stream);
 
-/* Autotuner of the batched solve (not in the paper): times mpcg_solve_batch
- * with the given arguments at each of MPCG_TUNE_CANDIDATES team granularities
- * (opts->team_rows = 8192, 16384, 32768, 65536 rows per block; a system's
- * team is the smallest with at most that many rows per block) and writes the
- * fastest to *team_rows_out (host), and each candidate's milliseconds to
- * ms_out (host float[MPCG_TUNE_CANDIDATES], nullable).  Pass the result in
- * opts->team_rows to later batch calls or to a server.  Unlike the other
- * entry points this call synchronises the host with `stream` (one event wait
- * per candidate).  x and res hold the last candidate's results. */
+/* Autotuner of the batched solve (not in the paper): the tile shape of every
+ * system, i.e. its team size.  Times mpcg_solve_batch with the given arguments
+ * at each of MPCG_TUNE_CANDIDATES team granularities (opts->team_rows =
+ * 8192, 16384, 32768, 65536 rows per block for every system; a system's team
+ * is the smallest with at most that many rows per block) and writes the
+ * fastest to *team_rows_out (host).  With team_rows_sys_out (host int32[nsys],
+ * nullable) it then picks a granularity per system from those runs' device
+ * clock marks: each system's busy time and block-time (team blocks x busy
+ * time) under every candidate; under a bound T on one system's time each
+ * system takes its cheapest candidate within T, and the T that minimises
+ * max(T, summed block-time / (grid x the best uniform run's block
+ * efficiency)) is kept.  One more timed call with that choice
+ * (opts->team_rows_sys) decides: if it is faster than the best uniform
+ * candidate the per-system choice is written, else the uniform best for
+ * every system.  ms_out (host float[MPCG_TUNE_RUNS], nullable): each
+ * candidate's milliseconds, then the per-system call's (-1 if not run).
+ * Pass the results in opts->team_rows and opts->team_rows_sys to later batch
+ * calls over the same systems.  The column format of each system's SpMV is
+ * its own set-up choice (option spmv_variant).  Unlike the other entry
+ * points this call synchronises the host with `stream` (once per timed
+ * call).  x and res hold the last call's results. */
 #define MPCG_TUNE_CANDIDATES 4
+#define MPCG_TUNE_RUNS (MPCG_TUNE_CANDIDATES + 1)
 int32_t mpcg_batch_tune(int32_t nsys, const mpcg_csr_t* A, const double* const* b,
                         double* const* x, const mpcg_sample_t* sample,
                         const mpcg_options_t* opts, void* ws, size_t ws_bytes,
                         mpcg_result_t* res, mpcg_stream_t stream, int32_t* team_rows_out,
-                        float* ms_out);
+                        int32_t* team_rows_sys_out, float* ms_out);
 
 /* ---- serving: continuous batching over a slot table (not in the paper) ----
  *

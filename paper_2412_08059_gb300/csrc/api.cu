@@ -27,6 +27,7 @@ bool options_ok(const mpcg_options_t* o) {
   if (o->precond != 0 && o->precond != 1) return false;
   if (o->stop_true_residual != 0 && o->stop_true_residual != 1) return false;
   if (o->acc32 != 0 && o->acc32 != 1) return false;
+  if (o->spmv_variant != 0 && o->spmv_variant != 1) return false;
   return true;
 }
 
@@ -107,6 +108,7 @@ mpcg_options_t mpcg_options_default(void) {
   o.precond = 0;
   o.stop_true_residual = 0;
   o.acc32 = 0;
+  o.spmv_variant = 0;
   return o;
 }
 

@@ -24,6 +24,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
+#include <queue>
+#include <utility>
 #include <vector>
 
 #include "stage.cuh"
@@ -43,7 +46,7 @@ static __device__ bool sys_prep(Team& t, const BatchSys& s, const BatchArgs& a, 
   if (sys_status(s) == 0) {
     if (t.rank == 0) block_scan_slices(s.w.slice_w, s.w.slice_ptr, s.nslices);
     if (!team_sync(t)) return false;
-    sys_fill(t, s);
+    sys_fill(t, s, true);
     // ||b||_2 in double
     double p = 0.0;
     for (int i = team_tid(t); i < s.n; i += team_threads(t)) p = __fma_rn(s.b[i], s.b[i], p);
@@ -127,7 +130,7 @@ static __device__ bool sys_solve(Team& t, const BatchSys& s, const BatchArgs& a)
   if (sys_status(s) == 0) {
     if (t.rank == 0) block_scan_slices(s.w.slice_w, s.w.slice_ptr, s.nslices);
     if (!team_sync(t)) return false;
-    sys_fill(t, s);
+    sys_fill(t, s, false);
     // ||b||_2 in double
     double p = 0.0;
     for (int i = team_tid(t); i < s.n; i += team_threads(t)) p = __fma_rn(s.b[i], s.b[i], p);
@@ -243,7 +246,8 @@ int team_smem(const void* kernel, int stage1) {
   return stage1 ? kTeamSmem : kScanSmem;
 }
 
-Plan make_plan(int nsys, const int* n, const double* work, int grid, int rows_per_block) {
+Plan make_plan(int nsys, const int* n, const double* work, int grid, int rows_per_block,
+               const int32_t* rows_sys) {
   if (rows_per_block <= 0) rows_per_block = kRowsPerBlock;
   Plan P;
   std::vector<int> cls(nsys);
@@ -251,7 +255,8 @@ Plan make_plan(int nsys, const int* n, const double* work, int grid, int rows_pe
   double cw[kTeamClasses] = {0};
   int cnt[kTeamClasses] = {0};
   for (int i = 0; i < nsys; ++i) {
-    cls[i] = size_class(n[i], rows_per_block);
+    const int rpb = rows_sys && rows_sys[i] > 0 ? rows_sys[i] : rows_per_block;
+    cls[i] = size_class(n[i], rpb);
     w[i] = work[i];
   }
   // Demote the largest classes while one team of every non-empty class does
@@ -411,7 +416,7 @@ extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const dou
   if (grid <= 0) return MPCG_ERR_CUDA;
   std::vector<double> work(nsys);
   for (int32_t i = 0; i < nsys; ++i) work[i] = work_of(nv[i], mv[i]);
-  const Plan P = make_plan(nsys, nv.data(), work.data(), grid, opts->team_rows);
+  const Plan P = make_plan(nsys, nv.data(), work.data(), grid, opts->team_rows, opts->team_rows_sys);
 
   // Header blob: [BatchHdr | BatchSys[nsys] | order | team_of_block |
   // rank_of_block | team_size | team_class], then the systems' regions.
@@ -488,12 +493,95 @@ extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const dou
   return e == cudaSuccess ? MPCG_OK : MPCG_ERR_CUDA;
 }
 
+namespace {
+
+// Busy times (ns) of one system measured on teams of 2^c blocks: set-up and
+// stage 1 (the first launch of a mixed batch), and stage 2; < 0 unmeasured.
+struct SysTimes {
+  double s1[kTeamClasses], s2[kTeamClasses];
+  int n1[kTeamClasses], n2[kTeamClasses];  // measurements averaged into each entry
+};
+
+// Busy time on a team of 2^c blocks: the measurement there, else the nearest
+// measured size scaled by the block ratio (perfect scaling).
+double busy_at(const double* v, int c) {
+  if (v[c] >= 0.0) return v[c];
+  for (int d = 1; d < kTeamClasses; ++d) {
+    if (c - d >= 0 && v[c - d] >= 0.0) return v[c - d] / (double)(1 << d);
+    if (c + d < kTeamClasses && v[c + d] >= 0.0) return v[c + d] * (double)(1 << d);
+  }
+  return 0.0;
+}
+
+// Simulated span (ns) of one launch under plan P: every team starts at 0 and
+// takes the next system of its own class queue, then of the smaller classes
+// (as batch_take does), until all queues are empty.  stage: 1 = the first
+// launch of a mixed batch, 2 = the second, 0 = one launch with both.
+double simulate_launch(const Plan& P, const std::vector<SysTimes>& T, int stage) {
+  using Ev = std::pair<double, int>;
+  std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> q;
+  for (int tm = 0; tm < (int)P.team_class.size(); ++tm) q.push({0.0, tm});
+  int head[kTeamClasses] = {0};
+  double span = 0.0;
+  while (!q.empty()) {
+    const Ev e = q.top();
+    q.pop();
+    const int c = P.team_class[e.second];
+    int sys = -1;
+    for (int cc = c; cc >= 0 && sys < 0; --cc)
+      if (head[cc] < P.qlen[cc]) sys = P.order[P.qbase[cc] + head[cc]++];
+    if (sys < 0) {
+      span = std::max(span, e.first);
+      continue;
+    }
+    const SysTimes& t = T[sys];
+    const double d = stage == 1 ? busy_at(t.s1, c)
+                     : stage == 2 ? busy_at(t.s2, c)
+                                  : busy_at(t.s1, c) + busy_at(t.s2, c);
+    q.push({e.first + d, e.second});
+  }
+  return span;
+}
+
+// Per-system team granularity: starting from the best uniform candidate,
+// each system in turn (largest block-time first) moves to another candidate
+// when that shortens the simulated batch (the planner re-run on the new
+// choice, then each launch simulated); two passes.
+std::vector<int32_t> per_system_rows(const std::vector<SysTimes>& T, const std::vector<double>& order_key,
+                                     const int* nv, const std::vector<double>& work, int grid,
+                                     const int* cand, int K, int best, bool two_launch) {
+  const int nsys = (int)T.size();
+  std::vector<int32_t> rows(nsys, cand[best]);
+  auto span = [&]() {
+    const Plan P = make_plan(nsys, nv, work.data(), grid, cand[best], rows.data());
+    return two_launch ? simulate_launch(P, T, 1) + simulate_launch(P, T, 2) : simulate_launch(P, T, 0);
+  };
+  std::vector<int> idx(nsys);
+  for (int i = 0; i < nsys; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return order_key[a] > order_key[b]; });
+  double cur = span();
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i : idx)
+      for (int k = 0; k < K; ++k) {
+        if (cand[k] == rows[i]) continue;
+        const int32_t old = rows[i];
+        rows[i] = cand[k];
+        const double m = span();
+        if (m < cur * (1.0 - 1e-4)) cur = m;
+        else rows[i] = old;
+      }
+  return rows;
+}
+
+}  // namespace
+
 extern "C" int32_t mpcg_batch_tune(int32_t nsys, const mpcg_csr_t* A, const double* const* b,
                                    double* const* x, const mpcg_sample_t* sample,
                                    const mpcg_options_t* opts, void* ws, size_t ws_bytes,
                                    mpcg_result_t* res, mpcg_stream_t stream,
-                                   int32_t* team_rows_out, float* ms_out) {
-  if (!opts || !team_rows_out) return MPCG_ERR_INVALID_ARG;
+                                   int32_t* team_rows_out, int32_t* team_rows_sys_out,
+                                   float* ms_out) {
+  if (!opts || !team_rows_out || nsys <= 0 || !A || !res) return MPCG_ERR_INVALID_ARG;
   static const int kCand[MPCG_TUNE_CANDIDATES] = {8192, 16384, 32768, 65536};
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -501,32 +589,85 @@ extern "C" int32_t mpcg_batch_tune(int32_t nsys, const mpcg_csr_t* A, const doub
     if (e0) cudaEventDestroy(e0);
     return MPCG_ERR_CUDA;
   }
-  int32_t status = MPCG_OK;
+  if (ms_out)
+    for (int k = 0; k < MPCG_TUNE_RUNS; ++k) ms_out[k] = -1.0f;
+  // One timed batch call; the records copied to `rec`.
+  std::vector<mpcg_result_t> rec(nsys);
+  auto timed = [&](const mpcg_options_t& o, float* ms) -> int32_t {
+    if (cudaEventRecord(e0, st) != cudaSuccess) return MPCG_ERR_CUDA;
+    const int32_t s = mpcg_solve_batch(nsys, A, b, x, sample, &o, ws, ws_bytes, res, st);
+    if (s != MPCG_OK) return s;
+    if (cudaEventRecord(e1, st) != cudaSuccess ||
+        cudaMemcpyAsync(rec.data(), res, sizeof(mpcg_result_t) * (size_t)nsys, cudaMemcpyDefault,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      return MPCG_ERR_CUDA;
+    return MPCG_OK;
+  };
+  std::vector<int> nv(nsys);
+  std::vector<double> work(nsys);
+  for (int i = 0; i < nsys; ++i) {
+    nv[i] = A[i].n;
+    work[i] = work_of(A[i].n, A[i].nnz);
+  }
+  const int smem = team_smem((const void*)k_batch<1>, 1);
+  const int grid = smem < 0 ? 0 : batch_grid(opts->grid_blocks, smem);
+  int32_t status = grid > 0 ? MPCG_OK : MPCG_ERR_CUDA;
   int best = -1;
   float best_ms = 0.0f;
+  std::vector<SysTimes> T(nsys);
+  for (SysTimes& t : T)
+    for (int c = 0; c < kTeamClasses; ++c) {
+      t.s1[c] = t.s2[c] = -1.0;
+      t.n1[c] = t.n2[c] = 0;
+    }
+  std::vector<double> key(nsys, 0.0);  // block-time under the best uniform candidate
   for (int k = 0; k < MPCG_TUNE_CANDIDATES && status == MPCG_OK; ++k) {
     mpcg_options_t o = *opts;
     o.team_rows = kCand[k];
+    o.team_rows_sys = nullptr;
     float ms = -1.0f;
-    if (cudaEventRecord(e0, st) != cudaSuccess) {
-      status = MPCG_ERR_CUDA;
-      break;
-    }
-    status = mpcg_solve_batch(nsys, A, b, x, sample, &o, ws, ws_bytes, res, st);
+    status = timed(o, &ms);
     if (status != MPCG_OK) break;
-    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-      status = MPCG_ERR_CUDA;
-      break;
-    }
     if (ms_out) ms_out[k] = ms;
-    if (best < 0 || ms < best_ms) {
+    const bool better = best < 0 || ms < best_ms;
+    if (better) {
       best = k;
       best_ms = ms;
+    }
+    for (int i = 0; i < nsys; ++i) {
+      const mpcg_result_t& r = rec[i];
+      int c = 0;
+      while (c < kTeamClasses - 1 && (1 << c) < r.team_blocks) ++c;
+      const long long a = (long long)(r.t_fp32_ns - r.t_start_ns);
+      const long long b2 = (long long)(r.t_end_ns - r.t_stage2_ns);
+      const double s1 = (double)(a > 0 ? a : 0), s2 = (double)(b2 > 0 ? b2 : 0);
+      SysTimes& t = T[i];
+      t.s1[c] = (t.n1[c] * std::max(t.s1[c], 0.0) + s1) / (t.n1[c] + 1);
+      t.s2[c] = (t.n2[c] * std::max(t.s2[c], 0.0) + s2) / (t.n2[c] + 1);
+      ++t.n1[c];
+      ++t.n2[c];
+      if (better) key[i] = (double)(1 << c) * (s1 + s2);
+    }
+  }
+  if (status == MPCG_OK) {
+    *team_rows_out = kCand[best];
+    if (team_rows_sys_out) {
+      std::vector<int32_t> rows = per_system_rows(T, key, nv.data(), work, grid, kCand,
+                                                  MPCG_TUNE_CANDIDATES, best, !opts->fp64_only);
+      mpcg_options_t o = *opts;
+      o.team_rows = kCand[best];
+      o.team_rows_sys = rows.data();
+      float ms = -1.0f;
+      status = timed(o, &ms);
+      if (status == MPCG_OK) {
+        if (ms_out) ms_out[MPCG_TUNE_CANDIDATES] = ms;
+        // keep the per-system choice only if it measured faster
+        for (int i = 0; i < nsys; ++i) team_rows_sys_out[i] = ms < best_ms ? rows[i] : kCand[best];
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (status == MPCG_OK) *team_rows_out = kCand[best];
   return status;
 }

@@ -61,6 +61,7 @@ struct Ctl {
   int x32_src;     // stage-1 result: -1 = x32, s >= 0 = snapshot slot s
   // device clock marks (ns)
   unsigned long long t_start, t_prep, t_features, t_fp32, t_fp64, t_end;
+  unsigned long long t_s2;  // team kernels: start of the double-precision stage (0: not marked)
   int bfs_starts;  // 2BFS runs for l~ (the repeated 2BFS of Sec. 6; 1 = the single run)
   double rz;       // r^T z of the preconditioned single-precision stage (carried to Continue)
   const volatile int* cancel;  // the caller's cancel word (option `cancel`), or null
@@ -71,8 +72,10 @@ struct Ctl {
   long long nreached;
   // Column format of the sliced layout: 1 = int16 offsets (column - row), set
   // by the fill when every stored entry's offset fits; 0 = int32 columns.
+  // (Team workspaces keep the int32 columns and add the int16 copy.)
   int col16;
-  int colwide;  // some stored entry's offset does not fit in int16
+  int colwide;  // some stored entry's offset does not fit in int16, or 32-bit columns asked for
+  int colbits;  // 16 or 32 once the fill has written the layout, else 0 (result record)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -84,6 +87,7 @@ struct Ws {
   uint32_t* slice_w;     // width | overflow flag
   int32_t* slice_ptr;    // [nslices + 1] element offsets
   int32_t* scol;         // sliced column indices (int32), or int16 offsets (Ctl::col16)
+  int16_t* scol16;       // team workspaces: 16-bit offsets beside scol (Ctl::col16)
   float* sv32;           // sliced values, single
   double* sv64;          // sliced values, double
   float *b32, *x32, *r32, *d32a, *d32b, *q32;

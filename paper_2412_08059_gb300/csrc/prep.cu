@@ -59,6 +59,9 @@ size_t carve(const Dims& d, char* base, Ws* ws) {
   w.label = (int32_t*)take(sizeof(int32_t) * n);
   w.ckey = (unsigned long long*)take(sizeof(unsigned long long) * n);
   w.snap = (float*)take(sizeof(float) * 6 * n);
+  // team kernels (batched solve, server): a 16-bit copy of the columns for
+  // the staged single-precision SpMV
+  w.scol16 = (int16_t*)take(sizeof(int16_t) * P);
   w.bytes = off;
   if (ws) *ws = w;
   return off;
@@ -92,6 +95,7 @@ __global__ void k_init(Ctl* c, int n, int nnz, int nslices, int wcap, mpcg_optio
   c->max_restarts = o.max_true_restarts > 0 ? o.max_true_restarts : 0;
   c->tol_relative = o.tol_relative ? 1 : 0;
   c->acc32 = o.acc32 ? 1 : 0;
+  c->colwide = o.spmv_variant == 1 ? 1 : 0;  // 32-bit columns asked for
   c->eps1 = o.eps1;
   c->eps2 = o.eps2;
   c->timeout_ns = (long long)(o.timeout_ms > 0 ? o.timeout_ms : 20000) * 1000000ll;
@@ -243,7 +247,10 @@ __global__ void k_fill(Ctl* c, const int32_t* __restrict__ rp, const int32_t* __
   const int s = i >> 5, lane = i & 31;
   if (s >= nslices) return;
   const bool c16 = c->colwide == 0;
-  if (i == 0) c->col16 = c16 ? 1 : 0;
+  if (i == 0) {
+    c->col16 = c16 ? 1 : 0;
+    c->colbits = c16 ? 16 : 32;
+  }
   int16_t* scol16 = reinterpret_cast<int16_t*>(scol);
   const int w = (int)(slice_w[s] & ~kOverflowBit);
   const int base = slice_ptr[s] + lane;
@@ -344,6 +351,9 @@ __global__ void k_finalize(const Ctl* c, mpcg_result_t* res, mpcg_features_t* fe
     res->t_fp64_ns = c->t_fp64 ? c->t_fp64 : res->t_fp32_ns;
     res->t_end_ns = now;
     res->t_prep_ns = t0;
+    res->t_stage2_ns = c->t_s2 ? c->t_s2 : res->t_fp32_ns;
+    res->spmv_cols = c->colbits;
+    res->team_blocks = 0;
   }
   if (feat) {
     feat->n = (double)c->n;

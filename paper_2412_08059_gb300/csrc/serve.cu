@@ -37,7 +37,7 @@ struct ServeArgs {
 
 // Set-up of a new system (as in the batched solve).  Returns false if the
 // launch aborted.
-__device__ bool slot_setup(Team& t, const BatchSys& s, const BatchArgs& a, int& red) {
+__device__ bool slot_setup(Team& t, const BatchSys& s, const BatchArgs& a, int& red, bool narrow) {
   Ctl* ctl = s.w.ctl;
   sys_init(t, s, a);
   if (!team_sync(t)) return false;
@@ -46,7 +46,7 @@ __device__ bool slot_setup(Team& t, const BatchSys& s, const BatchArgs& a, int& 
   if (sys_status(s) != 0) return true;
   if (t.rank == 0) block_scan_slices(s.w.slice_w, s.w.slice_ptr, s.nslices);
   if (!team_sync(t)) return false;
-  sys_fill(t, s);
+  sys_fill(t, s, narrow);
   double p = 0.0;
   for (int i = team_tid(t); i < s.n; i += team_threads(t)) p = __fma_rn(s.b[i], s.b[i], p);
   double bb;
@@ -102,7 +102,7 @@ __device__ bool slot_advance(Team& t, const BatchSys& s, int* phase_p, const Bat
   int red = 0;
   bool done = true;
   if (ph == kPhNew) {
-    if (!slot_setup(t, s, a, red)) return false;
+    if (!slot_setup(t, s, a, red, kStage)) return false;
     if (sys_status(s) != 0) {
       ph = kPhDone;
     } else if (*reinterpret_cast<volatile int*>(&ctl->trivial)) {  // b = 0: x = 0

@@ -13,6 +13,7 @@
 #pragma once
 #include <math.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "bfs_block.cuh"
@@ -249,6 +250,7 @@ static __device__ void sys_init(const Team& t, const BatchSys& s, const BatchArg
     c->max_restarts = o.max_true_restarts > 0 ? o.max_true_restarts : 0;
     c->tol_relative = o.tol_relative ? 1 : 0;
     c->acc32 = o.acc32 ? 1 : 0;
+    c->colwide = o.spmv_variant == 1 ? 1 : 0;  // 32-bit columns asked for
     c->eps1 = o.fp64_only ? 0.0 : (a.auto_eps1 ? -1.0 : o.eps1);
     c->eps2 = s.eps2;
     c->timeout_ns = (long long)(o.timeout_ms > 0 ? o.timeout_ms : 20000) * 1000000ll;
@@ -258,7 +260,10 @@ static __device__ void sys_init(const Team& t, const BatchSys& s, const BatchArg
   }
 }
 
-// CSR check, b~ = float32(b), slice widths (one warp per slice).
+// CSR check, b~ = float32(b), slice widths (one warp per slice).  Also
+// notes whether some entry kept in the slices (the first wcap of its row)
+// lies more than 32767 columns from its row: the fill then stores 32-bit
+// columns, otherwise 16-bit offsets from the row.
 static __device__ void sys_rows(const Team& t, const BatchSys& s) {
   Ctl* c = s.w.ctl;
   const int lane = threadIdx.x & 31;
@@ -267,7 +272,7 @@ static __device__ void sys_rows(const Team& t, const BatchSys& s) {
   const int32_t* col = s.A.col;
   for (int base = team_tid(t) - lane; base < s.nslices * kSlice; base += T) {
     const int i = base + lane;
-    int len = 0, ok = 1;
+    int len = 0, ok = 1, wide = 0;
     if (i < s.n) {
       const int a0 = rp[i], e = rp[i + 1];
       if (a0 < 0 || e < a0 || e > s.nnz) {
@@ -281,6 +286,7 @@ static __device__ void sys_rows(const Team& t, const BatchSys& s) {
             ok = 0;
             break;
           }
+          if (k - a0 < s.wcap && (cc - i > 32767 || i - cc > 32768)) wide = 1;
           prev = cc;
         }
       }
@@ -296,6 +302,7 @@ static __device__ void sys_rows(const Team& t, const BatchSys& s) {
     const int wmax = __reduce_max_sync(0xffffffffu, w);
     const int any_ovf = __any_sync(0xffffffffu, len > s.wcap);
     if (lane == 0) s.w.slice_w[i >> 5] = (uint32_t)wmax | (any_ovf ? kOverflowBit : 0u);
+    if (__any_sync(0xffffffffu, wide) && lane == 0) atomicExch(&c->colwide, 1);
   }
 }
 
@@ -343,10 +350,20 @@ static __device__ void block_scan_slices(const uint32_t* slice_w, int32_t* slice
 }
 
 // Sliced arrays: entry k of row i at slice_ptr[s] + 32 k + (i mod 32); short
-// rows padded with value 0 and their own column.
-static __device__ void sys_fill(const Team& t, const BatchSys& s) {
+// rows padded with value 0 and their own column, the rows past n that fill
+// the last slice with value 0 and column 0 (n - 1 in the 16-bit copy).
+// narrow: the launch's single-precision SpMV is the staged one, which also
+// gets a copy of the columns as 16-bit offsets from the row (Ctl::col16)
+// when sys_rows found that every one fits and 32-bit columns were not asked
+// for.  Both copies hold the same entries in the same order.
+static __device__ void sys_fill(const Team& t, const BatchSys& s, bool narrow) {
   const int T = team_threads(t);
   const int32_t* rp = s.A.row_ptr;
+  const bool c16 = narrow && *reinterpret_cast<volatile int*>(&s.w.ctl->colwide) == 0;
+  if (t.rank == 0 && threadIdx.x == 0) {
+    s.w.ctl->col16 = c16 ? 1 : 0;
+    s.w.ctl->colbits = c16 ? 16 : 32;
+  }
   for (int i = team_tid(t); i < s.nslices * kSlice; i += T) {
     const int sl = i >> 5, lane = i & 31;
     const int w = (int)(s.w.slice_w[sl] & ~kOverflowBit);
@@ -358,16 +375,16 @@ static __device__ void sys_fill(const Team& t, const BatchSys& s) {
     }
     for (int k = 0; k < w; ++k) {
       const int e = base + kSlice * k;
+      double v = 0.0;
+      int cc = i < s.n ? i : 0;
       if (k < len) {
-        const double v = s.A.val[a0 + k];
-        s.w.scol[e] = s.A.col[a0 + k];
-        s.w.sv64[e] = v;
-        s.w.sv32[e] = (float)v;
-      } else {
-        s.w.scol[e] = i < s.n ? i : 0;
-        s.w.sv64[e] = 0.0;
-        s.w.sv32[e] = 0.0f;
+        v = s.A.val[a0 + k];
+        cc = s.A.col[a0 + k];
       }
+      s.w.scol[e] = cc;
+      if (c16) s.w.scol16[e] = (int16_t)((i < s.n ? cc : s.n - 1) - i);
+      s.w.sv64[e] = v;
+      s.w.sv32[e] = (float)v;
     }
   }
 }
@@ -410,14 +427,23 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Copy one slice's (column, value) pairs -- 32 w contiguous elements from
 // element p0 (a multiple of 32, so every 16-byte copy is aligned) -- into a
-// warp's stage.
-template <typename T>
-__device__ __forceinline__ void stage_slice(int32_t* cdst, T* vdst, const int32_t* sc, const T* sv,
-                                            int p0, int w, int lane) {
+// warp's stage.  CT: 32-bit columns or 16-bit offsets.
+template <typename T, typename CT>
+__device__ __forceinline__ void stage_slice(CT* cdst, T* vdst, const CT* sc, const T* sv, int p0,
+                                            int w, int lane) {
   const int E = kSlice * w;
-  for (int q = lane; q < E / 4; q += 32) cp_async16(cdst + 4 * q, sc + p0 + 4 * q);
+  constexpr int cper = 16 / (int)sizeof(CT);
+  for (int q = lane; q < E / cper; q += 32) cp_async16(cdst + cper * q, sc + p0 + cper * q);
   constexpr int per = 16 / (int)sizeof(T);
   for (int q = lane; q < E / per; q += 32) cp_async16(vdst + per * q, sv + p0 + per * q);
+}
+
+// Column of a stored entry of row i: a 32-bit column, or a 16-bit offset
+// from the row.
+template <bool C16>
+__device__ __forceinline__ int col_at(typename std::conditional<C16, int16_t, int32_t>::type c, int i) {
+  if constexpr (C16) return i + (int)c;
+  else return c;
 }
 
 // SpMV over the team's slices, pairs staged in shared memory (the single-
@@ -434,19 +460,23 @@ __device__ __forceinline__ void stage_slice(int32_t* cdst, T* vdst, const int32_
 // Slices wider than kTeamFastW, or with an overflow tail, read their pairs
 // from global memory instead.  The metadata of 32 of the warp's slices is
 // loaded at once (one slice per lane).
-template <typename T, class Gather, class Pre, class Row>
+template <typename T, bool C16, class Gather, class Pre, class Row>
 __device__ __forceinline__ void team_spmv_staged(const Team& t, const BatchSys& s, Gather G, Pre P,
                                                  Row Rw) {
   static_assert(sizeof(T) == 4, "the stages hold 4-byte values");
+  using CT = typename std::conditional<C16, int16_t, int32_t>::type;
   constexpr int kS = kSpmvStep;
   constexpr int kE = kSlice * kTeamFastW;      // elements of a staged slice
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gw = team_warp(t), W = team_warps(t);
   const T* sv = bvals<T>(s);
-  const int32_t* sc = s.w.scol;
-  int32_t* cbuf = reinterpret_cast<int32_t*>(team_dyn + warp * kStageWarpBytes);  // [2][kS][kE]
-  T* vbuf = reinterpret_cast<T*>(cbuf + 2 * kS * kE);                             // [2][kS][kE]
+  const CT* sc;
+  if constexpr (C16) sc = s.w.scol16;
+  else sc = s.w.scol;
+  int32_t* stage = reinterpret_cast<int32_t*>(team_dyn + warp * kStageWarpBytes);
+  CT* cbuf = reinterpret_cast<CT*>(stage);            // [2][kS][kE]
+  T* vbuf = reinterpret_cast<T*>(stage + 2 * kS * kE);  // [2][kS][kE]
   for (int base = gw; base < s.nslices; base += 32 * W) {
     const int mine = base + lane * W;
     uint32_t mwf = 0u;
@@ -467,7 +497,7 @@ __device__ __forceinline__ void team_spmv_staged(const Team& t, const BatchSys& 
           const int w = (int)(wf & ~kOverflowBit);
           if (!(wf & kOverflowBit) && w <= kTeamFastW) {
             const int slot = ((step & 1) * kS + u) * kE;
-            stage_slice<T>(cbuf + slot, vbuf + slot, sc, sv, pp, w, lane);
+            stage_slice<T, CT>(cbuf + slot, vbuf + slot, sc, sv, pp, w, lane);
           }
         }
       }
@@ -500,13 +530,14 @@ __device__ __forceinline__ void team_spmv_staged(const Team& t, const BatchSys& 
       for (int u = 0; u < kS; ++u) {
         if (!(wf[u] & kOverflowBit) && w[u] <= kTeamFastW) {
           const int slot = ((step & 1) * kS + u) * kE + lane;
-          const int32_t* cs = cbuf + slot;
+          const CT* cs = cbuf + slot;
           const T* vs = vbuf + slot;
 #pragma unroll
           for (int k = 0; k < kTeamFastW; ++k)
-            if (k < w[u]) a[u] = fma(vs[kSlice * k], G(cs[kSlice * k]), a[u]);
+            if (k < w[u]) a[u] = fma(vs[kSlice * k], G(col_at<C16>(cs[kSlice * k], i[u])), a[u]);
         } else if (step * kS + u < cnt) {
-          for (int k = 0; k < w[u]; ++k) a[u] = fma(sv[p[u] + kSlice * k], G(sc[p[u] + kSlice * k]), a[u]);
+          for (int k = 0; k < w[u]; ++k)
+            a[u] = fma(sv[p[u] + kSlice * k], G(col_at<C16>(sc[p[u] + kSlice * k], i[u])), a[u]);
           if (i[u] < s.n) a[u] = btail<T>(s, i[u], w[u], a[u], G);
         }
       }
@@ -587,11 +618,20 @@ __device__ __forceinline__ void team_spmv_regs(const Team& t, const BatchSys& s,
 // memory they take comes out of the L1 cache that the stage's gathers use
 // (measured on the 512-system batch: the FP64 stage lost more to the
 // smaller L1 than it gained from the staging).
+//
+// The staged SpMV reads the 16-bit copy of the columns when the set-up built
+// one (Ctl::col16; each format has its own copy of the loop); the SpMV from
+// global memory reads the 32-bit columns, so the double-precision loops keep
+// the one form whose schedule was measured.
 template <typename T, bool kStage, class Gather, class Pre, class Row>
 __device__ __forceinline__ void team_spmv(const Team& t, const BatchSys& s, Gather G, Pre P,
                                           Row Rw) {
-  if constexpr (kStage && sizeof(T) == 4) team_spmv_staged<T>(t, s, G, P, Rw);
-  else team_spmv_regs<T>(t, s, G, P, Rw);
+  if constexpr (kStage && sizeof(T) == 4) {
+    if (s.w.ctl->col16) team_spmv_staged<T, true>(t, s, G, P, Rw);
+    else team_spmv_staged<T, false>(t, s, G, P, Rw);
+  } else {
+    team_spmv_regs<T>(t, s, G, P, Rw);
+  }
 }
 
 __device__ __forceinline__ int team_warp(const Team& t) { return t.rank * kBatchWarps + (threadIdx.x >> 5); }
@@ -814,6 +854,7 @@ static __device__ bool sys_cg64(Team& t, const BatchSys& s, int from_zero, int& 
   double* q = s.w.q64;
   const double* b = s.b;
   if (!resume) {
+    if (lead0) ctl->t_s2 = globaltimer();
     for (int sl = gw; sl < s.nslices; sl += W) {
       const int i = sl * kSlice + lane;
       if (i < n) x[i] = from_zero ? 0.0 : (double)s.w.x32[i];
@@ -997,6 +1038,9 @@ static __device__ void sys_finalize(const Team& t, const BatchSys& s) {
   res->t_fp64_ns = c->t_fp64 ? c->t_fp64 : res->t_fp32_ns;
   res->t_end_ns = globaltimer();
   res->t_prep_ns = t0;
+  res->t_stage2_ns = c->t_s2 ? c->t_s2 : res->t_fp32_ns;
+  res->spmv_cols = c->colbits;
+  res->team_blocks = t.size;
 }
 
 // Status of the system as seen after a team barrier (identical in every block).
@@ -1066,8 +1110,10 @@ struct Plan {
 };
 // Teams for a grid of `grid` blocks and the class queues of nsys systems of
 // n rows with estimated work `work` (largest first within a class); a system
-// goes to the smallest team with at most rows_per_block rows per block.
-Plan make_plan(int nsys, const int* n, const double* work, int grid, int rows_per_block);
+// goes to the smallest team with at most rows_per_block rows per block, or
+// rows_sys[i] when that array is given and its entry is positive.
+Plan make_plan(int nsys, const int* n, const double* work, int grid, int rows_per_block,
+               const int32_t* rows_sys = nullptr);
 // Dynamic shared memory of a team launch of `kernel`: kTeamSmem when it runs
 // a single-precision stage (stage1 != 0), else only the scan's kScanSmem.
 // Raises the kernel's limit on the current device; -1 on a CUDA error.

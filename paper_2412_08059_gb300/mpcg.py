@@ -11,6 +11,7 @@ import ctypes as C
 import os
 import threading
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -58,7 +59,8 @@ class Options(C.Structure):
                 ("stage1_only", C.c_int32), ("team_rows", C.c_int32),
                 ("serve_split", C.c_int32), ("bfs_starts", C.c_int32),
                 ("precond", C.c_int32), ("stop_true_residual", C.c_int32),
-                ("cancel", C.c_void_p), ("acc32", C.c_int32)]
+                ("cancel", C.c_void_p), ("acc32", C.c_int32),
+                ("spmv_variant", C.c_int32), ("team_rows_sys", C.c_void_p)]
 
 
 class Result(C.Structure):
@@ -68,7 +70,8 @@ class Result(C.Structure):
                 ("res_fp32", C.c_double), ("res_fp64", C.c_double),
                 ("t_start_ns", C.c_uint64), ("t_features_ns", C.c_uint64),
                 ("t_fp32_ns", C.c_uint64), ("t_fp64_ns", C.c_uint64), ("t_end_ns", C.c_uint64),
-                ("t_prep_ns", C.c_uint64)]
+                ("t_prep_ns", C.c_uint64), ("t_stage2_ns", C.c_uint64), ("spmv_cols", C.c_int32),
+                ("team_blocks", C.c_int32)]
 
     def as_dict(self) -> dict:
         """Fields plus phase durations from the device clock marks: ms_prep (set-up),
@@ -131,7 +134,7 @@ def load(path: str = LIB_PATH):
         L.mpcg_pseudo_diameter.argtypes = [C.POINTER(CsrDesc), P, P, SZ, P]
         L.mpcg_batch_tune.restype = I32
         L.mpcg_batch_tune.argtypes = [I32, P, P, P, C.POINTER(SampleDesc), C.POINTER(Options),
-                                      P, SZ, P, P, C.POINTER(I32), P]
+                                      P, SZ, P, P, C.POINTER(I32), P, P]
         L.mpcg_server_workspace_bytes.restype = SZ
         L.mpcg_server_workspace_bytes.argtypes = [I32, SZ]
         L.mpcg_server_create.restype = I32
@@ -169,10 +172,16 @@ def status_string(st: int) -> str:
 
 
 def options(**kw) -> Options:
+    """Default options with the given fields set.  team_rows_sys takes a
+    sequence of per-system rows per block (kept alive by the returned object)."""
     o = load().mpcg_options_default()
     for k, v in kw.items():
         if not hasattr(o, k):
             raise KeyError(k)
+        if k == "team_rows_sys" and v is not None and not isinstance(v, int):
+            arr = np.ascontiguousarray(v, dtype=np.int32)
+            o._team_rows_sys = arr
+            v = arr.ctypes.data
         setattr(o, k, v)
     return o
 
@@ -352,22 +361,29 @@ def solve_batch_async(mats: list[DeviceCSR], bs: list, xs: list, opts: Options,
 
 
 TUNE_CANDIDATES = 4
+TUNE_RUNS = TUNE_CANDIDATES + 1
 
 
 def batch_tune(mats: list[DeviceCSR], bs: list, xs: list, opts: Options, ws: torch.Tensor,
-               res: torch.Tensor, sample: DeviceSample | None = None, stream=None):
-    """mpcg_batch_tune: (fastest team_rows, milliseconds per candidate).  Synchronises."""
+               res: torch.Tensor, sample: DeviceSample | None = None, stream=None,
+               per_system: bool = False):
+    """mpcg_batch_tune: (fastest uniform team_rows, milliseconds per timed call
+    [4 candidates, then the per-system call or -1]), plus with per_system the
+    per-system rows per block (numpy int32).  Synchronises."""
     n = len(mats)
     descs = (CsrDesc * n)(*[m.desc for m in mats])
     bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
     xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
     best = C.c_int32(0)
-    ms = (C.c_float * TUNE_CANDIDATES)()
+    ms = (C.c_float * TUNE_RUNS)()
+    rows = np.zeros(n, dtype=np.int32)
     st = load().mpcg_batch_tune(n, descs, bp, xp,
                                 C.byref(sample.desc) if sample is not None else None,
                                 C.byref(opts), _ptr(ws), ws.numel(), _ptr(res), _stream(stream),
-                                C.byref(best), ms)
+                                C.byref(best), rows.ctypes.data if per_system else None, ms)
     _check(st, "mpcg_batch_tune")
+    if per_system:
+        return best.value, list(ms), rows
     return best.value, list(ms)
 
 

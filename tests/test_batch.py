@@ -182,14 +182,73 @@ def test_batch_tune_picks_a_candidate_and_results_hold(mp):
     res = mp.result_buffer(len(mats))
     opts = mp.options(eps1=1e-4)
     best, ms = mp.batch_tune(dmats, dbs, xs, opts, ws, res, None)
-    assert best in (8192, 16384, 32768, 65536)
-    assert len(ms) == 4 and all(t > 0 for t in ms)
-    assert ms[(8192, 16384, 32768, 65536).index(best)] == min(ms)
+    assert best in CANDIDATES
+    assert len(ms) == 5 and all(t > 0 for t in ms[:4]) and ms[4] == -1
+    assert ms[CANDIDATES.index(best)] == min(ms[:4])
     # a batch with the chosen granularity still matches the oracle
     xs2, rs = run_batch(mp, mats, bs, None, eps1=1e-4, team_rows=best)
     for A, b, x, r in zip(mats, bs, xs2, rs):
         xo, ro = oracle.solve(A, b, eps1=1e-4)
         parity(r, ro, x, xo)
+
+
+CANDIDATES = (8192, 16384, 32768, 65536)
+
+
+@pytest.mark.parametrize("mode", ["mixed", "fp64"])
+def test_batch_tune_per_system_and_results_hold(mp, mode):
+    """The per-system choice: every entry is a candidate; it is kept only if
+    its own timed call beat the best uniform candidate (else every entry is
+    that candidate); a batch run with it matches the oracle."""
+    mats = mixed_systems()
+    bs = [synth.rhs(A, seed=140 + i)[1] for i, A in enumerate(mats)]
+    dmats = [mp.DeviceCSR.from_host(A) for A in mats]
+    dbs = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in bs]
+    xs = [torch.empty(A.n, dtype=torch.float64, device="cuda") for A in mats]
+    ws = torch.empty(mp.batch_workspace_bytes(dmats), dtype=torch.uint8, device="cuda")
+    res = mp.result_buffer(len(mats))
+    kw = dict(eps1=1e-5) if mode == "mixed" else dict(fp64_only=1)
+    best, ms, rows = mp.batch_tune(dmats, dbs, xs, mp.options(**kw), ws, res, None,
+                                   per_system=True)
+    assert best in CANDIDATES and len(rows) == len(mats)
+    assert all(int(r) in CANDIDATES for r in rows)
+    assert ms[4] > 0
+    if ms[4] >= ms[CANDIDATES.index(best)]:
+        assert all(int(r) == best for r in rows)
+    xs2, rs = run_batch(mp, mats, bs, None, team_rows=best, team_rows_sys=rows, **kw)
+    for A, b, x, r in zip(mats, bs, xs2, rs):
+        if mode == "mixed":
+            xo, ro = oracle.solve(A, b, eps1=1e-5)
+            parity(r, ro, x, xo)
+        else:
+            xo, it, st = oracle.cg64(A, b, 1e-10)
+            assert st == 0 and r["status"] >= 0 and r["n1"] == 0 and close_count(r["n2"], it)
+            assert r["true_rel_resid"] <= 1e-10
+            assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
+        assert r["t_start_ns"] <= r["t_stage2_ns"] <= r["t_end_ns"]
+
+
+def test_batch_per_system_team_sizes(mp):
+    """Per-system rows per block that put neighbouring systems in teams of
+    different sizes (1 to 8 blocks): every system still matches the oracle.
+    A team of several blocks sums its partials in another order than one
+    block, so x~ ends stage 1 with other last bits, and an FP64 stage that
+    meets eps2 after a flat stretch of its residual moves by up to two
+    iterations (the 37 x 29 grid on a 2-block team: N2 38 against the
+    oracle's 40), below 2 % only from 100 iterations on: the counts are held
+    to 2 % or 2 iterations here; status, x and the true residual keep the
+    full bar."""
+    mats = mixed_systems()
+    bs = [synth.rhs(A, seed=160 + i)[1] for i, A in enumerate(mats)]
+    rows = [CANDIDATES[i % 4] // 8 if i % 3 == 0 else CANDIDATES[i % 4] for i in range(len(mats))]
+    xs, rs = run_batch(mp, mats, bs, None, eps1=1e-5, team_rows_sys=rows)
+    near = lambda a, c: abs(a - c) <= max(2, int(0.02 * max(a, c)))
+    for A, b, x, r in zip(mats, bs, xs, rs):
+        xo, ro = oracle.solve(A, b, eps1=1e-5)
+        assert r["status"] == ro["status"], (A.n, r, ro)
+        assert near(r["n1"], ro["n1"]) and near(r["n2"], ro["n2"]), (A.n, r, ro)
+        assert r["true_rel_resid"] <= 1e-10
+        assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
 
 
 def test_batch_abort_reports_timeout_not_stale_records(mp):
@@ -253,3 +312,38 @@ def test_batch_call_does_not_wait_for_earlier_stream_work(mp):
     for k in [0, 3, 5, 6, 205]:
         xo, ro = oracle.solve(mats[k], bs[k], eps1=1e-5)
         parity(rs[k], ro, xs[k].cpu().numpy(), xo)
+
+
+def test_spmv_column_formats_give_identical_bits(mp):
+    """Option spmv_variant: the sliced layout with 16-bit offsets from the row
+    (chosen per system when every kept entry fits) and with 32-bit columns sum
+    the same entries in the same order, so every result is bit-identical.
+    Grids and a banded matrix fit; a random graph and a star past 32768 rows
+    do not, and keep 32-bit columns under the default too.  A pure-FP64
+    batch has no single-precision SpMV and reports 32."""
+    mats = [synth.laplacian_3d(32), synth.laplacian_2d(200, 200),
+            synth.banded(1000, 29, 0.6, 1.1, seed=7),
+            synth.random_regular_laplacian(40000, 8, 1e-3, seed=5), synth.star(40001, 1.1)]
+    fits = [True, True, True, False, False]
+    bs = [synth.rhs(A, seed=300 + i)[1] for i, A in enumerate(mats)]
+    feat, cls = sample_over(mats, seed=5)
+    S = mp.DeviceSample(feat, cls)
+    keys = ("status", "n1", "n2", "cls", "k0_done", "restarts", "eps1", "true_rel_resid",
+            "pdiam", "v", "res_fp32", "res_fp64")
+    for kw in (dict(), dict(fp64_only=1), dict(eps1=1e-5)):
+        s = None if kw else S
+        xa, ra = run_batch(mp, mats, bs, s, **kw)
+        xb, rb = run_batch(mp, mats, bs, s, spmv_variant=1, **kw)
+        for A, f, x0, x1, r0, r1 in zip(mats, fits, xa, xb, ra, rb):
+            assert r0["status"] >= 0, (A.n, r0)
+            narrow = f and "fp64_only" not in kw
+            assert r0["spmv_cols"] == (16 if narrow else 32) and r1["spmv_cols"] == 32, (A.n, kw)
+            assert np.array_equal(x0, x1), (A.n, kw)
+            assert all(r0[k] == r1[k] for k in keys), (A.n, kw, r0, r1)
+    for A, f, b in zip(mats, fits, bs):  # the single-system kernels
+        dA, db = mp.DeviceCSR.from_host(A), torch.from_numpy(b).cuda()
+        x0, r0 = mp.solve(dA, db, S)
+        x1, r1 = mp.solve(dA, db, S, spmv_variant=1)
+        assert r0["spmv_cols"] == (16 if f else 32) and r1["spmv_cols"] == 32, A.n
+        assert torch.equal(x0, x1), A.n
+        assert all(r0[k] == r1[k] for k in keys), (A.n, r0, r1)
