@@ -294,10 +294,12 @@ int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const double* const*
  * fastest to *team_rows_out (host).  With team_rows_sys_out (host int32[nsys],
  * nullable) it then picks a granularity per system from those runs' device
  * clock marks: each system's busy time and block-time (team blocks x busy
- * time) under every candidate; under a bound T on one system's time each
- * system takes its cheapest candidate within T, and the T that minimises
- * max(T, summed block-time / (grid x the best uniform run's block
- * efficiency)) is kept.  One more timed call with that choice
+ * time) under every candidate.  A host simulation of the launch (the
+ * planner's teams taking systems from their class queues, then from the
+ * smaller classes, as the kernel does) estimates the batch; starting from
+ * the best uniform candidate, the systems with the largest block-time (at
+ * most 256) each move to another candidate when that shortens the
+ * simulated batch.  One more timed call with that choice
  * (opts->team_rows_sys) decides: if it is faster than the best uniform
  * candidate the per-system choice is written, else the uniform best for
  * every system.  ms_out (host float[MPCG_TUNE_RUNS], nullable): each

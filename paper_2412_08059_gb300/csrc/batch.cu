@@ -544,9 +544,11 @@ double simulate_launch(const Plan& P, const std::vector<SysTimes>& T, int stage)
 }
 
 // Per-system team granularity: starting from the best uniform candidate,
-// each system in turn (largest block-time first) moves to another candidate
+// each system in turn (largest block-time first; at most kTuneMoves of them,
+// which bounds the host time for large batches) moves to another candidate
 // when that shortens the simulated batch (the planner re-run on the new
 // choice, then each launch simulated); two passes.
+constexpr int kTuneMoves = 256;
 std::vector<int32_t> per_system_rows(const std::vector<SysTimes>& T, const std::vector<double>& order_key,
                                      const int* nv, const std::vector<double>& work, int grid,
                                      const int* cand, int K, int best, bool two_launch) {
@@ -559,6 +561,7 @@ std::vector<int32_t> per_system_rows(const std::vector<SysTimes>& T, const std::
   std::vector<int> idx(nsys);
   for (int i = 0; i < nsys; ++i) idx[i] = i;
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return order_key[a] > order_key[b]; });
+  if ((int)idx.size() > kTuneMoves) idx.resize(kTuneMoves);
   double cur = span();
   for (int pass = 0; pass < 2; ++pass)
     for (int i : idx)
