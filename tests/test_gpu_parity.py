@@ -341,6 +341,25 @@ def test_algorithm_ii_classes_outside_two_to_seven(mp, classes):
     parity(r, ro, x.cpu().numpy(), xo)
 
 
+@pytest.mark.parametrize("seed", [2, 10])
+def test_algorithm_ii_more_classes_than_snapshots(mp, seed):
+    """A sample with labels t = 0 .. 11 on a 5000-vertex path with a_ii = 2 deg:
+    stage 1 meets the candidate eps1 within a few dozen iterations, long
+    before the 2BFS of 4999 levels ends, and keeps only six snapshots of x~,
+    so past the sixth crossing it waits for the label (here t = 8 and 10);
+    label, eps1, l~ and the solve match the oracle."""
+    A = synth.path(5000, 2.0)
+    xs, b = synth.rhs(A, seed=13)
+    feat, cls = synth.random_sample(240, seed=seed, classes=tuple(range(12)))
+    feat[:, 0] = np.linspace(0.5, 2.0, 240) * A.n
+    feat[:, 1] = np.linspace(0.5, 2.0, 240)[::-1] * A.nnz
+    S = mp.DeviceSample(feat, cls)
+    x, r = mp.solve(mp.DeviceCSR.from_host(A), torch.from_numpy(b).cuda(), S)
+    xo, ro = oracle.solve(A, b, S=(feat, cls))
+    assert r["cls"] == ro["cls"] and r["eps1"] == ro["eps1"] and r["pdiam"] == ro["pdiam"]
+    parity(r, ro, x.cpu().numpy(), xo)
+
+
 def _coupled_band(n, D, sigma=0.1):
     """Tridiagonal SPD matrix plus a symmetric coupling at column offset +-D:
     4 + sigma on the diagonal, -1 off it (strictly diagonally dominant)."""
