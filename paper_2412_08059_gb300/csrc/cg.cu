@@ -205,11 +205,15 @@ __device__ __forceinline__ bool cgrid_barrier(Ctl* ctl, int slot, unsigned long 
 template <int NC>
 __device__ __forceinline__ double cgrid_total(double block_part, double* partials, int& red,
                                               Ctl* ctl, int slot, unsigned long long& round,
-                                              CShared<NC>& S, bool& ok, bool f32 = false) {
+                                              CShared<NC>& S, bool& ok, bool f32 = false,
+                                              double* extra = nullptr) {
   double* buf = partials + (red & 1) * kMaxGrid;
   ++red;
   if (threadIdx.x == 0) buf[blockIdx.x] = block_part;
   ok = cgrid_barrier<NC>(ctl, slot, round, &S.ok);
+  // extra (thread 0): the slot after the partials, which block 0 wrote before
+  // the barrier; loaded beside them rather than after the sum
+  if (extra && threadIdx.x == 0) *extra = buf[gridDim.x];
   double s = 0.0;
   if (threadIdx.x < 32) {
     if (f32) {  // option acc32: the blocks' float partials summed in float
@@ -1456,12 +1460,18 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
   // thread 0 only:
   double vsum = 0.0;
   int k0done = 0, in_k0 = 1, cls = -1, nslots = 0;
-  int nt[16], snap_it[kSnapSlots];
-  double res_at[16];
-  for (int t = 0; t < 16; ++t) {
-    nt[t] = -1;
-    res_at[t] = 0.0;
-  }
+  // Thread 0's record of the candidate crossings, in shared memory: as a
+  // thread-local array it lived in local memory, whose lines the gathers
+  // evict from L1, so the decision at every loop head waited on L2 round
+  // trips (measured at 128^3: the loop head took 3.65 us per iteration,
+  // 1.9 us with the record here, against 0.55 us in k_cg32).
+  __shared__ int nt[16], snap_it[kSnapSlots];
+  __shared__ double res_at[16];
+  if (lead)
+    for (int t = 0; t < 16; ++t) {
+      nt[t] = -1;
+      res_at[t] = 0.0;
+    }
   enum { kGoOn = 0, kEnd = 1, kFailed = 2, kBrokeDown = 3, kEndForLabel = 4 };
   int broke = 0;
   // thread 0: stop thresholds of eps2 (slot 16) and of every candidate
@@ -1605,9 +1615,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
       double* buf = a.partials + (red & 1) * kMaxGrid;
       const double bp = block_ff(prr, S, f32);
       if (lead0) buf[gridDim.x] = (double)label_now;
-      const double rrn = cgrid_total(bp, a.partials, red, ctl, a.slot, round, S, ok, f32);
+      double label_slot = 0.0;
+      const double rrn = cgrid_total(bp, a.partials, red, ctl, a.slot, round, S, ok, f32, &label_slot);
       if (lead) {
-        const int label = (int)buf[gridDim.x];
+        const int label = (int)label_slot;
         int d3 = kGoOn;
         if (label < 0) {
           d3 = kFailed;
