@@ -1435,7 +1435,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
     ff_add_prod(acc, bi, bi, f32);
   }
   double rr, bnorm;
-  unsigned cmask = 0u;  // thread 0
+  // thread 0: the classes present in the sample, and those met so far (in
+  // shared memory: registers are scarce here)
+  __shared__ unsigned cmask, met;
   {
     double* buf = a.partials + (red & 1) * kMaxGrid;
     const double bp = block_ff(acc, S, f32);  // all consumer warps past the mask
@@ -1443,6 +1445,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
     const double tot = cgrid_total(bp, a.partials, red, ctl, a.slot, round, S, ok, f32);
     if (lead) {
       cmask = (unsigned)buf[gridDim.x];
+      met = 0u;
       S.rr = tot;
       S.val = sqrt(tot);
       if (lead0) {
@@ -1510,18 +1513,24 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_stage1(Stage1Args sa) {
           }
         }
         if (!in_k0) {
-          bool fresh = false, all = true;
-          for (int t = 0; t < 16; ++t) {
-            if (!((cmask >> t) & 1u)) continue;
-            if (nt[t] < 0 &&
-                (rr <= s_lo[t] ||
-                 (rr <= s_hi[t] && stop_measure(rr, bnorm, rel) <= pow10_neg(t)))) {
-              nt[t] = it;
-              res_at[t] = stop_measure(rr, bnorm, rel);
-              fresh = true;
+          // Candidates are met in the order of t (a smaller eps1 has the
+          // smaller threshold): while r^T r stays above the upper bracket of
+          // the lowest present class not met yet, none is met this iteration.
+          bool fresh = false;
+          const unsigned open = cmask & ~met;
+          if (open && rr <= s_hi[__ffs(open) - 1]) {
+            for (int t = 0; t < 16; ++t) {
+              if (!((open >> t) & 1u)) continue;
+              if (rr <= s_lo[t] ||
+                  (rr <= s_hi[t] && stop_measure(rr, bnorm, rel) <= pow10_neg(t))) {
+                nt[t] = it;
+                res_at[t] = stop_measure(rr, bnorm, rel);
+                met |= 1u << t;
+                fresh = true;
+              }
             }
-            if (nt[t] < 0) all = false;
           }
+          const bool all = (cmask & ~met) == 0u;  // every present class is met
           if (cls < 0 && (all || it >= max1)) {
             // Stage 1 ends here whatever the label (every present class is
             // met, or the cap): the loop ends, and the consumers help the
