@@ -262,8 +262,8 @@ static __device__ void sys_init(const Team& t, const BatchSys& s, const BatchArg
 
 // CSR check, b~ = float32(b), slice widths (one warp per slice).  Also
 // notes whether some entry kept in the slices (the first wcap of its row)
-// lies more than 32767 columns from its row: the fill then stores 32-bit
-// columns, otherwise 16-bit offsets from the row.
+// lies more than 32767 columns from its row: the fill then writes no 16-bit
+// copy of the columns.
 static __device__ void sys_rows(const Team& t, const BatchSys& s) {
   Ctl* c = s.w.ctl;
   const int lane = threadIdx.x & 31;
