@@ -58,6 +58,11 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve section")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched-solve section")
     ap.add_argument("--batch-systems", type=int, default=512)
+    ap.add_argument("--batch-profile-case", action="store_true",
+                    help="run only a small batch for an ncu capture: the first --batch-systems "
+                         "systems of the batch family, Algorithm I at eps1 = 1e-6, once with the "
+                         "column format chosen per system and once with 32-bit columns (four "
+                         "k_batch launches)")
     ap.add_argument("--batch-eps1-sweep", action="store_true",
                     help="with the batch section: also time the batch at every fixed eps1 "
                          "(Algorithm I) and account for its block-time per launch")
@@ -524,6 +529,44 @@ def batch_section(args, dev, steps, warmup):
     }
 
 
+def batch_profile_case(args, dev):
+    """A small batch for an ncu capture (`-k regex:k_batch`): the first
+    --batch-systems systems of the batch family (seed 11), Algorithm I at
+    eps1 = 1e-6 and 32768 rows per block, once with the column format chosen
+    per system (16-bit offsets where they fit) and once with 32-bit columns:
+    launches 0-1 and 2-3.  Prints each call's milliseconds and the records'
+    column formats."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2412_08059_gb300 import mpcg
+
+    descs = synth.batch_family(512, seed=11)[: args.batch_systems]
+    mats = [synth.build_desc(d) for d in descs]
+    dmats = [mpcg.DeviceCSR.from_host(A, dev) for A in mats]
+    dbs = [torch.from_numpy(synth.rhs(A, seed=1000 + i)[1]).to(dev) for i, A in enumerate(mats)]
+    xs = [torch.empty(A.n, dtype=torch.float64, device=dev) for A in mats]
+    ws = torch.empty(mpcg.batch_workspace_bytes(dmats), dtype=torch.uint8, device=dev)
+    res = mpcg.result_buffer(len(mats), dev)
+    out = {"systems": len(mats), "sum_n": int(sum(A.n for A in mats)),
+           "sum_nnz": int(sum(A.nnz for A in mats))}
+    for v in (0, 1):
+        o = mpcg.options(eps1=1e-6, team_rows=32768, spmv_variant=v)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mpcg.solve_batch_async(dmats, dbs, xs, o, ws, res, None)
+        e1.record()
+        torch.cuda.synchronize()
+        rr = mpcg.read_results(res, len(mats))
+        out[f"spmv_variant_{v}"] = {
+            "ms": round(e0.elapsed_time(e1), 3),
+            "systems_16bit": int(sum(r["spmv_cols"] == 16 for r in rr)),
+            "sum_n1": int(sum(r["n1"] for r in rr)), "sum_n2": int(sum(r["n2"] for r in rr)),
+            "failed": int(sum(r["status"] < 0 for r in rr))}
+    return out
+
+
 def batch_eps1_sweep(mpcg, dmats, dbs, xs, ws, res, S, team_rows, timed):
     """The batch at one team granularity: pure FP64, auto eps1 and every fixed
     eps1 = 1e-2 .. 1e-7 (Algorithm I).  Per mode: ms per batch, mean N1 and N2,
@@ -721,6 +764,10 @@ def native_arm(args, rank, world, local_rank):
         torch.distributed.barrier()
     mpcg.load()
 
+    if args.batch_profile_case:
+        if rank == 0:
+            print(json.dumps({"batch_profile_case": batch_profile_case(args, dev)}), flush=True)
+        return
     if args.batch_only:
         if rank == 0:
             print(json.dumps({"batch": batch_section(args, dev, args.steps, args.warmup)}), flush=True)
