@@ -286,6 +286,21 @@ int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const double* const*
                          const mpcg_options_t* opts, void* ws, size_t ws_bytes,
                          mpcg_result_t* res, mpcg_stream_t stream);
 
+/* Plan of the batched solve (not in the paper; host only when grid_blocks > 0):
+ * the team size (blocks) the planner of mpcg_solve_batch gives each system,
+ * from n and nnz and the options' team_rows and team_rows_sys, for a grid of
+ * grid_blocks blocks (0: the grid mpcg_solve_batch would launch with these
+ * options on the current device).  A system goes to the smallest team (1, 2,
+ * 4, ..., 128 blocks) with at most its rows per block; while one team of
+ * every size present does not fit in the grid, the largest size present is
+ * halved.  At run time a larger team may also take a system from a smaller
+ * size's queue when its own is empty.  team_blocks_out: host int32[nsys].
+ * MPCG_ERR_INVALID_ARG on bad arguments, MPCG_ERR_CUDA if grid_blocks is 0
+ * and the device cannot be queried. */
+int32_t mpcg_batch_plan(int32_t nsys, const int32_t* n, const int32_t* nnz,
+                        const mpcg_options_t* opts, int32_t grid_blocks,
+                        int32_t* team_blocks_out);
+
 /* Autotuner of the batched solve (not in the paper): the tile shape of every
  * system, i.e. its team size.  Times mpcg_solve_batch with the given arguments
  * at each of MPCG_TUNE_CANDIDATES team granularities (opts->team_rows =

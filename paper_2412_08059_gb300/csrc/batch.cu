@@ -387,6 +387,30 @@ extern "C" size_t mpcg_batch_workspace_bytes(int32_t nsys, const int32_t* n, con
   return total;
 }
 
+extern "C" int32_t mpcg_batch_plan(int32_t nsys, const int32_t* n, const int32_t* nnz,
+                                   const mpcg_options_t* opts, int32_t grid_blocks,
+                                   int32_t* team_blocks_out) {
+  if (nsys <= 0 || !n || !nnz || !opts || !team_blocks_out || grid_blocks < 0)
+    return MPCG_ERR_INVALID_ARG;
+  std::vector<int> nv(nsys);
+  std::vector<double> work(nsys);
+  for (int32_t i = 0; i < nsys; ++i) {
+    if (n[i] <= 0 || nnz[i] < 0) return MPCG_ERR_INVALID_ARG;
+    nv[i] = n[i];
+    work[i] = work_of(n[i], nnz[i]);
+  }
+  int grid = grid_blocks;
+  if (grid == 0) {  // the grid mpcg_solve_batch would launch with these options
+    const int smem = team_smem((const void*)k_batch<1>, 1);
+    grid = smem < 0 ? 0 : batch_grid(opts->grid_blocks, smem);
+    if (grid <= 0) return MPCG_ERR_CUDA;
+  }
+  const Plan P = make_plan(nsys, nv.data(), work.data(), grid, opts->team_rows, opts->team_rows_sys);
+  for (int c = 0; c < kTeamClasses; ++c)
+    for (int k = 0; k < P.qlen[c]; ++k) team_blocks_out[P.order[P.qbase[c] + k]] = 1 << c;
+  return MPCG_OK;
+}
+
 extern "C" int32_t mpcg_solve_batch(int32_t nsys, const mpcg_csr_t* A, const double* const* b,
                                     double* const* x, const mpcg_sample_t* sample,
                                     const mpcg_options_t* opts, void* ws, size_t ws_bytes,

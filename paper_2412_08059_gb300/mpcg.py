@@ -91,7 +91,7 @@ SYMBOLS = ("mpcg_options_default", "mpcg_status_string", "mpcg_workspace_bytes",
            "mpcg_choose_eps1", "mpcg_solve", "mpcg_batch_workspace_bytes", "mpcg_solve_batch",
            "mpcg_spmv", "mpcg_bfs", "mpcg_pseudo_diameter", "mpcg_solve_static",
            "mpcg_server_workspace_bytes", "mpcg_server_create", "mpcg_server_destroy",
-           "mpcg_server_admit", "mpcg_batch_step", "mpcg_batch_step_launches", "mpcg_server_retire", "mpcg_batch_tune",
+           "mpcg_server_admit", "mpcg_batch_step", "mpcg_batch_step_launches", "mpcg_server_retire", "mpcg_batch_tune", "mpcg_batch_plan",
            "mpcg_knn_batch")
 
 
@@ -132,6 +132,8 @@ def load(path: str = LIB_PATH):
         L.mpcg_bfs.argtypes = [C.POINTER(CsrDesc), I32, P, P, SZ, P]
         L.mpcg_pseudo_diameter.restype = I32
         L.mpcg_pseudo_diameter.argtypes = [C.POINTER(CsrDesc), P, P, SZ, P]
+        L.mpcg_batch_plan.restype = I32
+        L.mpcg_batch_plan.argtypes = [I32, P, P, C.POINTER(Options), I32, P]
         L.mpcg_batch_tune.restype = I32
         L.mpcg_batch_tune.argtypes = [I32, P, P, P, C.POINTER(SampleDesc), C.POINTER(Options),
                                       P, SZ, P, P, C.POINTER(I32), P, P]
@@ -385,6 +387,19 @@ def batch_tune(mats: list[DeviceCSR], bs: list, xs: list, opts: Options, ws: tor
     if per_system:
         return best.value, list(ms), rows
     return best.value, list(ms)
+
+
+def batch_plan(ns, nnzs, opts: Options | None = None, grid_blocks: int = 0) -> list[int]:
+    """mpcg_batch_plan: the team size (blocks) the batch planner gives each
+    system (host only when grid_blocks > 0)."""
+    k = len(ns)
+    nv = (C.c_int32 * k)(*[int(v) for v in ns])
+    mv = (C.c_int32 * k)(*[int(v) for v in nnzs])
+    out = (C.c_int32 * k)()
+    o = opts if opts is not None else options()
+    _check(load().mpcg_batch_plan(k, nv, mv, C.byref(o), int(grid_blocks), out),
+           "mpcg_batch_plan")
+    return list(out)
 
 
 def batch_workspace_bytes(mats: list[DeviceCSR]) -> int:

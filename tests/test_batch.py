@@ -242,8 +242,13 @@ def test_batch_per_system_team_sizes(mp):
     bs = [synth.rhs(A, seed=160 + i)[1] for i, A in enumerate(mats)]
     rows = [CANDIDATES[i % 4] // 8 if i % 3 == 0 else CANDIDATES[i % 4] for i in range(len(mats))]
     xs, rs = run_batch(mp, mats, bs, None, eps1=1e-5, team_rows_sys=rows)
+    # the planner's sizes on the grid the call used; a larger team may also take
+    # a system from a smaller size's queue
+    plan = mp.batch_plan([A.n for A in mats], [A.nnz for A in mats],
+                         mp.options(eps1=1e-5, team_rows_sys=rows), 0)
     near = lambda a, c: abs(a - c) <= max(2, int(0.02 * max(a, c)))
-    for A, b, x, r in zip(mats, bs, xs, rs):
+    for A, b, x, r, z in zip(mats, bs, xs, rs, plan):
+        assert r["team_blocks"] >= z and r["team_blocks"] & (r["team_blocks"] - 1) == 0, (A.n, r, z)
         xo, ro = oracle.solve(A, b, eps1=1e-5)
         assert r["status"] == ro["status"], (A.n, r, ro)
         assert near(r["n1"], ro["n1"]) and near(r["n2"], ro["n2"]), (A.n, r, ro)
